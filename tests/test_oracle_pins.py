@@ -1,0 +1,332 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed forms, an eigen-decomposition of the exact linear solution, the Arnoldi relation
+written with a dense inverse, finite differences, convergence orders and invariants."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from synth import circuits as S
+from oracle import ers_oracle as O
+
+
+def exact_linear_step(circ, x, t, h):
+    """Exact solution of C x' = -G x + B u(t) over [t, t+h] with u linear on the step,
+    by the generalized symmetric eigenproblem G q = lambda C q (independent of expm)."""
+    G = circ.G.toarray(); C = circ.C.toarray(); B = circ.B.toarray()
+    lam, Q = sla.eigh(G, C)          # Q^T C Q = I, J = -C^{-1} G = Q (-lam) Q^{-1}
+    uk = circ.u(t); s = (circ.u(t + h) - uk) / h
+    y0 = Q.T @ C @ x
+    f = Q.T @ B @ uk
+    g = Q.T @ B @ s
+    e = np.exp(-lam * h)
+    y = e * y0 + f * (1 - e) / lam + g * (h / lam - (1 - e) / lam ** 2)
+    return Q @ y
+
+
+# --- Whole ER step, linear circuits: exact up to the Krylov error (Eq. 13) ---------------
+def test_single_rc_step_current_closed_form():
+    g, c, i0 = 1e-3, 1e-15, 1e-3
+    circ = S.single_rc(g=g, c=c, i_amp=i0)
+    for h in (1e-13, 1e-12, 5e-12):
+        r = O.er_step(circ, np.zeros(1), 0.0, h, m=3)
+        exact = (i0 / g) * (1 - np.exp(-h * g / c))
+        assert abs(r.x[0] - exact) <= 1e-13 * abs(exact)
+        assert r.m1 == 1  # one-dimensional space: happy breakdown at j = 1
+
+
+def test_single_rc_ramp_closed_form():
+    g, c, s = 2e-3, 3e-15, 1e9
+    circ = S.single_rc(g=g, c=c, ramp=s, t_end=20e-12)
+    tau = c / g
+    for h in (1e-13, 2e-12, 7e-12):
+        r = O.er_step(circ, np.zeros(1), 0.0, h, m=3)
+        exact = (s / g) * (h - tau * (1 - np.exp(-h / tau)))
+        assert abs(r.x[0] - exact) <= 1e-12 * abs(exact)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_rc_step_matches_eigen_solution(seed):
+    circ = S.random_rc(n=16, seed=seed)
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=circ.n) * 0.1
+    t, h = 3e-12, 2e-12       # inside a ramp for some sources
+    bps = circ.breakpoints()
+    assert not np.any((bps > t) & (bps < t + h)) or True
+    nb = bps[bps > t]
+    h = min(h, nb[0] - t) if nb.size else h
+    r = O.er_step(circ, x, t, h, m=circ.n)
+    ex = exact_linear_step(circ, x, t, h)
+    assert np.max(np.abs(r.x - ex)) <= 1e-11 * np.max(np.abs(ex))
+
+
+def test_random_rc_trajectory_exact():
+    circ = S.random_rc(n=12, seed=5, p=3, t_end=30e-12)
+    bps = list(circ.breakpoints())
+    grid = sorted(set([0.0] + [b for b in bps if b < circ.t_end] + [circ.t_end]))
+    x = np.zeros(circ.n); xe = np.zeros(circ.n)
+    for a, b in zip(grid[:-1], grid[1:]):
+        x = O.er_step(circ, x, a, b - a, m=circ.n).x
+        xe = exact_linear_step(circ, xe, a, b - a)
+    # m = n spans the whole space in exact arithmetic; in floating point plain MGS (no
+    # re-orthogonalisation) on a stiff spectrum (tau 3e-14 .. 7e-12 s) loses ~1e-8 on
+    # some steps, while any dropped term or sign error shows up at the O(h) ~ 1e-2 level.
+    assert np.max(np.abs(x - xe)) <= 1e-6 * np.max(np.abs(xe))
+
+
+def test_combined_vector_equals_separate_spaces():
+    circ = S.random_rc(n=16, seed=4)
+    x = np.random.default_rng(1).normal(size=circ.n) * 0.05
+    a = O.er_step(circ, x, 5e-12, 1e-12, m=circ.n)
+    b = O.er_step(circ, x, 5e-12, 1e-12, m=circ.n, opts=O.Options(combined=True))
+    assert np.max(np.abs(a.x - b.x)) <= 1e-11 * np.max(np.abs(a.x))
+
+
+# --- ER formula with explicit phi functions (Eq. 9-13) ----------------------------------
+def phi_step_dense(circ, x, t, h):
+    """x + h phi1(hJ) g_k + h^2 phi2(hJ) b_k with J = -C^{-1} G_k, g_k and b_k of Eq. 12 and
+    Eq. 12's input term, phi functions of Eq. 9 applied per eigenvalue of J."""
+    lin = O.linearize(circ, x)
+    C = circ.C.toarray(); Gk = lin.Gk.toarray(); Ci = np.linalg.inv(C)
+    J = -Ci @ Gk
+    uk = circ.u(t); s = (circ.u(t + h) - uk) / h
+    g = J @ x + Ci @ (lin.F + circ.B @ uk)
+    b = Ci @ (circ.B @ s)
+    lam, Q = np.linalg.eig(J)
+    Qi = np.linalg.inv(Q)
+    z = h * lam
+    phi1 = (np.exp(z) - 1) / z
+    phi2 = (np.exp(z) - 1 - z) / z ** 2
+    step = Q @ (h * phi1 * (Qi @ g) + h * h * phi2 * (Qi @ b))
+    return x + step.real
+
+
+def test_er_step_nonlinear_equals_phi_formula():
+    circ = S.inverter_chain(stages=2, tree_nodes=3, seed=7, t_end=1e-9)
+    x = O.dc_solution(circ)
+    x = x + np.random.default_rng(0).normal(size=circ.n) * 0.05
+    t = 0.1e-9 + 2e-12   # on the input's rising edge
+    h = 3e-12
+    r = O.er_step(circ, x, t, h, m=circ.n)
+    ref = phi_step_dense(circ, x, t, h)
+    assert np.max(np.abs(r.x - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+
+
+# --- MEVP_IKS / Arnoldi (Algorithm 1, Eq. 14, Eq. 16) -----------------------------------
+def _basis(circ, m, seed=0):
+    lin = O.linearize(circ, np.zeros(circ.n))
+    v = np.random.default_rng(seed).normal(size=circ.n)
+    return lin, O.arnoldi_iks(circ.C, lin, lin.Gk, v, 1e-12, 1e-7, m, 1, m), v
+
+
+def test_arnoldi_relation_and_orthonormality():
+    circ = S.random_rc(n=30, seed=11)
+    m = 10
+    lin, K, v = _basis(circ, m)
+    Jinv = -np.linalg.inv(circ.G.toarray()) @ circ.C.toarray()
+    lhs = Jinv @ K.V[:, :m]
+    rhs = K.V[:, :m + 1] @ K.H[:m + 1, :m]
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(lhs))
+    assert np.max(np.abs(K.V.T @ K.V - np.eye(m + 1))) <= 1e-10
+    assert np.allclose(K.V[:, 0] * K.beta, v, rtol=0, atol=1e-14 * np.max(np.abs(v)))
+
+
+def test_residual_formula_matches_kcl_residual():
+    circ = S.random_rc(n=30, seed=12)
+    m = 6
+    lin, K, v = _basis(circ, m)
+    G = circ.G.toarray(); C = circ.C.toarray()
+    for h in (1e-13, 1e-12, 1e-11):
+        Hm = K.H[:m, :m]
+        Hinv = np.linalg.inv(Hm)
+        E = sla.expm(h * Hinv)
+        xm = K.beta * K.V[:, :m] @ E[:, 0]
+        dxm = K.beta * K.V[:, :m] @ (Hinv @ E[:, 0])
+        r_explicit = C @ dxm + G @ xm                 # C (dx/dt - J x)
+        r_formula = K.residual(m, h) * K.beta * np.linalg.norm(G @ K.V[:, 0])
+        # the identity rests on the Arnoldi relation (1e-12 of ||J^-1 V||); the residual is
+        # a small difference of large terms, so agreement to 1e-6 of its norm is the bar
+        assert abs(np.linalg.norm(r_explicit) - r_formula) <= 1e-6 * np.linalg.norm(r_explicit)
+
+
+def test_exp_small_against_eigendecomposition():
+    rng = np.random.default_rng(3)
+    m = 8
+    S_ = rng.normal(size=(m, m)) + 3 * np.eye(m)
+    D = -np.exp(rng.uniform(np.log(1e-15), np.log(1e-12), m))   # Ritz values: -tau_i
+    Hm = S_ @ np.diag(D) @ np.linalg.inv(S_)
+    h = 1e-13
+    y, last = O.exp_hinv_e1(Hm, h)
+    ref = S_ @ (np.exp(h / D) * np.linalg.solve(S_, np.eye(m)[:, 0]))
+    assert np.max(np.abs(y - ref)) <= 1e-9 * max(1e-300, np.max(np.abs(ref))) + 1e-14
+    ref_last = (S_ @ ((1 / D) * np.exp(h / D) * np.linalg.solve(S_, np.eye(m)[:, 0])))[m - 1]
+    assert abs(last - ref_last) <= 1e-8 * abs(ref_last) + 1e-14 * np.max(np.abs(1 / D))
+
+
+def test_exp_small_scalar():
+    for mu, h in ((-1e-12, 3e-13), (-5e-15, 1e-14)):
+        y, last = O.exp_hinv_e1(np.array([[mu]]), h)
+        assert abs(y[0] - np.exp(h / mu)) <= 1e-15
+        assert abs(last - np.exp(h / mu) / mu) <= 1e-13 * abs(1 / mu)
+
+
+def test_zero_vector_mevp_is_zero():
+    circ = S.random_rc(n=10, seed=1)
+    lin = O.linearize(circ, np.zeros(circ.n))
+    K = O.arnoldi_iks(circ.C, lin, lin.Gk, np.zeros(circ.n), 1e-12, 1e-7, 10)
+    assert K.beta == 0.0 and np.all(K.mevp(1e-12) == 0.0)
+
+
+def test_scaling_invariance_retry_equals_fresh_step():
+    circ = S.random_rc(n=20, seed=8)
+    x = np.random.default_rng(2).normal(size=circ.n) * 0.1
+    t, h, m = 6e-12, 1e-12, 8
+    lin = O.linearize(circ, x)
+    st = O.step_setup(circ, lin, t, O.pwl_slope(circ, t, h))
+    st.K1 = O.arnoldi_iks(circ.C, lin, lin.Gk, st.v1, h, 1e-7, m, 1, m)
+    st.K2 = O.arnoldi_iks(circ.C, lin, lin.Gk, st.v2, h, 1e-7, m, 1, m) if np.any(st.v2) else None
+    for a in (0.5, 0.25):
+        reused = O.er_update(st, a * h)
+        fresh = O.er_step(circ, x, t, a * h, m=m).x
+        assert np.max(np.abs(reused - fresh)) <= 1e-12 * np.max(np.abs(fresh))
+
+
+# --- Device model ----------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_mosfet_partials_finite_difference(dtype):
+    rng = np.random.default_rng(dtype)
+    for _ in range(200):
+        vd, vg, vs = rng.uniform(-0.2, 1.2, 3)
+        vt, k, lam = 0.35, 1e-4, 0.05
+        i0, dvd, dvg, dvs = O.mosfet_eval(dtype, vd, vg, vs, vt, k, lam)
+        eps = 1e-7
+        for idx, der in ((0, dvd), (1, dvg), (2, dvs)):
+            vp = [vd, vg, vs]; vm = [vd, vg, vs]
+            vp[idx] += eps; vm[idx] -= eps
+            fd = (O.mosfet_eval(dtype, *vp, vt, k, lam)[0] - O.mosfet_eval(dtype, *vm, vt, k, lam)[0]) / (2 * eps)
+            assert abs(fd - der) <= 1e-6 * k + 1e-3 * abs(der)
+
+
+def test_mosfet_symmetry_and_regions():
+    vt, k = 0.3, 1e-4
+    # source/drain swap: I(d,g,s) = -I(s,g,d)
+    a = O.mosfet_eval(0, 0.2, 1.0, 0.7, vt, k, 0.0)[0]
+    b = O.mosfet_eval(0, 0.7, 1.0, 0.2, vt, k, 0.0)[0]
+    assert a == -b
+    # saturation value and cut-off
+    assert abs(O.mosfet_eval(0, 1.0, 0.8, 0.0, vt, k, 0.0)[0] - 0.5 * k * 0.5 ** 2) < 1e-18
+    assert O.mosfet_eval(0, 1.0, 0.2, 0.0, vt, k, 0.0)[0] == 0.0
+    # PMOS with source at vdd, gate low, drain low: current flows from source into drain
+    assert O.mosfet_eval(1, 0.0, 0.0, 1.0, vt, k, 0.0)[0] < 0.0
+
+
+def test_device_jacobian_finite_difference():
+    circ = S.inverter_chain(stages=3, tree_nodes=4, seed=3)
+    x = np.random.default_rng(5).uniform(0, 1, circ.n)
+    idev, Gdev = O.device_eval(circ, x)
+    Gd = Gdev.toarray()
+    eps = 1e-7
+    for j in range(circ.n):
+        xp = x.copy(); xp[j] += eps
+        xm = x.copy(); xm[j] -= eps
+        fd = (O.device_eval(circ, xp)[0] - O.device_eval(circ, xm)[0]) / (2 * eps)
+        assert np.max(np.abs(fd - Gd[:, j])) <= 1e-9
+
+
+# --- DC, convergence orders, error estimate --------------------------------------------
+def test_dc_inverter_rails():
+    circ = S.inverter_chain(stages=6, tree_nodes=5, seed=4)
+    x = O.dc_solution(circ)
+    outs = [int(d["d"]) for d in circ.dev[::2]]
+    expect = [1.0 if s % 2 == 0 else 0.0 for s in range(len(outs))]
+    assert np.max(np.abs(x[outs] - expect)) < 1e-5
+    idev, _ = O.device_eval(circ, x)
+    res = circ.G @ x + idev - circ.B @ circ.u(0.0)
+    assert np.max(np.abs(res)) <= 1e-12
+
+
+def _switching_window():
+    circ = S.inverter_chain(stages=2, tree_nodes=3, seed=9, t_end=1e-9)
+    x0 = O.dc_solution(circ)
+    return circ, x0, 0.11e-9, 0.11e-9 + 16e-12
+
+
+def _fixed_er(circ, x0, t0, t1, h, m=0, correction=False):
+    """Fixed-h ER steps; m = 0 takes the Krylov dimension from the Eq.-16 test at a tight
+    eps so that the Krylov error stays far below the time-discretisation error."""
+    x = x0.copy(); t = t0
+    nsteps = int(round((t1 - t0) / h))
+    opts = O.Options(correction=correction, eps=1e-12, m_max=circ.n)
+    for _ in range(nsteps):
+        x = O.er_step(circ, x, t, h, m=m, opts=opts).x
+        t += h
+    return x
+
+
+def test_er_second_order_on_nonlinear_circuit():
+    circ, x0, t0, t1 = _switching_window()
+    ref = _fixed_er(circ, x0, t0, t1, 0.03125e-12)
+    e = [np.max(np.abs(_fixed_er(circ, x0, t0, t1, h) - ref)) for h in (2e-12, 1e-12, 0.5e-12)]
+    for a, b in zip(e[:-1], e[1:]):
+        assert 3.0 < a / b < 6.0, e          # order 2: error / 4 per halving of h
+
+
+def test_be_first_order_and_er_beats_be():
+    circ, x0, t0, t1 = _switching_window()
+    ref = _fixed_er(circ, x0, t0, t1, 0.03125e-12)
+
+    def be(h):
+        x = x0.copy()
+        for k in range(int(round((t1 - t0) / h))):
+            x = O.be_run(_shifted(circ, t0 + k * h), h, t_end=h, x0=x)
+        return x
+
+    e_be = [np.max(np.abs(be(h) - ref)) for h in (1e-12, 0.5e-12, 0.25e-12)]
+    for a, b in zip(e_be[:-1], e_be[1:]):
+        assert 1.4 < a / b < 2.6, e_be            # order 1 (pre-asymptotic above 1.4)
+    e_er = np.max(np.abs(_fixed_er(circ, x0, t0, t1, 1e-12) - ref))
+    assert e_er < e_be[0]                         # Fig. 2: ER more accurate than BENR at equal h
+
+
+def _shifted(circ, t0):
+    """Same circuit with its sources shifted so that local time 0 is global time t0."""
+    pwl = []
+    for tt, vv in circ.pwl:
+        grid = np.unique(np.concatenate([[t0], tt[tt > t0]])) - t0
+        pwl.append((grid, np.interp(grid + t0, tt, vv)))
+    return S.Circuit(name=circ.name, n=circ.n, G=circ.G, C=circ.C, B=circ.B, dev=circ.dev,
+                     pwl=pwl, vdd=circ.vdd, t_end=circ.t_end - t0, meta=circ.meta)
+
+
+def test_error_estimate_second_order():
+    circ, x0, t0, _ = _switching_window()
+    opts = O.Options(eps=1e-12, m_max=circ.n)
+    errs = [O.er_step(circ, x0, t0 + 5e-12, h, m=0, opts=opts).err_inf for h in (2e-12, 1e-12, 0.5e-12)]
+    # dF = O(h^2) since F'(x_k) = 0; h phi_1(hJ) C^{-1} is O(h) for non-stiff modes and
+    # O(1) (-> G^{-1}) for stiff ones, so e_rr falls like h^2 .. h^3
+    assert errs[0] > errs[1] > errs[2] > 0
+    for a, b in zip(errs[:-1], errs[1:]):
+        assert 2.5 < a / b < 9.0, errs
+
+
+def test_linear_circuit_error_estimate_is_zero():
+    circ = S.random_rc(n=10, seed=3)
+    r = O.er_step(circ, np.zeros(circ.n), 0.0, 1e-12, m=5)
+    assert r.err_inf == 0.0
+
+
+def test_adaptive_run_one_lu_per_step_and_accuracy():
+    circ = S.inverter_chain(stages=3, tree_nodes=4, seed=6, t_end=0.3e-9)
+    x, t, st = O.er_run(circ, tol=1e-6)
+    assert abs(t - circ.t_end) < 1e-20
+    assert st.lu == st.steps                       # no LU on a rejected try
+    ref = _fixed_er(circ, O.dc_solution(circ), 0.0, circ.t_end, 0.05e-12)
+    assert np.max(np.abs(x - ref)) < 50 * 1e-6 * st.steps ** 0.5
+
+
+def test_ercorrection_runs_and_changes_solution():
+    circ, x0, t0, t1 = _switching_window()
+    ref = _fixed_er(circ, x0, t0, t1, 0.03125e-12)
+    a = _fixed_er(circ, x0, t0, t1, 2e-12, correction=False)
+    b = _fixed_er(circ, x0, t0, t1, 2e-12, correction=True)
+    assert np.max(np.abs(a - b)) > 0
+    assert np.all(np.isfinite(b))
