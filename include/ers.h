@@ -1,0 +1,184 @@
+/*
+ * ers.h -- C ABI of a GB300 (sm_103a) FP64 implementation of the exponential
+ * Rosenbrock-Euler (ER) circuit transient with the invert-Krylov matrix exponential
+ * (Zhuang, Yu, Kang, Wang, Cheng, DAC 2015, arXiv 1511.04515).
+ *
+ * Problem (Sec. II, Eq. 1; Sec. III linearised form):
+ *     C x'(t) + G_lin x + i_dev(x) = B u(t)
+ * x: node voltages (n), C: capacitances (n x n), G_lin: linear conductances (n x n),
+ * i_dev: square-law MOSFET currents, B (n x p) with piecewise-linear inputs u(t).
+ * At x_k the step uses G_k = G_lin + d i_dev/dx (x_k) and the remainder
+ * F(x) = (G_k - G_lin) x - i_dev(x), so that C x' = -G_k x + F(x) + B u (Sec. III).
+ *
+ * Conventions shared by every entry point:
+ *  - All pointers are HOST pointers unless a name ends in _dev.  Inputs are copied; the
+ *    caller keeps ownership of everything it passes and of every output buffer.
+ *  - CSR matrices are 0-based with sorted, unique column indices per row.
+ *  - Every call returns an ers_status and never aborts the process; on failure
+ *    ers_last_error() returns a message.  No call traps or hangs the GPU: device-side
+ *    waits are bounded and report ERS_ERR_TIMEOUT.
+ *  - A context is bound to the CUDA device that was current at ers_create and to one
+ *    CUDA stream (ers_set_stream); calls on one context must not overlap.
+ */
+#ifndef ERS_H
+#define ERS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ers_ctx ers_ctx;
+
+typedef enum {
+  ERS_OK = 0,
+  ERS_ERR_INVALID = 1,          /* bad argument, bad CSR, step crossing a PWL corner   */
+  ERS_ERR_SINGULAR = 2,         /* zero / tiny pivot in the static-pivot LU of G_k      */
+  ERS_ERR_NONFINITE = 3,        /* NaN or Inf in inputs or results                       */
+  ERS_ERR_STEP_UNDERFLOW = 4,   /* adaptive h fell below h_min                           */
+  ERS_ERR_KRYLOV = 5,           /* exp(h H_m^{-1}) not finite in fixed-m mode            */
+  ERS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up                    */
+  ERS_ERR_CUDA = 7,             /* CUDA runtime error                                    */
+  ERS_ERR_OOM = 8               /* device allocation failed                              */
+} ers_status;
+
+typedef struct {
+  int32_t n_rows, n_cols, nnz;
+  const int32_t* rowptr;        /* n_rows + 1 */
+  const int32_t* colidx;        /* nnz */
+  const double* val;            /* nnz */
+} ers_csr;
+
+/* MOSFET record (square-law stand-in for the paper's BSIM3 devices, Sec. V).
+ * type 0 = NMOS, 1 = PMOS; terminals are node indices, -1 = ground, -2 = vdd rail.
+ * Current flows d -> s; source/drain swap when v_ds < 0; PMOS mirrors NMOS. */
+typedef struct {
+  int32_t type, d, g, s;
+  double vt, k, lambda;
+} ers_mosfet;
+
+/* Piecewise-linear input (Sec. III, u linear on every step): npts corner times
+ * (strictly increasing) and values; constant before the first and after the last. */
+typedef struct {
+  int32_t npts;
+  const double* t;
+  const double* v;
+} ers_pwl;
+
+typedef struct {
+  double eps_krylov;   /* Krylov residual tolerance of Eq. 16, relative (default 1e-7, Sec. V) */
+  double E_rr;         /* absolute error budget of Alg. 2 (0: tol * max(1, ||x||_inf))          */
+  double alpha;        /* h <- alpha h on rejection (Alg. 2, default 0.5)                        */
+  double beta;         /* h <- beta h after a fast acceptance (Alg. 2, default 2)                */
+  double gamma;        /* ER-C correction weight (Eq. 17, default 0.1)                            */
+  double h_min;        /* step underflow limit (default 1e-20 s)                                  */
+  double h_max;        /* largest step (0: t_end / 100)                                           */
+  double h_init;       /* first step (0: h_max)                                                   */
+  double vdd;          /* supply rail voltage for terminals tagged -2 (default 1 V)               */
+  int32_t i_grow;      /* grow h when the retry count i < i_grow (Alg. 2, default 5)              */
+  int32_t m_min;       /* first dimension at which Eq. 16 is tested (default 3)                   */
+  int32_t m_max;       /* Algorithm 1's m_c (default 40, at most 64)                              */
+  int32_t combined_vector; /* 1: one Krylov space on v1 + v2 instead of two (default 0)           */
+  int32_t correction;  /* 1: ER-C (Eq. 20), 0: ER (default 0)                                      */
+} ers_opts;
+
+typedef struct {
+  int64_t steps, rejects, refactors, krylov_vectors, solves;
+  int32_t n, nsn, nlevels, etree_height, max_front;
+  int64_t nnz_L, factor_doubles, arena_doubles;
+  double refactor_flops;
+  int64_t kernel_launches;     /* kernels launched by the library so far              */
+  int64_t solve_passes;        /* forward+backward solve pairs (any number of RHS)    */
+  int64_t solve_rhs;           /* right-hand sides solved                              */
+  double solve_ms;             /* device time of the solve kernels (profiling on)     */
+  double solve_bytes_per_pass; /* factor bytes one solve pair reads (values+indices)  */
+  double solve_fma_per_rhs;    /* FP64 FMAs of one solve pair per right-hand side     */
+} ers_stats_t;
+
+/* Fill opts with the defaults listed above. */
+ers_status ers_default_opts(ers_opts* opts);
+
+/* Create a simulation context (Alg. 2 "initialization phase": load netlist, build linear
+ * matrices).  G_lin, C: n x n; B: n x p; dev: ndev MOSFETs (may be NULL if ndev = 0);
+ * u: p PWL inputs.  Performs the one-time symbolic analysis of G_k's pattern (the union of
+ * G_lin and the device stamps) and allocates device memory.  The state starts at t = 0,
+ * x = 0; call ers_dc for the DC operating point.  opts may be NULL (defaults). */
+ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, const ers_csr* B,
+                      const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
+                      const ers_opts* opts);
+
+/* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL = a private stream
+ * created at ers_create).  All device work of later calls is ordered on it. */
+ers_status ers_set_stream(ers_ctx* ctx, void* stream);
+
+/* x(0) = DC solution (Alg. 2): Newton on G_lin x + i_dev(x) = B u(0) through the same LU
+ * kernels (voltage step clamp 0.5 V, at most 50 iterations, residual 1e-12 A).
+ * x0_guess (n, may be NULL = zeros) is the starting point.  Sets t = 0. */
+ers_status ers_dc(ers_ctx* ctx, const double* x0_guess);
+
+/* Device evaluation at the current x, stamping of G_k and the numeric LU refactor of G_k
+ * (Alg. 2: "Derive C_k, G_k, F_k" and "LU_decompose(G_k)"; C is never factored). */
+ers_status ers_refactor(ers_ctx* ctx);
+
+/* One ER (ER-C if opts.correction) step of exactly h from the current (t, x) (Eq. 13;
+ * error Eq. 15/19; correction Eq. 20).  m > 0: every Krylov space uses exactly m Arnoldi
+ * iterations (fewer only at a happy breakdown); m = 0: the dimension is chosen by the
+ * residual test of Eq. 16 (Algorithm 1).  [t, t+h] must not contain a PWL corner
+ * (ERS_ERR_INVALID).  Refactors G_k if x changed since the last factorisation.  On
+ * success x <- x_{k+1}, t <- t + h.  m_used (may be NULL) receives the dimension of the
+ * first Krylov space; err_inf (may be NULL) receives ||e_rr||_inf (0 for linear circuits). */
+ers_status ers_step(ers_ctx* ctx, double h, int32_t m, int32_t* m_used, double* err_inf);
+
+/* Adaptive transient from the current state to t_end (Alg. 2): one LU per accepted step,
+ * rejected tries shrink h by alpha and reuse the solution's Krylov bases (no LU); tol
+ * sets E_rr = tol * max(1 V, ||x_k||_inf) unless opts.E_rr > 0.  Steps are clipped to
+ * PWL corners, h_max and t_end.  max_steps > 0 stops after that many accepted steps
+ * (the proposed h is kept in the context, so a later call continues seamlessly). */
+ers_status ers_run(ers_ctx* ctx, double t_end, double tol, int32_t max_steps, int32_t* nsteps,
+                   int32_t* nreject);
+
+/* State access (original node order; caller-owned buffers of n doubles). */
+ers_status ers_get_state(const ers_ctx* ctx, double* t, double* x, double* h);
+ers_status ers_set_state(ers_ctx* ctx, double t, const double* x, double h);
+/* Same on device buffers (n doubles, original node order) for callers whose data already
+ * lives in GPU memory; ordered on the context's stream. */
+ers_status ers_get_state_dev(const ers_ctx* ctx, double* x_dev);
+ers_status ers_set_state_dev(ers_ctx* ctx, double t, const double* x_dev, double h);
+
+/* Building blocks, exposed for verification of each stage against an independent CPU
+ * implementation.  Vectors are host buffers of n doubles in original node order. */
+/* x = G_k^{-1} b with the current factorisation (forward + backward supernodal solves). */
+ers_status ers_solve(ers_ctx* ctx, const double* b, double* x);
+/* y = C v (sparse matrix-vector product with the capacitance matrix). */
+ers_status ers_spmv_C(ers_ctx* ctx, const double* v, double* y);
+/* MEVP_IKS (Algorithm 1): out = ||v|| V_m exp(h H_m^{-1}) e_1 with the current G_k; m > 0
+ * fixed dimension, m = 0 adaptive by Eq. 16.  m_used may be NULL. */
+ers_status ers_mevp(ers_ctx* ctx, const double* v, double h, int32_t m, double* out,
+                    int32_t* m_used);
+/* Small dense stage (Eq. 14, Eq. 16): for the m x m upper-left block of H (column-major,
+ * leading dimension ldh), y = exp(h H^{-1}) e_1 (m doubles) and
+ * last = e_m^T H^{-1} exp(h H^{-1}) e_1.  Runs the same device kernel the step uses. */
+ers_status ers_phi_small(ers_ctx* ctx, const double* H, int32_t ldh, int32_t m, double h,
+                         double* y, double* last);
+
+/* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
+ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
+/* Turn CUDA-event timing of the triangular-solve kernels on (1) or off (0); resets the
+ * accumulated solve_ms.  Events are recorded on the context's stream around each solve. */
+ers_status ers_profile(ers_ctx* ctx, int32_t enable);
+
+/* Host-only symbolic analysis of an n x n pattern (no GPU needed): fills the fields of
+ * out that describe the ordering and factor (n, nsn, nlevels, etree_height, max_front,
+ * nnz_L, factor_doubles, arena_doubles, refactor_flops).  perm (may be NULL) receives the
+ * fill-reducing permutation new -> old. */
+ers_status ers_analyze(const ers_csr* pattern, ers_stats_t* out, int32_t* perm);
+
+const char* ers_last_error(const ers_ctx* ctx);
+void ers_destroy(ers_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERS_H */

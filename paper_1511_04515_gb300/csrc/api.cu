@@ -1,0 +1,1099 @@
+// C ABI of the ER / invert-Krylov circuit transient (Sec. III-IV, Algorithms 1-2).
+// Host orchestration of the device kernels; all arithmetic of a step runs on the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "ers_internal.h"
+#include "kcommon.cuh"
+
+namespace ers {
+// k_factor.cu
+void launch_dev_eval(ers_ctx* c, const double* x, double* dev_I, int with_jac);
+void launch_stamp(ers_ctx* c);
+void launch_node_F(ers_ctx* c, int mode, const double* dev_In, const double* xn, double* out);
+cudaError_t launch_refactor(ers_ctx* c);
+cudaError_t factor_kernel_attributes();
+// k_solve.cu
+void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
+                 const double* x, double* y, double alpha);
+cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+// k_krylov.cu
+cudaError_t krylov_init_constants();
+cudaError_t launch_arnoldi_init(ers_ctx* c, const VecGroup& g, int adaptive);
+cudaError_t launch_mgs(ers_ctx* c, const VecGroup& g, int j, int adaptive);
+cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int m_max);
+cudaError_t launch_small_test(ers_ctx* c, const double* H, int ldh, int m, double h, double* y,
+                              double* last);
+cudaError_t launch_combine(ers_ctx* c, double* out, const double* in, double a, const VecGroup* g,
+                           const double* cb, const double* u0, double d0, const double* u1,
+                           double d1, unsigned long long* maxout);
+cudaError_t launch_absmax(ers_ctx* c, const double* x, unsigned long long* out);
+int coop_max_blocks(int sm_count);
+
+// ---------------------------------------------------------------------------------------
+// small kernels local to the driver
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np, double x) {
+  if (x <= t[0]) return v[0];
+  if (x >= t[np - 1]) return v[np - 1];
+  int lo = 0, hi = np - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (t[mid] <= x) lo = mid; else hi = mid;
+  }
+  double f = (x - t[lo]) / (t[hi] - t[lo]);
+  return v[lo] + f * (v[hi] - v[lo]);
+}
+
+// u = u(t); slope = (u(t+h) - u(t)) / h
+__global__ void k_pwl(int p, const int32_t* ptr, const double* tt, const double* vv, double t,
+                      double h, double* u, double* slope) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= p) return;
+  int o = ptr[q], np = ptr[q + 1] - ptr[q];
+  double u0 = pwl_eval(tt + o, vv + o, np, t);
+  u[q] = u0;
+  if (slope) slope[q] = h > 0.0 ? (pwl_eval(tt + o, vv + o, np, t + h) - u0) / h : 0.0;
+}
+
+// out = a*x + b*y (+ c*z)
+__global__ void k_axpby(int n, double* out, double a, const double* x, double b, const double* y,
+                        double c, const double* z) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = a * x[i];
+  if (y) v += b * y[i];
+  if (z) v += c * z[i];
+  out[i] = v;
+}
+
+// rhs = B u (+ F)
+__global__ void k_bu(int n, const int32_t* ptr, const int32_t* idx, const double* val,
+                     const double* u, const double* F, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = F ? F[i] : 0.0;
+  for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * u[idx[e]];
+  out[i] = acc;
+}
+
+// Newton update with voltage clamp: x += clamp(y - x, -lim, lim)
+__global__ void k_newton(int n, double* x, const double* y, double lim) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = y[i] - x[i];
+  d = fmin(fmax(d, -lim), lim);
+  x[i] += d;
+}
+
+// residual r = G_k x - F - B u (equals G_lin x + i_dev(x) - B u)
+__global__ void k_dc_res(int n, const int32_t* Gp, const int32_t* Gi, const double* Gv,
+                         const double* x, const double* F, const double* bu, double* r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int e = Gp[i]; e < Gp[i + 1]; ++e) acc += Gv[e] * x[Gi[e]];
+  r[i] = acc - F[i] - bu[i];
+}
+
+__global__ void k_permute(int n, const int32_t* perm, const double* src, double* dst, int inverse) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // forward: dst[new] = src[perm[new]] ; inverse: dst[perm[new]] = src[new]
+  if (!inverse) dst[i] = src[perm[i]];
+  else dst[perm[i]] = src[i];
+}
+
+struct RhsArgs {
+  int n, nv;
+  const double* x[MAX_RHS];
+  double* y;
+};
+__global__ void k_rhs_C(RhsArgs A, const int32_t* ptr, const int32_t* idx, const double* val) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  for (int v = 0; v < A.nv; ++v) {
+    double acc = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * A.x[v][idx[e]];
+    A.y[(int64_t)v * A.n + i] = acc;
+  }
+}
+
+}  // namespace ers
+
+using namespace ers;
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
+namespace {
+
+inline int nblk(int n, int b = 256) { return std::max(1, (n + b - 1) / b); }
+
+ers_status fail(ers_ctx* c, ers_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? ERS_ERR_OOM : ERS_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <class T>
+cudaError_t dalloc(T** dst, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, count) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemset(*dst, 0, std::max<size_t>(1, count) * sizeof(T));
+}
+
+std::string check_csr(const ers_csr* a, int rows, int cols, const char* name) {
+  if (!a) return std::string(name) + " is NULL";
+  if (a->n_rows != rows || a->n_cols != cols)
+    return std::string(name) + " has wrong shape";
+  if (a->nnz < 0 || !a->rowptr || (a->nnz > 0 && (!a->colidx || !a->val)))
+    return std::string(name) + " has missing arrays";
+  if (a->rowptr[0] != 0 || a->rowptr[rows] != a->nnz) return std::string(name) + " rowptr invalid";
+  for (int i = 0; i < rows; ++i) {
+    if (a->rowptr[i + 1] < a->rowptr[i]) return std::string(name) + " rowptr not monotone";
+    for (int e = a->rowptr[i]; e < a->rowptr[i + 1]; ++e) {
+      if (a->colidx[e] < 0 || a->colidx[e] >= cols) return std::string(name) + " column out of range";
+      if (e > a->rowptr[i] && a->colidx[e] <= a->colidx[e - 1])
+        return std::string(name) + " columns not sorted/unique";
+      if (!std::isfinite(a->val[e])) return std::string(name) + " has a non-finite value";
+    }
+  }
+  return "";
+}
+
+// poll device status and CUDA errors after a sequence of launches
+ers_status sync_status(ers_ctx* c) {
+  CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  unsigned st = c->h_status[0];
+  if (st & ST_TIMEOUT) return fail(c, ERS_ERR_TIMEOUT, "device wait timed out");
+  if (st & ST_SINGULAR) return fail(c, ERS_ERR_SINGULAR, "zero or non-finite pivot in LU of G_k");
+  if (st & ST_NONFINITE) return fail(c, ERS_ERR_NONFINITE, "non-finite value in a Krylov vector");
+  if (st & ST_KRYLOV) return fail(c, ERS_ERR_KRYLOV, "exp(h H_m^-1) not finite");
+  return ERS_OK;
+}
+
+ers_status clear_status(ers_ctx* c) {
+  CU(cudaMemsetAsync(c->d_status, 0, 8 * sizeof(unsigned), c->stream));
+  return ERS_OK;
+}
+
+VecGroup make_group(ers_ctx* c, int nb, const int* slots, const double* const* src) {
+  VecGroup g{};
+  g.nb = nb;
+  for (int b = 0; b < nb; ++b) {
+    g.slot[b] = slots[b];
+    g.V[b] = c->V + (size_t)slots[b] * (MAX_M + 1) * c->n;
+    g.H[b] = c->H + (size_t)slots[b] * (MAX_M + 1) * MAX_M;
+    g.src[b] = src ? src[b] : nullptr;
+  }
+  return g;
+}
+
+// Refactor: device evaluation at x, stamp G_k, numeric LU, F_k (Alg. 2, lines "Derive
+// C_k, G_k, F_k" and "LU_decompose(G_k)").
+ers_status do_refactor(ers_ctx* c) {
+  CU(cudaMemcpyAsync(c->xk, c->x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->ndev) {
+    launch_dev_eval(c, c->xk, c->dev_I, 1);
+    launch_stamp(c);
+    launch_node_F(c, 0, nullptr, nullptr, c->F);
+  } else {
+    CU(cudaMemsetAsync(c->F, 0, sizeof(double) * c->n, c->stream));
+  }
+  CU(launch_refactor(c));
+  c->factored = true;
+  c->stats.refactors++;
+  return ERS_OK;
+}
+
+// Build invert-Krylov bases for the vectors of group g (Algorithm 1 up to the MEVP) and
+// leave y = exp(h H_m^-1) e_1 in the Krylov states.  mfixed > 0: fixed dimension.
+ers_status build_bases(ers_ctx* c, VecGroup g, double h, int mfixed) {
+  const int adaptive = mfixed == 0;
+  const int mc = adaptive ? c->opts.m_max : mfixed;
+  CU(launch_arnoldi_init(c, g, adaptive));
+  VecGroup act = g;
+  for (int j = 0; j < mc; ++j) {
+    if (adaptive && j > 0) {
+      // host reads which spaces are still running
+      for (int b = 0; b < g.nb; ++b)
+        CU(cudaMemcpyAsync(c->h_scalars + b, &c->ks[g.slot[b]].done, sizeof(int),
+                           cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      act.nb = 0;
+      for (int b = 0; b < g.nb; ++b) {
+        int done;
+        std::memcpy(&done, c->h_scalars + b, sizeof(int));
+        if (!done) {
+          act.slot[act.nb] = g.slot[b];
+          act.V[act.nb] = g.V[b];
+          act.H[act.nb] = g.H[b];
+          act.nb++;
+        }
+      }
+      if (act.nb == 0) break;
+    }
+    RhsArgs R{};
+    R.n = c->n;
+    R.nv = act.nb;
+    for (int b = 0; b < act.nb; ++b) R.x[b] = act.V[b] + (size_t)j * c->n;
+    R.y = c->solve_buf;
+    k_rhs_C<<<nblk(c->n), 256, 0, c->stream>>>(R, c->C_ptr, c->C_idx, c->C_val);
+    c->stats.kernel_launches++;
+    CU(launch_solve(c, c->solve_buf, act.nb));
+    for (int b = 0; b < act.nb; ++b) act.src[b] = c->solve_buf + (size_t)b * c->n;
+    CU(launch_mgs(c, act, j, adaptive));
+    c->stats.krylov_vectors += act.nb;
+    if (adaptive) CU(launch_small(c, SMALL_RESID, act, h, mc));
+  }
+  if (!adaptive) CU(launch_small(c, SMALL_FIXED_END, g, h, mc));
+  return ERS_OK;
+}
+
+// exp(h H_m^-1) e_1 again for bases that already exist (rejected step: same m, new h)
+ers_status rescale_bases(ers_ctx* c, const VecGroup& g, double h) {
+  CU(launch_small(c, SMALL_FINAL, g, h, c->opts.m_max));
+  return ERS_OK;
+}
+
+struct StepWork {
+  int nsol = 0;           // number of solution bases (1 or 2)
+  bool has_w1 = false;
+  VecGroup sol{};
+};
+
+// Setup vectors of Eq. 12-13 at (t, x_k) for a step of h, and the solution bases.
+ers_status step_setup(ers_ctx* c, double t, double h, int mfixed, StepWork& W) {
+  k_pwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, t, h, c->u,
+                                             c->slope);
+  // host needs to know whether the slope vanishes (v2 and w1 skipped)
+  std::vector<double> hs(c->p);
+  CU(cudaMemcpyAsync(hs.data(), c->slope, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream));
+  // v1 = x_k - G^-1 (F_k + B u(t_k))
+  k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F, c->rhs);
+  c->stats.kernel_launches++;
+  CU(cudaStreamSynchronize(c->stream));
+  bool ramp = false;
+  for (double s : hs) ramp = ramp || s != 0.0;
+  if (ramp) {
+    // two right-hand sides in one pass: F + B u and B s
+    CU(cudaMemcpyAsync(c->solve_buf, c->rhs, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->slope, nullptr,
+                                             c->solve_buf + c->n);
+    CU(launch_solve(c, c->solve_buf, 2));
+    k_axpby<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->v1, 1.0, c->x, -1.0, c->solve_buf, 0.0, nullptr);
+    c->stats.kernel_launches++;
+    CU(cudaMemcpyAsync(c->w1, c->solve_buf + c->n, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    // v2 = G^-1 C w1
+    launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->w1, c->solve_buf, 1.0);
+    CU(launch_solve(c, c->solve_buf, 1));
+    CU(cudaMemcpyAsync(c->v2, c->solve_buf, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CU(cudaMemcpyAsync(c->solve_buf, c->rhs, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    CU(launch_solve(c, c->solve_buf, 1));
+    k_axpby<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->v1, 1.0, c->x, -1.0, c->solve_buf, 0.0, nullptr);
+    c->stats.kernel_launches++;
+  }
+  W.has_w1 = ramp;
+  int slots[2] = {0, 1};
+  const double* src[2] = {c->v1, c->v2};
+  if (ramp && c->opts.combined_vector) {
+    k_axpby<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->v1, 1.0, c->v1, 1.0, c->v2, 0.0, nullptr);
+    c->stats.kernel_launches++;
+    W.nsol = 1;
+  } else {
+    W.nsol = ramp ? 2 : 1;
+  }
+  W.sol = make_group(c, W.nsol, slots, src);
+  return build_bases(c, W.sol, h, mfixed);
+}
+
+// x_new = x_k + sum_b beta_b V_b (y_b - e_1) + h w1   (Eq. 13)
+ers_status step_update(ers_ctx* c, const StepWork& W, double h) {
+  double cb[2] = {1.0, 1.0};
+  CU(launch_combine(c, c->xnew, c->x, 1.0, &W.sol, cb, W.has_w1 ? c->w1 : nullptr, h, nullptr,
+                    0.0, nullptr));
+  return ERS_OK;
+}
+
+// e_rr = -(e^{hJ} - I) G^-1 dF (Eq. 15/19); ER-C correction (Eq. 20) when enabled.
+ers_status step_error(ers_ctx* c, double h, int mfixed, double* err_inf) {
+  *err_inf = 0.0;
+  if (!c->ndev) return ERS_OK;
+  launch_dev_eval(c, c->xnew, c->dev_I + c->ndev, 0);
+  launch_node_F(c, 1, c->dev_I + c->ndev, c->xnew, c->solve_buf);
+  CU(launch_solve(c, c->solve_buf, 1));
+  CU(cudaMemcpyAsync(c->ve, c->solve_buf, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  int slot = 2;
+  const double* src[1] = {c->ve};
+  VecGroup ge = make_group(c, 1, &slot, src);
+  ers_status st = build_bases(c, ge, h, mfixed);
+  if (st != ERS_OK) return st;
+  unsigned long long* mx = (unsigned long long*)(c->red + 2 * MAX_RHS * 4096 + 64);
+  CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
+  double cb[1] = {-1.0};
+  CU(launch_combine(c, c->tmp, nullptr, 0.0, &ge, cb, nullptr, 0.0, nullptr, 0.0, mx));
+  if (c->opts.correction) {
+    // z = G^-1 C v_e; D = (gamma/h) [(e^{hJ} - I) z + h v_e]; x_new -= D
+    launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->ve, c->solve_buf, 1.0);
+    CU(launch_solve(c, c->solve_buf, 1));
+    int zs = 1;
+    const double* zsrc[1] = {c->solve_buf};
+    VecGroup gz = make_group(c, 1, &zs, zsrc);
+    st = build_bases(c, gz, h, mfixed);
+    if (st != ERS_OK) return st;
+    double cz[1] = {-c->opts.gamma / h};
+    CU(launch_combine(c, c->xnew, c->xnew, 1.0, &gz, cz, c->ve, -c->opts.gamma, nullptr, 0.0, nullptr));
+  }
+  unsigned long long bits;
+  CU(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  double e;
+  std::memcpy(&e, &bits, sizeof(e));
+  *err_inf = e;
+  return ERS_OK;
+}
+
+double next_breakpoint(const ers_ctx* c, double t) {
+  auto it = std::upper_bound(c->bp.begin(), c->bp.end(), t * (1 + 1e-14) + 1e-30);
+  return it == c->bp.end() ? INFINITY : *it;
+}
+
+ers_status read_m(ers_ctx* c, int slot, int* m) {
+  CU(cudaMemcpyAsync(c->h_scalars, &c->ks[slot].m, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  std::memcpy(m, c->h_scalars, sizeof(int));
+  return ERS_OK;
+}
+
+double host_absmax(ers_ctx* c, const double* x, ers_status* st) {
+  unsigned long long* mx = (unsigned long long*)(c->red + 2 * MAX_RHS * 4096 + 72);
+  cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream);
+  launch_absmax(c, x, mx);
+  unsigned long long bits = 0;
+  cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) *st = fail(c, ERS_ERR_CUDA, cudaGetErrorString(e));
+  double v;
+  std::memcpy(&v, &bits, sizeof(v));
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+ers_status ers_default_opts(ers_opts* o) {
+  if (!o) return ERS_ERR_INVALID;
+  std::memset(o, 0, sizeof(*o));
+  o->eps_krylov = 1e-7;
+  o->E_rr = 0.0;
+  o->alpha = 0.5;
+  o->beta = 2.0;
+  o->gamma = 0.1;
+  o->h_min = 1e-20;
+  o->h_max = 0.0;
+  o->h_init = 0.0;
+  o->vdd = 1.0;
+  o->i_grow = 5;
+  o->m_min = 3;
+  o->m_max = 40;
+  o->combined_vector = 0;
+  o->correction = 0;
+  return ERS_OK;
+}
+
+const char* ers_last_error(const ers_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+static ers_status build_union(ers_ctx* c, const ers_csr* G, const ers_mosfet* dev, int ndev,
+                              std::vector<int32_t>& uptr, std::vector<int32_t>& uidx,
+                              std::vector<double>& uval) {
+  int n = G->n_rows;
+  std::vector<std::vector<int32_t>> extra(n);
+  for (int d = 0; d < ndev; ++d) {
+    int term[3] = {dev[d].d, dev[d].g, dev[d].s};
+    for (int t = 0; t < 3; ++t)
+      if (term[t] < -2 || term[t] >= n) return fail(c, ERS_ERR_INVALID, "device terminal out of range");
+    if (dev[d].type != 0 && dev[d].type != 1) return fail(c, ERS_ERR_INVALID, "device type must be 0 or 1");
+    for (int node : {dev[d].d, dev[d].s}) {
+      if (node < 0) continue;
+      for (int t = 0; t < 3; ++t)
+        if (term[t] >= 0) extra[node].push_back(term[t]);
+    }
+  }
+  uptr.assign(n + 1, 0);
+  uidx.clear();
+  uval.clear();
+  for (int i = 0; i < n; ++i) {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int e = G->rowptr[i]; e < G->rowptr[i + 1]; ++e) row.push_back({G->colidx[e], G->val[e]});
+    row.push_back({i, 0.0});  // the diagonal is always part of the pattern
+    for (int j : extra[i]) row.push_back({j, 0.0});
+    std::sort(row.begin(), row.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    int last = -1;
+    for (auto& pr : row) {
+      if (pr.first == last) { uval.back() += pr.second; continue; }
+      uidx.push_back(pr.first);
+      uval.push_back(pr.second);
+      last = pr.first;
+    }
+    uptr[i + 1] = (int32_t)uidx.size();
+  }
+  return ERS_OK;
+}
+
+ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const ers_csr* B,
+                      const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
+                      const ers_opts* opts) {
+  if (!out) return ERS_ERR_INVALID;
+  *out = nullptr;
+  ers_ctx* c = new ers_ctx();
+  auto bail = [&](ers_status st) { *out = c; return st; };
+  if (!G) return bail(fail(c, ERS_ERR_INVALID, "G_lin is NULL"));
+  int n = G->n_rows;
+  if (n <= 0) return bail(fail(c, ERS_ERR_INVALID, "n must be positive"));
+  std::string m;
+  if (!(m = check_csr(G, n, n, "G_lin")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
+  if (!(m = check_csr(C, n, n, "C")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
+  if (p < 0) return bail(fail(c, ERS_ERR_INVALID, "p must be >= 0"));
+  if (!(m = check_csr(B, n, p, "B")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
+  if (ndev < 0 || (ndev > 0 && !dev)) return bail(fail(c, ERS_ERR_INVALID, "bad device list"));
+  if (p > 0 && !u) return bail(fail(c, ERS_ERR_INVALID, "u is NULL"));
+  for (int q = 0; q < p; ++q) {
+    if (u[q].npts < 1 || !u[q].t || !u[q].v) return bail(fail(c, ERS_ERR_INVALID, "empty PWL table"));
+    for (int k = 0; k < u[q].npts; ++k) {
+      if (!std::isfinite(u[q].t[k]) || !std::isfinite(u[q].v[k]))
+        return bail(fail(c, ERS_ERR_NONFINITE, "non-finite PWL value"));
+      if (k > 0 && !(u[q].t[k] > u[q].t[k - 1]))
+        return bail(fail(c, ERS_ERR_INVALID, "PWL times must increase"));
+    }
+  }
+  for (int d = 0; d < ndev; ++d)
+    if (!std::isfinite(dev[d].vt) || !std::isfinite(dev[d].k) || !std::isfinite(dev[d].lambda))
+      return bail(fail(c, ERS_ERR_NONFINITE, "non-finite device parameter"));
+  if (opts) c->opts = *opts; else ers_default_opts(&c->opts);
+  if (c->opts.m_max < 1 || c->opts.m_max > MAX_M)
+    return bail(fail(c, ERS_ERR_INVALID, "m_max must be in 1..64"));
+  if (c->opts.m_min < 1) c->opts.m_min = 1;
+  c->n = n;
+  c->p = p;
+  c->ndev = ndev;
+  c->linear = ndev == 0;
+
+  // union pattern of G_k and its symbolic analysis
+  std::vector<int32_t> uptr, uidx;
+  std::vector<double> uval;
+  ers_status st = build_union(c, G, dev, ndev, uptr, uidx, uval);
+  if (st != ERS_OK) return bail(st);
+  SymbolicOptions so;
+  std::string err = analyze(n, uptr.data(), uidx.data(), so, c->sym);
+  if (!err.empty()) return bail(fail(c, ERS_ERR_INVALID, "symbolic analysis: " + err));
+  const Symbolic& S = c->sym;
+
+  cudaError_t ce = cudaGetDevice(&c->device);
+  if (ce != cudaSuccess) return bail(fail(c, ERS_ERR_CUDA, cudaGetErrorString(ce)));
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, c->device);
+  c->sm_count = prop.multiProcessorCount;
+#define CUB(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bail(fail(c, e_ == cudaErrorMemoryAllocation ? ERS_ERR_OOM : ERS_ERR_CUDA,  \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)));             \
+  } while (0)
+  CUB(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  c->own_stream = true;
+  CUB(factor_kernel_attributes());
+  CUB(krylov_init_constants());
+  c->coop_blocks = coop_max_blocks(c->sm_count);
+
+  // G values in the permuted slot order, stamp gather lists
+  int nnzG = S.a_ptr[n];
+  c->nnzG = nnzG;
+  std::vector<double> glin(nnzG);
+  std::vector<int32_t> old2new(nnzG);
+  for (int e = 0; e < nnzG; ++e) {
+    glin[e] = uval[S.a_src[e]];
+    old2new[S.a_src[e]] = e;
+  }
+  auto find_slot = [&](int row, int col) -> int {  // old indices -> new slot
+    auto b = uidx.begin() + uptr[row], en = uidx.begin() + uptr[row + 1];
+    auto it = std::lower_bound(b, en, col);
+    return old2new[(int)(it - uidx.begin())];
+  };
+  std::vector<std::vector<int32_t>> slot_ent(nnzG), node_ent(n);
+  for (int d = 0; d < ndev; ++d) {
+    int term[3] = {dev[d].d, dev[d].g, dev[d].s};
+    for (int side = 0; side < 2; ++side) {
+      int node = side == 0 ? dev[d].d : dev[d].s;
+      if (node < 0) continue;
+      node_ent[S.iperm[node]].push_back(d * 2 + side);
+      for (int t = 0; t < 3; ++t)
+        if (term[t] >= 0) slot_ent[find_slot(node, term[t])].push_back(d * 8 + t * 2 + side);
+    }
+  }
+  std::vector<int32_t> sptr(nnzG + 1, 0), sent, nptr(n + 1, 0), nent;
+  for (int e = 0; e < nnzG; ++e) {
+    sent.insert(sent.end(), slot_ent[e].begin(), slot_ent[e].end());
+    sptr[e + 1] = (int32_t)sent.size();
+  }
+  for (int i = 0; i < n; ++i) {
+    nent.insert(nent.end(), node_ent[i].begin(), node_ent[i].end());
+    nptr[i + 1] = (int32_t)nent.size();
+  }
+  // C and B permuted
+  auto permute_csr = [&](const ers_csr* A, bool perm_cols, std::vector<int32_t>& pp,
+                         std::vector<int32_t>& pi, std::vector<double>& pv) {
+    pp.assign(n + 1, 0);
+    pi.clear(); pv.clear();
+    std::vector<std::pair<int32_t, double>> row;
+    for (int k = 0; k < n; ++k) {
+      int i = S.perm[k];
+      row.clear();
+      for (int e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e)
+        row.push_back({perm_cols ? S.iperm[A->colidx[e]] : A->colidx[e], A->val[e]});
+      std::sort(row.begin(), row.end(), [](auto& a, auto& b) { return a.first < b.first; });
+      for (auto& pr : row) { pi.push_back(pr.first); pv.push_back(pr.second); }
+      pp[k + 1] = (int32_t)pi.size();
+    }
+  };
+  std::vector<int32_t> cp, ci, bp_, bi;
+  std::vector<double> cv, bv;
+  permute_csr(C, true, cp, ci, cv);
+  permute_csr(B, false, bp_, bi, bv);
+  c->nnzC = (int)ci.size();
+  c->nnzB = (int)bi.size();
+  // PWL tables and breakpoints
+  std::vector<int32_t> pptr(p + 1, 0);
+  std::vector<double> pt, pv;
+  for (int q = 0; q < p; ++q) {
+    for (int k = 0; k < u[q].npts; ++k) {
+      pt.push_back(u[q].t[k]);
+      pv.push_back(u[q].v[k]);
+      c->bp.push_back(u[q].t[k]);
+    }
+    pptr[q + 1] = (int32_t)pt.size();
+  }
+  std::sort(c->bp.begin(), c->bp.end());
+  c->bp.erase(std::unique(c->bp.begin(), c->bp.end()), c->bp.end());
+  // devices
+  std::vector<int32_t> dtype(ndev), dterm(3 * std::max(ndev, 0));
+  std::vector<double> dpar(3 * std::max(ndev, 0));
+  for (int d = 0; d < ndev; ++d) {
+    dtype[d] = dev[d].type;
+    int term[3] = {dev[d].d, dev[d].g, dev[d].s};
+    for (int t = 0; t < 3; ++t) dterm[3 * d + t] = term[t] >= 0 ? S.iperm[term[t]] : term[t];
+    dpar[3 * d] = dev[d].vt;
+    dpar[3 * d + 1] = dev[d].k;
+    dpar[3 * d + 2] = dev[d].lambda;
+  }
+
+  // ---- device uploads ----
+  CUB(upload(&c->d_perm, S.perm));
+  CUB(upload(&c->G_ptr, S.a_ptr));
+  CUB(upload(&c->G_idx, S.a_idx));
+  CUB(upload(&c->Glin_val, glin));
+  CUB(upload(&c->G_val, glin));
+  CUB(upload(&c->stamp_ptr, sptr));
+  CUB(upload(&c->stamp_ent, sent));
+  CUB(upload(&c->node_ptr, nptr));
+  CUB(upload(&c->node_ent, nent));
+  CUB(upload(&c->C_ptr, cp));
+  CUB(upload(&c->C_idx, ci));
+  CUB(upload(&c->C_val, cv));
+  CUB(upload(&c->B_ptr, bp_));
+  CUB(upload(&c->B_idx, bi));
+  CUB(upload(&c->B_val, bv));
+  CUB(upload(&c->pwl_ptr, pptr));
+  CUB(upload(&c->pwl_t, pt));
+  CUB(upload(&c->pwl_v, pv));
+  CUB(dalloc(&c->u, p));
+  CUB(dalloc(&c->slope, p));
+  CUB(upload(&c->dev_type, dtype));
+  CUB(upload(&c->dev_term, dterm));
+  CUB(upload(&c->dev_par, dpar));
+  CUB(dalloc(&c->dev_I, 2 * (size_t)std::max(ndev, 1)));
+  CUB(dalloc(&c->dev_J, 3 * (size_t)std::max(ndev, 1)));
+  for (double** v : {&c->x, &c->xk, &c->xnew, &c->F, &c->rhs, &c->v1, &c->w1, &c->v2, &c->ve, &c->tmp})
+    CUB(dalloc(v, n));
+  CUB(dalloc(&c->solve_buf, (size_t)MAX_RHS * n));
+  CUB(dalloc(&c->V, (size_t)3 * (MAX_M + 1) * n));
+  CUB(dalloc(&c->H, (size_t)3 * (MAX_M + 1) * MAX_M));
+  CUB(dalloc(&c->ks, 3));
+  CUB(dalloc(&c->red, (size_t)2 * MAX_RHS * 4096 + 256));
+  CUB(dalloc(&c->d_status, 16));
+  CUB(cudaMallocHost((void**)&c->h_status, 16 * sizeof(unsigned)));
+  CUB(cudaMallocHost((void**)&c->h_scalars, 64 * sizeof(double)));
+  // plan
+  DevicePlan& P = c->plan;
+  P.n = n;
+  P.nsn = S.nsn;
+  P.nlevels = S.nlevels;
+  CUB(upload(&P.sn_start, S.sn_start));
+  CUB(upload(&P.sn_parent, S.sn_parent));
+  CUB(upload(&P.rows, S.rows));
+  CUB(upload(&P.rel, S.rel));
+  CUB(upload(&P.rptr, S.rptr));
+  CUB(upload(&P.d_off, S.d_off));
+  CUB(upload(&P.o_off, S.o_off));
+  CUB(upload(&P.front_off, S.front_off));
+  CUB(upload(&P.lvl_sn, S.lvl_sn));
+  CUB(upload(&P.lvl_slot, S.lvl_slot));
+  CUB(upload(&P.ea_child, S.ea_child));
+  CUB(upload(&P.asm_dst, S.asm_dst));
+  CUB(upload(&P.tile_sn, S.tile_sn));
+  CUB(upload(&P.tile_ij, S.tile_ij));
+  CUB(upload(&P.ptask_sn, S.ptask_sn));
+  CUB(upload(&P.ptask_r0, S.ptask_r0));
+  CUB(upload(&P.fwd, S.fwd));
+  CUB(upload(&P.bwd, S.bwd));
+  CUB(upload(&P.fwd_tgt, S.fwd_tgt));
+  CUB(upload(&P.fwd_expect, S.fwd_expect));
+  CUB(upload(&P.bwd_nchunk, S.bwd_nchunk));
+  P.nfwd = (int)S.fwd.size();
+  P.nbwd = (int)S.bwd.size();
+  CUB(dalloc(&P.LDi, S.d_total));
+  CUB(dalloc(&P.UDi, S.d_total));
+  CUB(dalloc(&P.Lo, S.o_total));
+  CUB(dalloc(&P.Uo, S.o_total));
+  CUB(dalloc(&P.arena, S.arena_size));
+  CUB(dalloc(&P.sync, 2 + 3 * (size_t)S.nsn));
+  CUB(cudaDeviceSynchronize());
+#undef CUB
+  c->t = 0.0;
+  c->h = 0.0;
+  c->factored = false;
+  c->stats.n = n;
+  c->stats.nsn = S.nsn;
+  c->stats.nlevels = S.nlevels;
+  c->stats.etree_height = S.etree_height;
+  c->stats.max_front = S.max_front;
+  c->stats.nnz_L = S.nnz_L;
+  c->stats.factor_doubles = 2 * (S.d_total + S.o_total);
+  c->stats.arena_doubles = S.arena_size;
+  c->stats.refactor_flops = S.flops;
+  {
+    double diag = 0.0, off = 0.0, rows = 0.0;
+    for (int s2 = 0; s2 < S.nsn; ++s2) {
+      double w = S.sn_start[s2 + 1] - S.sn_start[s2];
+      double r = (double)(S.rptr[s2 + 1] - S.rptr[s2]);
+      diag += w * (w + 1.0);
+      off += 2.0 * r * w;
+      rows += r;
+    }
+    c->stats.solve_fma_per_rhs = diag + off;
+    c->stats.solve_bytes_per_pass = 8.0 * (diag + off) + 8.0 * rows + 4.0 * 2.0 * S.nsn;
+  }
+  *out = c;
+  return ERS_OK;
+}
+
+ers_status ers_set_stream(ers_ctx* c, void* stream) {
+  if (!c) return ERS_ERR_INVALID;
+  if (stream) c->stream = (cudaStream_t)stream;
+  else {
+    if (!c->own_stream) {
+      CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+  }
+  return ERS_OK;
+}
+
+ers_status ers_refactor(ers_ctx* c) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  st = do_refactor(c);
+  if (st != ERS_OK) return st;
+  return sync_status(c);
+}
+
+ers_status ers_dc(ers_ctx* c, const double* x0) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (x0) {
+    for (int i = 0; i < c->n; ++i)
+      if (!std::isfinite(x0[i])) return fail(c, ERS_ERR_NONFINITE, "non-finite initial guess");
+    std::vector<double> xp(c->n);
+    for (int k = 0; k < c->n; ++k) xp[k] = x0[c->sym.perm[k]];
+    CU(cudaMemcpyAsync(c->x, xp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  } else {
+    CU(cudaMemsetAsync(c->x, 0, sizeof(double) * c->n, c->stream));
+  }
+  k_pwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, 0.0, 0.0, c->u,
+                                             nullptr);
+  k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, nullptr, c->tmp);
+  c->stats.kernel_launches++;
+  for (int it = 0; it < 50; ++it) {
+    st = do_refactor(c);
+    if (st != ERS_OK) return st;
+    k_dc_res<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->G_ptr, c->G_idx, c->G_val, c->x, c->F,
+                                                 c->tmp, c->rhs);
+    double res = host_absmax(c, c->rhs, &st);
+    if (st != ERS_OK) return st;
+    if (res <= 1e-12) break;
+    k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F,
+                                             c->solve_buf);
+    CU(launch_solve(c, c->solve_buf, 1));
+    k_newton<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->x, c->solve_buf, 0.5);
+    c->stats.kernel_launches++;
+    if (c->linear) {
+      c->factored = true;
+      break;
+    }
+    c->factored = false;
+  }
+  if (!c->linear) c->factored = false;
+  c->t = 0.0;
+  return sync_status(c);
+}
+
+static ers_status step_core(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* err_inf) {
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(c, ERS_ERR_INVALID, "h must be positive");
+  if (m < 0 || m > MAX_M) return fail(c, ERS_ERR_INVALID, "m must be in 0..64");
+  double nb = next_breakpoint(c, c->t);
+  if (c->t + h > nb * (1 + 1e-12) + 1e-30)
+    return fail(c, ERS_ERR_INVALID, "step crosses a PWL corner");
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (!c->factored) {
+    st = do_refactor(c);
+    if (st != ERS_OK) return st;
+  }
+  StepWork W;
+  st = step_setup(c, c->t, h, m, W);
+  if (st != ERS_OK) return st;
+  st = step_update(c, W, h);
+  if (st != ERS_OK) return st;
+  double err = 0.0;
+  st = step_error(c, h, m, &err);
+  if (st != ERS_OK) return st;
+  st = sync_status(c);
+  if (st != ERS_OK) return st;
+  if (m_used) {
+    st = read_m(c, 0, m_used);
+    if (st != ERS_OK) return st;
+  }
+  if (err_inf) *err_inf = err;
+  return ERS_OK;
+}
+
+ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* err_inf) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_status st = step_core(c, h, m, m_used, err_inf);
+  if (st != ERS_OK) return st;
+  CU(cudaMemcpyAsync(c->x, c->xnew, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  c->t += h;
+  if (!c->linear) c->factored = false;
+  c->stats.steps++;
+  CU(cudaStreamSynchronize(c->stream));
+  return ERS_OK;
+}
+
+ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int32_t* nsteps,
+                   int32_t* nreject) {
+  if (!c) return ERS_ERR_INVALID;
+  if (!(t_end > c->t)) return fail(c, ERS_ERR_INVALID, "t_end must exceed the current time");
+  if (!(tol > 0.0)) return fail(c, ERS_ERR_INVALID, "tol must be positive");
+  const ers_opts& o = c->opts;
+  double h_max = o.h_max > 0 ? o.h_max : t_end / 100.0;
+  double h_prop = c->h > 0 ? c->h : (o.h_init > 0 ? o.h_init : h_max);
+  int steps = 0, rejects = 0;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  while (c->t < t_end * (1 - 1e-12) && (max_steps <= 0 || steps < max_steps)) {
+    double nb = std::min(next_breakpoint(c, c->t), t_end);
+    double h = std::min(std::min(h_prop, h_max), nb - c->t);
+    double E_rr = o.E_rr;
+    if (!(E_rr > 0)) {
+      double xm = host_absmax(c, c->x, &st);
+      if (st != ERS_OK) return st;
+      E_rr = tol * std::max(1.0, xm);
+    }
+    if (!c->factored) {
+      st = do_refactor(c);
+      if (st != ERS_OK) return st;
+    }
+    StepWork W;
+    st = step_setup(c, c->t, h, 0, W);
+    if (st != ERS_OK) return st;
+    int i = 0;
+    bool first = true;
+    while (true) {
+      if (!first) {
+        st = rescale_bases(c, W.sol, h);
+        if (st != ERS_OK) return st;
+      }
+      first = false;
+      st = step_update(c, W, h);
+      if (st != ERS_OK) return st;
+      double err = 0.0;
+      st = step_error(c, h, 0, &err);
+      if (st != ERS_OK) return st;
+      st = sync_status(c);
+      if (st != ERS_OK) return st;
+      if (err <= E_rr) break;
+      ++i;
+      ++rejects;
+      h *= o.alpha;
+      if (h < o.h_min) return fail(c, ERS_ERR_STEP_UNDERFLOW, "step size underflow");
+    }
+    bool landed = h == nb - c->t;
+    c->t = landed ? nb : c->t + h;
+    CU(cudaMemcpyAsync(c->x, c->xnew, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    if (!c->linear) c->factored = false;
+    ++steps;
+    c->stats.steps++;
+    h_prop = i < o.i_grow ? std::min(o.beta * h, h_max) : h;
+    c->h = h_prop;
+  }
+  c->stats.rejects += rejects;
+  if (nsteps) *nsteps = steps;
+  if (nreject) *nreject = rejects;
+  CU(cudaStreamSynchronize(c->stream));
+  return ERS_OK;
+}
+
+ers_status ers_get_state(const ers_ctx* cc, double* t, double* x, double* h) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c) return ERS_ERR_INVALID;
+  if (t) *t = c->t;
+  if (h) *h = c->h;
+  if (x) {
+    std::vector<double> xp(c->n);
+    CU(cudaMemcpyAsync(xp.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < c->n; ++k) x[c->sym.perm[k]] = xp[k];
+  }
+  return ERS_OK;
+}
+
+ers_status ers_set_state(ers_ctx* c, double t, const double* x, double h) {
+  if (!c || !x) return ERS_ERR_INVALID;
+  if (!std::isfinite(t) || !std::isfinite(h)) return fail(c, ERS_ERR_NONFINITE, "non-finite t or h");
+  std::vector<double> xp(c->n);
+  for (int k = 0; k < c->n; ++k) {
+    xp[k] = x[c->sym.perm[k]];
+    if (!std::isfinite(xp[k])) return fail(c, ERS_ERR_NONFINITE, "non-finite state");
+  }
+  CU(cudaMemcpyAsync(c->x, xp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->t = t;
+  c->h = h;
+  if (!c->linear) c->factored = false;
+  return ERS_OK;
+}
+
+ers_status ers_get_state_dev(const ers_ctx* cc, double* x_dev) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c || !x_dev) return ERS_ERR_INVALID;
+  // scatter back to the original order on the device
+  k_permute<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->d_perm, c->x, x_dev, 1);
+  c->stats.kernel_launches++;
+  CU(cudaGetLastError());
+  return ERS_OK;
+}
+
+ers_status ers_set_state_dev(ers_ctx* c, double t, const double* x_dev, double h) {
+  if (!c || !x_dev) return ERS_ERR_INVALID;
+  k_permute<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->d_perm, x_dev, c->x, 0);
+  c->stats.kernel_launches++;
+  CU(cudaGetLastError());
+  c->t = t;
+  c->h = h;
+  if (!c->linear) c->factored = false;
+  return ERS_OK;
+}
+
+static ers_status to_dev_perm(ers_ctx* c, const double* host, double* dev) {
+  std::vector<double> xp(c->n);
+  for (int k = 0; k < c->n; ++k) xp[k] = host[c->sym.perm[k]];
+  CU(cudaMemcpyAsync(dev, xp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return ERS_OK;
+}
+static ers_status from_dev_perm(ers_ctx* c, const double* dev, double* host) {
+  std::vector<double> xp(c->n);
+  CU(cudaMemcpyAsync(xp.data(), dev, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < c->n; ++k) host[c->sym.perm[k]] = xp[k];
+  return ERS_OK;
+}
+
+ers_status ers_solve(ers_ctx* c, const double* b, double* x) {
+  if (!c || !b || !x) return ERS_ERR_INVALID;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (!c->factored) {
+    st = do_refactor(c);
+    if (st != ERS_OK) return st;
+  }
+  st = to_dev_perm(c, b, c->solve_buf);
+  if (st != ERS_OK) return st;
+  CU(launch_solve(c, c->solve_buf, 1));
+  st = sync_status(c);
+  if (st != ERS_OK) return st;
+  return from_dev_perm(c, c->solve_buf, x);
+}
+
+ers_status ers_spmv_C(ers_ctx* c, const double* v, double* y) {
+  if (!c || !v || !y) return ERS_ERR_INVALID;
+  ers_status st = to_dev_perm(c, v, c->tmp);
+  if (st != ERS_OK) return st;
+  launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->tmp, c->rhs, 1.0);
+  CU(cudaGetLastError());
+  return from_dev_perm(c, c->rhs, y);
+}
+
+ers_status ers_mevp(ers_ctx* c, const double* v, double h, int32_t m, double* out, int32_t* m_used) {
+  if (!c || !v || !out) return ERS_ERR_INVALID;
+  if (!(h > 0.0)) return fail(c, ERS_ERR_INVALID, "h must be positive");
+  if (m < 0 || m > MAX_M) return fail(c, ERS_ERR_INVALID, "m must be in 0..64");
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (!c->factored) {
+    st = do_refactor(c);
+    if (st != ERS_OK) return st;
+  }
+  st = to_dev_perm(c, v, c->ve);
+  if (st != ERS_OK) return st;
+  int slot = 2;
+  const double* src[1] = {c->ve};
+  VecGroup g = make_group(c, 1, &slot, src);
+  st = build_bases(c, g, h, m);
+  if (st != ERS_OK) return st;
+  // out = beta V y = v + beta V (y - e_1)
+  double cb[1] = {1.0};
+  CU(launch_combine(c, c->tmp, c->ve, 1.0, &g, cb, nullptr, 0.0, nullptr, 0.0, nullptr));
+  st = sync_status(c);
+  if (st != ERS_OK) return st;
+  if (m_used) {
+    st = read_m(c, 2, m_used);
+    if (st != ERS_OK) return st;
+  }
+  return from_dev_perm(c, c->tmp, out);
+}
+
+ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, double h, double* y,
+                         double* last) {
+  if (!c || !H || !y || !last) return ERS_ERR_INVALID;
+  if (m < 1 || m > MAX_M || ldh < m) return fail(c, ERS_ERR_INVALID, "bad m / ldh");
+  double *dH = nullptr, *dy = nullptr;
+  CU(cudaMalloc((void**)&dH, sizeof(double) * (size_t)ldh * m));
+  CU(cudaMalloc((void**)&dy, sizeof(double) * (m + 1)));
+  CU(cudaMemcpyAsync(dH, H, sizeof(double) * (size_t)ldh * m, cudaMemcpyHostToDevice, c->stream));
+  CU(launch_small_test(c, dH, ldh, m, h, dy, dy + m));
+  std::vector<double> hy(m + 1);
+  CU(cudaMemcpyAsync(hy.data(), dy, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  cudaFree(dH);
+  cudaFree(dy);
+  for (int k = 0; k < m; ++k) y[k] = hy[k];
+  *last = hy[m];
+  return ERS_OK;
+}
+
+ers_status ers_stats(const ers_ctx* cc, ers_stats_t* out) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c || !out) return ERS_ERR_INVALID;
+  CU(cudaStreamSynchronize(c->stream));
+  for (auto& ev : c->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) c->stats.solve_ms += ms;
+    c->ev_free.push_back(ev);
+  }
+  c->ev_used.clear();
+  *out = c->stats;
+  return ERS_OK;
+}
+
+ers_status ers_profile(ers_ctx* c, int32_t enable) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_stats_t tmp;
+  ers_status st = ers_stats(c, &tmp);
+  if (st != ERS_OK) return st;
+  c->profile = enable != 0;
+  c->stats.solve_ms = 0.0;
+  return ERS_OK;
+}
+
+ers_status ers_analyze(const ers_csr* pat, ers_stats_t* out, int32_t* perm) {
+  if (!pat || !out) return ERS_ERR_INVALID;
+  if (pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
+  Symbolic S;
+  SymbolicOptions so;
+  std::string err = analyze(pat->n_rows, pat->rowptr, pat->colidx, so, S);
+  if (!err.empty()) return ERS_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  out->n = S.n;
+  out->nsn = S.nsn;
+  out->nlevels = S.nlevels;
+  out->etree_height = S.etree_height;
+  out->max_front = S.max_front;
+  out->nnz_L = S.nnz_L;
+  out->factor_doubles = 2 * (S.d_total + S.o_total);
+  out->arena_doubles = S.arena_size;
+  out->refactor_flops = S.flops;
+  if (perm) std::memcpy(perm, S.perm.data(), sizeof(int32_t) * S.n);
+  return ERS_OK;
+}
+
+void ers_destroy(ers_ctx* c) {
+  if (!c) return;
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  DevicePlan& P = c->plan;
+  for (void* p : {(void*)P.sn_start, (void*)P.sn_parent, (void*)P.rows, (void*)P.rel, (void*)P.rptr,
+                  (void*)P.d_off, (void*)P.o_off, (void*)P.front_off, (void*)P.lvl_sn,
+                  (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.asm_dst, (void*)P.tile_sn,
+                  (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd,
+                  (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.LDi,
+                  (void*)P.UDi, (void*)P.Lo, (void*)P.Uo, (void*)P.arena, (void*)P.sync})
+    f(p);
+  for (void* p : {(void*)c->G_ptr, (void*)c->G_idx, (void*)c->Glin_val, (void*)c->G_val,
+                  (void*)c->C_ptr, (void*)c->C_idx, (void*)c->C_val, (void*)c->B_ptr,
+                  (void*)c->B_idx, (void*)c->B_val, (void*)c->pwl_ptr, (void*)c->pwl_t,
+                  (void*)c->pwl_v, (void*)c->u, (void*)c->slope, (void*)c->dev_type,
+                  (void*)c->dev_term, (void*)c->dev_par, (void*)c->dev_I, (void*)c->dev_J,
+                  (void*)c->stamp_ptr, (void*)c->stamp_ent, (void*)c->node_ptr, (void*)c->node_ent,
+                  (void*)c->x, (void*)c->xk, (void*)c->xnew, (void*)c->F, (void*)c->rhs,
+                  (void*)c->v1, (void*)c->w1, (void*)c->v2, (void*)c->ve, (void*)c->tmp,
+                  (void*)c->solve_buf, (void*)c->V, (void*)c->H, (void*)c->ks, (void*)c->red,
+                  (void*)c->d_status, (void*)c->d_perm})
+    f(p);
+  for (auto& ev : c->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal data layout shared by the CUDA translation units of libers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ers.h"
+#include "symbolic.h"
+
+namespace ers {
+
+// device status bits (OR-ed into ctx->d_status[0])
+enum : unsigned {
+  ST_SINGULAR = 1u,     // zero or tiny pivot in the refactor
+  ST_NONFINITE = 2u,    // NaN/Inf met in a vector or a small dense result
+  ST_TIMEOUT = 4u,      // a bounded spin-wait gave up
+  ST_KRYLOV = 8u,       // exp(h H^-1) not finite
+};
+
+constexpr int MAX_M = 64;        // largest Krylov dimension supported
+constexpr int MAX_RHS = 3;       // right-hand sides solved in one pass over the factors
+constexpr int SPIN_LIMIT = 1 << 22;
+
+// Per-basis device-side Arnoldi state (one per Krylov space).
+struct KrylovState {
+  double beta;          // ||v||
+  double gv1;           // ||G v_1|| (scale of the relative residual test)
+  double w0;            // ||w|| before orthogonalisation (current iteration)
+  double gvnext[MAX_M + 1];
+  double y[MAX_M];      // exp(h H_m^-1) e_1 of the chosen dimension
+  double last;          // e_m^T H_m^-1 exp(h H_m^-1) e_1
+  double res;           // last residual ratio
+  double best_res;
+  int built;            // Arnoldi iterations done
+  int m;                // dimension chosen for the MEVP (0 = zero vector)
+  int best_m;
+  int done;             // 1 = converged / breakdown / zero vector: no further iterations
+  int breakdown;
+  int pad[3];
+};
+
+// A set of Krylov spaces advanced in lockstep (their solves share one pass over the factors).
+struct VecGroup {
+  int nb;
+  int slot[MAX_RHS];
+  double* V[MAX_RHS];            // basis columns (stride n)
+  double* H[MAX_RHS];            // (MAX_M+1) x MAX_M column-major
+  const double* src[MAX_RHS];    // init: v ; mgs: solve output x (w = -x)
+};
+
+// modes of the small dense kernel
+enum : int { SMALL_RESID = 0, SMALL_FINAL = 1, SMALL_FIXED_END = 2, SMALL_TEST = 3 };
+
+// Factor and solve plan resident on the device.
+struct DevicePlan {
+  int n = 0, nsn = 0, nlevels = 0;
+  int32_t *sn_start = nullptr, *sn_parent = nullptr, *rows = nullptr, *rel = nullptr;
+  int64_t *rptr = nullptr, *d_off = nullptr, *o_off = nullptr, *front_off = nullptr;
+  int32_t *lvl_sn = nullptr, *lvl_slot = nullptr, *ea_child = nullptr;
+  int64_t* asm_dst = nullptr;
+  int32_t *tile_sn = nullptr, *tile_ij = nullptr, *ptask_sn = nullptr, *ptask_r0 = nullptr;
+  SolveTask *fwd = nullptr, *bwd = nullptr;
+  int32_t *fwd_tgt = nullptr, *fwd_expect = nullptr, *bwd_nchunk = nullptr;
+  int nfwd = 0, nbwd = 0;
+  // factor values
+  double *LDi = nullptr, *UDi = nullptr, *Lo = nullptr, *Uo = nullptr;
+  double* arena = nullptr;
+  // solve sync words: [0] task counter, then per-supernode counters/flags
+  int32_t* sync = nullptr;   // 2 + 3*nsn ints
+};
+
+}  // namespace ers
+
+// the opaque context of the public C ABI
+struct ers_ctx {
+  std::string err;
+  ers_opts opts{};
+  int n = 0, p = 0, ndev = 0;
+  ers::Symbolic sym;
+  ers::DevicePlan plan;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int sm_count = 0;
+  // host copies (permuted) needed by the driver
+  std::vector<double> bp;              // sorted unique PWL corner times
+  // device arrays (permuted node order)
+  int32_t* d_perm = nullptr;                    // new -> old node index
+  int32_t *G_ptr = nullptr, *G_idx = nullptr;   // union pattern of G_k
+  double *Glin_val = nullptr, *G_val = nullptr; // linear values, current G_k values
+  int32_t *C_ptr = nullptr, *C_idx = nullptr; double* C_val = nullptr;
+  int32_t *B_ptr = nullptr, *B_idx = nullptr; double* B_val = nullptr;  // n x p
+  int nnzG = 0, nnzC = 0, nnzB = 0;
+  bool C_diag = false;
+  double* Cdiag = nullptr;
+  // PWL tables
+  int32_t* pwl_ptr = nullptr; double *pwl_t = nullptr, *pwl_v = nullptr;
+  double* u = nullptr;        // p
+  double* slope = nullptr;    // p
+  // devices (terminals already permuted; <0 = rail)
+  int32_t* dev_type = nullptr; int32_t* dev_term = nullptr;  // 3 per device: d,g,s
+  double* dev_par = nullptr;  // 3 per device: vt,k,lambda
+  double* dev_I = nullptr;    // current at x_k
+  double* dev_J = nullptr;    // 3 partials at x_k
+  int32_t* stamp_ptr = nullptr; int32_t* stamp_ent = nullptr;  // per G slot: device contributions
+  int32_t* node_ptr = nullptr; int32_t* node_ent = nullptr;    // per node: device incidences
+  // vectors
+  double *x = nullptr, *xk = nullptr, *xnew = nullptr, *F = nullptr, *rhs = nullptr;
+  double *v1 = nullptr, *w1 = nullptr, *v2 = nullptr, *ve = nullptr, *tmp = nullptr;
+  double* solve_buf = nullptr;       // MAX_RHS * n
+  double* V = nullptr;               // 3 bases, each (MAX_M+1) * n
+  double* H = nullptr;               // 3 * (MAX_M+1) * MAX_M
+  ers::KrylovState* ks = nullptr;    // 3
+  double* red = nullptr;             // reduction scratch
+  unsigned* d_status = nullptr;      // [0] status bits, [1..] barrier words
+  unsigned* h_status = nullptr;      // pinned mirror
+  double* h_scalars = nullptr;       // pinned scalars for host decisions
+  int coop_blocks = 0;
+  // state
+  double t = 0.0, h = 0.0;
+  bool factored = false;             // LU of G_k valid for the current x
+  bool linear = true;
+  ers_stats_t stats{};
+  // profiling of the solve kernels (CUDA events on the context's stream)
+  bool profile = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;
+};

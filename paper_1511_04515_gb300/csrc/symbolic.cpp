@@ -1,0 +1,699 @@
+// Symbolic analysis of the fixed pattern of G_k (host, once per circuit).
+//
+// The paper factors G_k once per time step and never C or C/h + G (Alg. 2, Sec. IV-A);
+// the pattern of G_k = G_lin + G_dev(x_k) is fixed by the netlist, so everything that
+// depends only on the pattern is computed here:
+//   1. fill-reducing ordering: nested dissection with level-structure vertex separators
+//      (George's method) on the symmetrised pattern, exact minimum degree on small parts;
+//   2. elimination tree (Liu), postorder, column counts by row subtrees;
+//   3. fundamental supernodes (width-capped) and their row structures;
+//   4. the multifrontal refactor plan (front arena, assembly/extend-add maps, tiles);
+//   5. the task lists of the warp-granular sync-free triangular solves.
+#include "symbolic.h"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+namespace ers {
+namespace {
+
+struct Graph {  // symmetric adjacency without the diagonal
+  int n = 0;
+  std::vector<int64_t> xadj;
+  std::vector<int32_t> adj;
+};
+
+Graph symmetrize(int n, const int32_t* ptr, const int32_t* idx) {
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int i = 0; i < n; ++i)
+    for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int j = idx[e];
+      if (j == i) continue;
+      cnt[i + 1]++;
+      cnt[j + 1]++;
+    }
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int32_t> tmp(cnt[n]);
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  for (int i = 0; i < n; ++i)
+    for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+      int j = idx[e];
+      if (j == i) continue;
+      tmp[pos[i]++] = j;
+      tmp[pos[j]++] = i;
+    }
+  Graph g;
+  g.n = n;
+  g.xadj.assign(n + 1, 0);
+  g.adj.reserve(tmp.size());
+  for (int i = 0; i < n; ++i) {
+    std::sort(tmp.begin() + cnt[i], tmp.begin() + cnt[i + 1]);
+    int last = -1;
+    for (int64_t e = cnt[i]; e < cnt[i + 1]; ++e)
+      if (tmp[e] != last) { g.adj.push_back(tmp[e]); last = tmp[e]; }
+    g.xadj[i + 1] = (int64_t)g.adj.size();
+  }
+  return g;
+}
+
+// ---- nested dissection --------------------------------------------------------------
+class Dissector {
+ public:
+  Dissector(const Graph& g, int leaf) : g_(g), leaf_(leaf), mark_(g.n, -1), lev_(g.n, -1),
+                                         loc_(g.n, -1) {}
+
+  // returns new -> old
+  std::vector<int32_t> run() {
+    int n = g_.n;
+    buf_.resize(n);
+    std::iota(buf_.begin(), buf_.end(), 0);
+    std::vector<std::pair<int, int>> stack;
+    if (n) stack.push_back({0, n});
+    while (!stack.empty()) {
+      auto [lo, hi] = stack.back();
+      stack.pop_back();
+      split(lo, hi, stack);
+    }
+    return buf_;
+  }
+
+ private:
+  const Graph& g_;
+  int leaf_;
+  std::vector<int32_t> buf_, mark_, lev_, loc_;
+  int stamp_ = 0;
+  std::vector<int32_t> queue_, tmp_;
+
+  void stamp_range(int lo, int hi) {
+    ++stamp_;
+    for (int k = lo; k < hi; ++k) mark_[buf_[k]] = stamp_;
+  }
+
+  // BFS inside the stamped part; fills lev_ and returns (#levels, last vertex visited)
+  int bfs(int root, int& far) {
+    queue_.clear();
+    queue_.push_back(root);
+    lev_[root] = 0;
+    mark_[root] = -stamp_;  // visited marker: negative stamp
+    size_t h = 0;
+    int maxl = 0;
+    while (h < queue_.size()) {
+      int v = queue_[h++];
+      for (int64_t e = g_.xadj[v]; e < g_.xadj[v + 1]; ++e) {
+        int u = g_.adj[e];
+        if (mark_[u] == stamp_) {
+          mark_[u] = -stamp_;
+          lev_[u] = lev_[v] + 1;
+          maxl = std::max(maxl, lev_[u]);
+          queue_.push_back(u);
+        }
+      }
+    }
+    far = queue_.back();
+    return maxl + 1;
+  }
+
+  void unvisit() {
+    for (int v : queue_) mark_[v] = stamp_;
+  }
+
+  int degree_in_part(int v) {
+    int d = 0;
+    for (int64_t e = g_.xadj[v]; e < g_.xadj[v + 1]; ++e) {
+      int u = g_.adj[e];
+      if (mark_[u] == stamp_ || mark_[u] == -stamp_) ++d;
+    }
+    return d;
+  }
+
+  void min_degree(int lo, int hi) {
+    // exact minimum degree on the induced subgraph (<= 64 vertices) with bit masks
+    int m = hi - lo;
+    uint64_t adjm[64];
+    for (int a = 0; a < m; ++a) loc_[buf_[lo + a]] = a;
+    for (int a = 0; a < m; ++a) {
+      int v = buf_[lo + a];
+      uint64_t mk = 0;
+      for (int64_t e = g_.xadj[v]; e < g_.xadj[v + 1]; ++e) {
+        int u = g_.adj[e];
+        if (mark_[u] == stamp_) mk |= (uint64_t)1 << loc_[u];
+      }
+      adjm[a] = mk;
+    }
+    uint64_t alive = (m == 64) ? ~(uint64_t)0 : (((uint64_t)1 << m) - 1);
+    tmp_.assign(m, 0);
+    for (int step = 0; step < m; ++step) {
+      int best = -1, bd = 1 << 30;
+      for (int a = 0; a < m; ++a)
+        if (alive >> a & 1) {
+          int d = __builtin_popcountll(adjm[a] & alive);
+          if (d < bd) { bd = d; best = a; }
+        }
+      uint64_t nb = adjm[best] & alive & ~((uint64_t)1 << best);
+      for (int a = 0; a < m; ++a)
+        if (nb >> a & 1) adjm[a] |= nb & ~((uint64_t)1 << a);
+      alive &= ~((uint64_t)1 << best);
+      tmp_[step] = buf_[lo + best];
+    }
+    for (int a = 0; a < m; ++a) {
+      buf_[lo + a] = tmp_[a];
+      loc_[tmp_[a]] = -1;
+    }
+  }
+
+  void by_degree(int lo, int hi) {
+    // fallback for parts of diameter < 3: low degree first, high degree last
+    std::vector<std::pair<int, int>> dv;
+    for (int k = lo; k < hi; ++k) dv.push_back({degree_in_part(buf_[k]), buf_[k]});
+    std::sort(dv.begin(), dv.end());
+    for (int k = lo; k < hi; ++k) buf_[k] = dv[k - lo].second;
+  }
+
+  void split(int lo, int hi, std::vector<std::pair<int, int>>& stack) {
+    int size = hi - lo;
+    stamp_range(lo, hi);
+    if (size <= leaf_ && size <= 64) {
+      min_degree(lo, hi);
+      return;
+    }
+    // connected components
+    int far;
+    bfs(buf_[lo], far);
+    if ((int)queue_.size() < size) {
+      // label all components, regroup the range component by component
+      std::vector<int32_t> comp_vertices;
+      comp_vertices.reserve(size);
+      std::vector<int> bounds{0};
+      for (int v : queue_) comp_vertices.push_back(v);
+      bounds.push_back((int)comp_vertices.size());
+      for (int k = lo; k < hi; ++k) {
+        int v = buf_[k];
+        if (mark_[v] == stamp_) {
+          bfs(v, far);
+          for (int u : queue_) comp_vertices.push_back(u);
+          bounds.push_back((int)comp_vertices.size());
+        }
+      }
+      std::copy(comp_vertices.begin(), comp_vertices.end(), buf_.begin() + lo);
+      for (size_t c = 0; c + 1 < bounds.size(); ++c)
+        stack.push_back({lo + bounds[c], lo + bounds[c + 1]});
+      return;
+    }
+    // pseudo-peripheral root
+    int root = buf_[lo];
+    unvisit();
+    int nlev = bfs(root, far);
+    for (int it = 0; it < 5; ++it) {
+      // candidate: minimum-degree vertex of the last level
+      int cand = far, cd = 1 << 30;
+      for (int v : queue_)
+        if (lev_[v] == nlev - 1) {
+          int d = degree_in_part(v);
+          if (d < cd) { cd = d; cand = v; }
+        }
+      unvisit();
+      int f2;
+      int nl2 = bfs(cand, f2);
+      if (nl2 <= nlev) {
+        unvisit();
+        nlev = bfs(root, far);
+        break;
+      }
+      root = cand;
+      nlev = nl2;
+      far = f2;
+    }
+    if (nlev < 3) {
+      unvisit();
+      if (size <= 64) min_degree(lo, hi); else by_degree(lo, hi);
+      return;
+    }
+    // separator level: where the cumulative count crosses half
+    std::vector<int> cnt(nlev, 0);
+    for (int v : queue_) cnt[lev_[v]]++;
+    int k = 1, acc = cnt[0];
+    while (k < nlev - 1 && acc + cnt[k] <= size / 2) { acc += cnt[k]; ++k; }
+    if (k >= nlev - 1) k = nlev - 2;
+    // classify: 0 = A (lev < k), 1 = B (lev > k), 2 = S
+    tmp_.clear();
+    std::vector<int32_t> A, B, S;
+    for (int v : queue_) {
+      int l = lev_[v];
+      if (l < k) A.push_back(v);
+      else if (l > k) B.push_back(v);
+      else S.push_back(v);
+    }
+    // refine: separator vertices with no neighbour in B move to A
+    std::vector<int32_t> S2;
+    for (int v : S) {
+      bool touchB = false;
+      for (int64_t e = g_.xadj[v]; e < g_.xadj[v + 1]; ++e) {
+        int u = g_.adj[e];
+        if ((mark_[u] == -stamp_) && lev_[u] == k + 1) { touchB = true; break; }
+      }
+      if (touchB) S2.push_back(v); else A.push_back(v);
+    }
+    unvisit();
+    int p = lo;
+    for (int v : A) buf_[p++] = v;
+    for (int v : B) buf_[p++] = v;
+    for (int v : S2) buf_[p++] = v;
+    if (!A.empty()) stack.push_back({lo, lo + (int)A.size()});
+    if (!B.empty()) stack.push_back({lo + (int)A.size(), lo + (int)(A.size() + B.size())});
+  }
+};
+
+}  // namespace
+
+std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const SymbolicOptions& opt,
+                    Symbolic& S) {
+  if (n <= 0) return "empty matrix";
+  for (int i = 0; i < n; ++i) {
+    if (ptr[i + 1] < ptr[i]) return "row pointer not monotone";
+    bool diag = false;
+    for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+      if (idx[e] < 0 || idx[e] >= n) return "column index out of range";
+      if (e > ptr[i] && idx[e] <= idx[e - 1]) return "columns not sorted/unique";
+      if (idx[e] == i) diag = true;
+    }
+    if (!diag) return "missing diagonal entry in row " + std::to_string(i);
+  }
+  S = Symbolic();
+  S.n = n;
+  Graph g = symmetrize(n, ptr, idx);
+
+  // 1. ordering
+  Dissector nd(g, std::min(opt.leaf_size, 64));
+  std::vector<int32_t> perm = nd.run();
+  std::vector<int32_t> iperm(n);
+  for (int k = 0; k < n; ++k) iperm[perm[k]] = k;
+
+  // permuted symmetric adjacency (for etree and counts)
+  auto permuted_adj = [&](const std::vector<int32_t>& iper, std::vector<int64_t>& px,
+                          std::vector<int32_t>& pa) {
+    px.assign(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      int v = perm[k];
+      px[k + 1] = px[k] + (g.xadj[v + 1] - g.xadj[v]);
+    }
+    pa.resize(px[n]);
+    for (int k = 0; k < n; ++k) {
+      int v = perm[k];
+      int64_t o = px[k];
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) pa[o++] = iper[g.adj[e]];
+      std::sort(pa.begin() + px[k], pa.begin() + px[k + 1]);
+    }
+  };
+  std::vector<int64_t> px;
+  std::vector<int32_t> pa;
+  permuted_adj(iperm, px, pa);
+
+  // 2. elimination tree (Liu), then postorder and re-permute
+  auto etree = [&](std::vector<int32_t>& par) {
+    par.assign(n, -1);
+    std::vector<int32_t> anc(n, -1);
+    for (int j = 0; j < n; ++j)
+      for (int64_t e = px[j]; e < px[j + 1]; ++e) {
+        int i = pa[e];
+        if (i >= j) break;
+        int r = i;
+        while (anc[r] != -1 && anc[r] != j) {
+          int t = anc[r];
+          anc[r] = j;
+          r = t;
+        }
+        if (anc[r] == -1) { anc[r] = j; par[r] = j; }
+      }
+  };
+  std::vector<int32_t> par;
+  etree(par);
+  {
+    // postorder (children in increasing order)
+    std::vector<int32_t> head(n, -1), next(n, -1), post;
+    post.reserve(n);
+    for (int j = n - 1; j >= 0; --j)
+      if (par[j] >= 0) { next[j] = head[par[j]]; head[par[j]] = j; }
+    std::vector<int32_t> st;
+    for (int r = 0; r < n; ++r) {
+      if (par[r] != -1) continue;
+      st.push_back(r);
+      while (!st.empty()) {
+        int v = st.back();
+        if (head[v] != -1) {
+          int c = head[v];
+          head[v] = next[c];
+          st.push_back(c);
+        } else {
+          st.pop_back();
+          post.push_back(v);
+        }
+      }
+    }
+    std::vector<int32_t> perm2(n);
+    for (int k = 0; k < n; ++k) perm2[k] = perm[post[k]];
+    perm = perm2;
+    for (int k = 0; k < n; ++k) iperm[perm[k]] = k;
+    permuted_adj(iperm, px, pa);
+    etree(par);
+  }
+  S.perm = perm;
+  S.iperm = iperm;
+  S.parent = par;
+
+  // permuted A pattern (not symmetrised) with the source slot of each entry
+  {
+    S.a_ptr.assign(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      int v = perm[k];
+      S.a_ptr[k + 1] = S.a_ptr[k] + (ptr[v + 1] - ptr[v]);
+    }
+    S.a_idx.resize(S.a_ptr[n]);
+    S.a_src.resize(S.a_ptr[n]);
+    std::vector<std::pair<int32_t, int32_t>> rowbuf;
+    for (int k = 0; k < n; ++k) {
+      int v = perm[k];
+      rowbuf.clear();
+      for (int32_t e = ptr[v]; e < ptr[v + 1]; ++e) rowbuf.push_back({iperm[idx[e]], e});
+      std::sort(rowbuf.begin(), rowbuf.end());
+      int32_t o = S.a_ptr[k];
+      for (auto& pr : rowbuf) { S.a_idx[o] = pr.first; S.a_src[o] = pr.second; ++o; }
+    }
+  }
+
+  // column counts by row subtrees (counts include the diagonal)
+  std::vector<int64_t> cc(n, 1);
+  {
+    std::vector<int32_t> mk(n, -1);
+    for (int i = 0; i < n; ++i) {
+      mk[i] = i;
+      for (int64_t e = px[i]; e < px[i + 1]; ++e) {
+        int j = pa[e];
+        if (j >= i) break;
+        while (mk[j] != i) { mk[j] = i; cc[j]++; j = par[j]; }
+      }
+    }
+  }
+  S.colcount = cc;
+  S.nnz_L = 0;
+  for (int j = 0; j < n; ++j) S.nnz_L += cc[j];
+  {
+    std::vector<int32_t> depth(n, 0);
+    int h = 0;
+    for (int j = n - 1; j >= 0; --j) {
+      depth[j] = par[j] >= 0 ? depth[par[j]] + 1 : 1;
+      h = std::max(h, depth[j]);
+    }
+    S.etree_height = h;
+  }
+
+  // 3. fundamental supernodes (width-capped)
+  std::vector<int32_t> nchild(n, 0);
+  for (int j = 0; j < n; ++j)
+    if (par[j] >= 0) nchild[par[j]]++;
+  S.sn_start.clear();
+  S.sn_start.push_back(0);
+  for (int j = 1; j < n; ++j) {
+    bool merge = par[j - 1] == j && cc[j - 1] == cc[j] + 1 && nchild[j] == 1 &&
+                 (j - S.sn_start.back()) < opt.max_width;
+    if (!merge) S.sn_start.push_back(j);
+  }
+  S.sn_start.push_back(n);
+  S.nsn = (int)S.sn_start.size() - 1;
+  int nsn = S.nsn;
+  S.sn_of.assign(n, 0);
+  for (int s = 0; s < nsn; ++s)
+    for (int j = S.sn_start[s]; j < S.sn_start[s + 1]; ++j) S.sn_of[j] = s;
+
+  // row structures: pattern rows of the supernode's columns plus children's structures
+  S.rptr.assign(nsn + 1, 0);
+  S.rows.clear();
+  S.sn_parent.assign(nsn, -1);
+  std::vector<std::vector<int32_t>> children(nsn);
+  {
+    std::vector<int32_t> mk(n, -1), lst;
+    for (int s = 0; s < nsn; ++s) {
+      int c0 = S.sn_start[s], c1 = S.sn_start[s + 1];
+      lst.clear();
+      for (int j = c0; j < c1; ++j)
+        for (int64_t e = px[j]; e < px[j + 1]; ++e) {
+          int i = pa[e];
+          if (i >= c1 && mk[i] != s) { mk[i] = s; lst.push_back(i); }
+        }
+      for (int c : children[s])
+        for (int64_t e = S.rptr[c]; e < S.rptr[c + 1]; ++e) {
+          int i = S.rows[e];
+          if (i >= c1 && mk[i] != s) { mk[i] = s; lst.push_back(i); }
+        }
+      std::sort(lst.begin(), lst.end());
+      if ((int64_t)lst.size() + (c1 - c0) != cc[c0])
+        return "internal: supernode structure does not match column count";
+      S.rows.insert(S.rows.end(), lst.begin(), lst.end());
+      S.rptr[s + 1] = (int64_t)S.rows.size();
+      if (!lst.empty()) {
+        int p = S.sn_of[lst[0]];
+        S.sn_parent[s] = p;
+        children[p].push_back(s);
+      }
+    }
+  }
+
+  // levels (leaves 0) and storage
+  S.level.assign(nsn, 0);
+  for (int s = 0; s < nsn; ++s)
+    if (S.sn_parent[s] >= 0) S.level[S.sn_parent[s]] = std::max(S.level[S.sn_parent[s]], S.level[s] + 1);
+  S.nlevels = 0;
+  for (int s = 0; s < nsn; ++s) S.nlevels = std::max(S.nlevels, S.level[s] + 1);
+  S.d_off.assign(nsn, 0);
+  S.o_off.assign(nsn, 0);
+  S.d_total = S.o_total = 0;
+  S.flops = 0.0;
+  S.max_front = 0;
+  for (int s = 0; s < nsn; ++s) {
+    int64_t w = S.sn_start[s + 1] - S.sn_start[s];
+    int64_t r = S.rptr[s + 1] - S.rptr[s];
+    S.d_off[s] = S.d_total;
+    S.d_total += w * w;
+    S.o_off[s] = S.o_total;
+    S.o_total += r * w;
+    S.max_front = std::max<int>(S.max_front, (int)(w + r));
+    double wd = (double)w, rd = (double)r;
+    S.flops += 2.0 / 3.0 * wd * wd * wd + 2.0 * wd * wd * rd + 2.0 * wd * rd * rd;
+  }
+
+  // 4. multifrontal plan ------------------------------------------------------------
+  // relative indices of each child's rows in the parent's front
+  S.rel.assign(S.rows.size(), 0);
+  for (int s = 0; s < nsn; ++s) {
+    int p = S.sn_parent[s];
+    if (p < 0) continue;
+    int pc0 = S.sn_start[p], pw = S.sn_start[p + 1] - pc0;
+    const int32_t* prow = S.rows.data() + S.rptr[p];
+    int64_t pr = S.rptr[p + 1] - S.rptr[p];
+    for (int64_t e = S.rptr[s]; e < S.rptr[s + 1]; ++e) {
+      int i = S.rows[e];
+      int pos;
+      if (i < pc0 + pw) pos = i - pc0;
+      else {
+        const int32_t* it = std::lower_bound(prow, prow + pr, i);
+        if (it == prow + pr || *it != i) return "internal: child row missing from parent";
+        pos = pw + (int)(it - prow);
+      }
+      S.rel[e] = pos;
+    }
+  }
+  // supernodes by level
+  S.lvl_sn_ptr.assign(S.nlevels + 1, 0);
+  for (int s = 0; s < nsn; ++s) S.lvl_sn_ptr[S.level[s] + 1]++;
+  for (int l = 0; l < S.nlevels; ++l) S.lvl_sn_ptr[l + 1] += S.lvl_sn_ptr[l];
+  S.lvl_sn.resize(nsn);
+  {
+    std::vector<int32_t> pos(S.lvl_sn_ptr.begin(), S.lvl_sn_ptr.end() - 1);
+    for (int s = 0; s < nsn; ++s) S.lvl_sn[pos[S.level[s]]++] = s;
+  }
+  // arena: first-fit allocator simulated level by level
+  {
+    struct Block { int64_t off, len; };
+    std::vector<Block> freel;  // sorted by offset
+    int64_t top = 0;
+    auto alloc = [&](int64_t len) -> int64_t {
+      len = (len + 31) & ~(int64_t)31;
+      for (size_t b = 0; b < freel.size(); ++b)
+        if (freel[b].len >= len) {
+          int64_t o = freel[b].off;
+          freel[b].off += len;
+          freel[b].len -= len;
+          if (freel[b].len == 0) freel.erase(freel.begin() + b);
+          return o;
+        }
+      int64_t o = top;
+      top += len;
+      return o;
+    };
+    auto release = [&](int64_t off, int64_t len) {
+      len = (len + 31) & ~(int64_t)31;
+      Block nb{off, len};
+      auto it = std::lower_bound(freel.begin(), freel.end(), nb,
+                                 [](const Block& a, const Block& b) { return a.off < b.off; });
+      it = freel.insert(it, nb);
+      size_t k = it - freel.begin();
+      if (k + 1 < freel.size() && freel[k].off + freel[k].len == freel[k + 1].off) {
+        freel[k].len += freel[k + 1].len;
+        freel.erase(freel.begin() + k + 1);
+      }
+      if (k > 0 && freel[k - 1].off + freel[k - 1].len == freel[k].off) {
+        freel[k - 1].len += freel[k].len;
+        freel.erase(freel.begin() + k);
+      }
+      if (!freel.empty() && freel.back().off + freel.back().len == top) {
+        top = freel.back().off;
+        freel.pop_back();
+      }
+    };
+    S.front_off.assign(nsn, 0);
+    int64_t peak = 0;
+    for (int l = 0; l < S.nlevels; ++l) {
+      for (int k = S.lvl_sn_ptr[l]; k < S.lvl_sn_ptr[l + 1]; ++k) {
+        int s = S.lvl_sn[k];
+        int64_t f = (S.sn_start[s + 1] - S.sn_start[s]) + (S.rptr[s + 1] - S.rptr[s]);
+        S.front_off[s] = alloc(f * f);
+        peak = std::max(peak, top);
+      }
+      for (int k = S.lvl_sn_ptr[l]; k < S.lvl_sn_ptr[l + 1]; ++k) {
+        int s = S.lvl_sn[k];
+        for (int c : children[s]) {
+          int64_t f = (S.sn_start[c + 1] - S.sn_start[c]) + (S.rptr[c + 1] - S.rptr[c]);
+          release(S.front_off[c], f * f);
+        }
+        if (S.sn_parent[s] < 0) {
+          int64_t f = (S.sn_start[s + 1] - S.sn_start[s]) + (S.rptr[s + 1] - S.rptr[s]);
+          release(S.front_off[s], f * f);
+        }
+      }
+    }
+    S.arena_size = std::max<int64_t>(peak, 32);
+  }
+  // assembly map of A's entries into fronts
+  {
+    int64_t nnzA = S.a_ptr[n];
+    S.asm_dst.assign(nnzA, 0);
+    std::vector<int32_t> slot_level(nnzA);
+    for (int i = 0; i < n; ++i)
+      for (int32_t e = S.a_ptr[i]; e < S.a_ptr[i + 1]; ++e) {
+        int j = S.a_idx[e];
+        int lo = std::min(i, j), hi = std::max(i, j);
+        int s = S.sn_of[lo];
+        int c0 = S.sn_start[s], w = S.sn_start[s + 1] - c0;
+        int64_t f = w + (S.rptr[s + 1] - S.rptr[s]);
+        auto pos = [&](int x) -> int64_t {
+          if (x < c0 + w) return x - c0;
+          const int32_t* b = S.rows.data() + S.rptr[s];
+          const int32_t* en = S.rows.data() + S.rptr[s + 1];
+          const int32_t* it = std::lower_bound(b, en, x);
+          return w + (it - b);
+        };
+        (void)hi;
+        S.asm_dst[e] = S.front_off[s] + pos(i) + pos(j) * f;
+        slot_level[e] = S.level[s];
+      }
+    S.lvl_slot_ptr.assign(S.nlevels + 1, 0);
+    for (int64_t e = 0; e < nnzA; ++e) S.lvl_slot_ptr[slot_level[e] + 1]++;
+    for (int l = 0; l < S.nlevels; ++l) S.lvl_slot_ptr[l + 1] += S.lvl_slot_ptr[l];
+    S.lvl_slot.resize(nnzA);
+    std::vector<int32_t> pos(S.lvl_slot_ptr.begin(), S.lvl_slot_ptr.end() - 1);
+    for (int64_t e = 0; e < nnzA; ++e) S.lvl_slot[pos[slot_level[e]]++] = (int32_t)e;
+  }
+  // extend-add pairs grouped by (parent level, child rank)
+  {
+    int maxrank = 1;
+    for (int s = 0; s < nsn; ++s) maxrank = std::max<int>(maxrank, (int)children[s].size());
+    S.ea_maxrank = maxrank;
+    std::vector<std::vector<int32_t>> groups((size_t)S.nlevels * maxrank);
+    for (int s = 0; s < nsn; ++s)
+      for (size_t r = 0; r < children[s].size(); ++r)
+        groups[(size_t)S.level[s] * maxrank + r].push_back(children[s][r]);
+    S.ea_ptr.assign(groups.size() + 1, 0);
+    S.ea_child.clear();
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      S.ea_child.insert(S.ea_child.end(), groups[gi].begin(), groups[gi].end());
+      S.ea_ptr[gi + 1] = (int32_t)S.ea_child.size();
+    }
+  }
+  // Schur-update tiles (64 x 64) and panel tasks (128 rows) per level
+  {
+    const int TB = 64, PB = 128;
+    S.tile_ptr.assign(S.nlevels + 1, 0);
+    S.ptask_ptr.assign(S.nlevels + 1, 0);
+    S.tile_sn.clear(); S.tile_ij.clear(); S.ptask_sn.clear(); S.ptask_r0.clear();
+    for (int l = 0; l < S.nlevels; ++l) {
+      for (int k = S.lvl_sn_ptr[l]; k < S.lvl_sn_ptr[l + 1]; ++k) {
+        int s = S.lvl_sn[k];
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        int nt = (r + TB - 1) / TB;
+        for (int ti = 0; ti < nt; ++ti)
+          for (int tj = 0; tj < nt; ++tj) {
+            S.tile_sn.push_back(s);
+            S.tile_ij.push_back((ti << 16) | tj);
+          }
+        for (int r0 = 0; r0 < r; r0 += PB) {
+          S.ptask_sn.push_back(s);
+          S.ptask_r0.push_back(r0);
+        }
+      }
+      S.tile_ptr[l + 1] = (int32_t)S.tile_sn.size();
+      S.ptask_ptr[l + 1] = (int32_t)S.ptask_sn.size();
+    }
+  }
+
+  // 5. triangular-solve task lists -------------------------------------------------
+  {
+    S.fwd.clear(); S.bwd.clear(); S.fwd_tgt.clear();
+    S.fwd_expect.assign(nsn, 0);
+    S.bwd_nchunk.assign(nsn, 0);
+    auto add_targets = [&](int s, int r0, int r1, SolveTask& t) {
+      t.tgt0 = (int32_t)S.fwd_tgt.size();
+      int last = -1;
+      for (int e = r0; e < r1; ++e) {
+        int tg = S.sn_of[S.rows[S.rptr[s] + e]];
+        if (tg != last) {
+          S.fwd_tgt.push_back(tg);
+          S.fwd_expect[tg]++;
+          last = tg;
+        }
+      }
+      t.ntgt = (int32_t)S.fwd_tgt.size() - t.tgt0;
+    };
+    for (int s = 0; s < nsn; ++s) {  // postorder: children before parents
+      int w = S.sn_start[s + 1] - S.sn_start[s];
+      int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+      if ((int64_t)r * w <= opt.fused_limit) {
+        SolveTask t{TASK_FUSED, s, 0, r, 0, 0};
+        add_targets(s, 0, r, t);
+        S.fwd.push_back(t);
+      } else {
+        S.fwd.push_back(SolveTask{TASK_DIAG, s, 0, 0, 0, 0});
+        for (int r0 = 0; r0 < r; r0 += opt.solve_chunk) {
+          SolveTask t{TASK_OFF, s, r0, std::min(r, r0 + opt.solve_chunk), 0, 0};
+          add_targets(s, t.r0, t.r1, t);
+          S.fwd.push_back(t);
+        }
+      }
+    }
+    for (int s = nsn - 1; s >= 0; --s) {  // reverse postorder: parents before children
+      int w = S.sn_start[s + 1] - S.sn_start[s];
+      int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+      if ((int64_t)r * w <= opt.fused_limit) {
+        S.bwd.push_back(SolveTask{TASK_FUSED, s, 0, r, 0, 0});
+      } else {
+        for (int r0 = 0; r0 < r; r0 += opt.solve_chunk) {
+          S.bwd.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + opt.solve_chunk), 0, 0});
+          S.bwd_nchunk[s]++;
+        }
+        S.bwd.push_back(SolveTask{TASK_DIAG, s, 0, 0, 0, 0});
+      }
+    }
+  }
+  return "";
+}
+
+}  // namespace ers

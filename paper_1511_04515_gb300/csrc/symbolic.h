@@ -1,0 +1,88 @@
+// Host-side symbolic analysis for the fixed-pattern LU of G_k (done once per circuit).
+//
+// G_k changes value every step but never pattern (the topology is fixed; Alg. 2 factors
+// G_k once per step), so ordering, elimination tree, supernodes, the multifrontal
+// refactor plan and the triangular-solve task lists are computed here once.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ers {
+
+struct SymbolicOptions {
+  int leaf_size = 64;        // nested-dissection parts at or below this size get minimum degree
+  int max_width = 64;        // supernode width cap (columns)
+  int relax_zeros = 0;       // reserved: relaxed amalgamation (0 = fundamental supernodes)
+  int solve_chunk = 256;     // rows per off-diagonal solve task of a large supernode
+  int fused_limit = 2048;    // r*w at or below which one task does a supernode's whole solve
+};
+
+// Task of the warp-granular triangular-solve kernels.
+enum TaskKind : int32_t { TASK_FUSED = 0, TASK_DIAG = 1, TASK_OFF = 2 };
+
+struct SolveTask {
+  int32_t kind;
+  int32_t sn;
+  int32_t r0, r1;       // row range inside R_off(sn) (OFF tasks; FUSED: 0..r)
+  int32_t tgt0, ntgt;   // distinct target supernodes of the rows (forward counters)
+};
+
+struct Symbolic {
+  int n = 0;
+  std::vector<int32_t> perm;    // new -> old
+  std::vector<int32_t> iperm;   // old -> new
+  // permuted pattern of A (G_lin union device stamps), CSR, new indices, rows sorted
+  std::vector<int32_t> a_ptr, a_idx;
+  std::vector<int32_t> a_src;   // slot in the caller's (old-order) union CSR for each new slot
+  // elimination tree (column level)
+  std::vector<int32_t> parent;
+  std::vector<int64_t> colcount;
+  // supernodes
+  int nsn = 0;
+  std::vector<int32_t> sn_start;   // nsn+1
+  std::vector<int32_t> sn_of;      // n
+  std::vector<int32_t> sn_parent;  // nsn
+  std::vector<int64_t> rptr;       // nsn+1 : R_off(s) = rows[rptr[s] .. rptr[s+1])
+  std::vector<int32_t> rows;       // sorted off-diagonal row structure of each supernode
+  std::vector<int32_t> rel;        // same layout: position of rows[.] inside the parent's front
+  std::vector<int32_t> level;      // multifrontal level (0 = leaves)
+  int nlevels = 0;
+  // factor storage (doubles)
+  std::vector<int64_t> d_off;      // nsn : offset of the w*w inverted diagonal blocks
+  std::vector<int64_t> o_off;      // nsn : offset of the r*w off-diagonal panels
+  int64_t d_total = 0, o_total = 0;
+  // multifrontal plan
+  std::vector<int64_t> front_off;  // nsn : offset of the f*f front in the arena (doubles)
+  int64_t arena_size = 0;
+  std::vector<int32_t> lvl_sn_ptr, lvl_sn;        // supernodes by level
+  std::vector<int64_t> asm_dst;                   // per A slot (new order): arena offset
+  std::vector<int32_t> lvl_slot_ptr, lvl_slot;    // A slots by level of their supernode
+  // extend-add: (child) pairs grouped by (level of parent, child rank)
+  std::vector<int32_t> ea_ptr;     // nlevels * maxrank + 1
+  std::vector<int32_t> ea_child;
+  int ea_maxrank = 0;
+  // GEMM tile lists per level (Schur update F22 -= F21 F12)
+  std::vector<int32_t> tile_ptr;   // nlevels+1
+  std::vector<int32_t> tile_sn;    // per tile: supernode
+  std::vector<int32_t> tile_ij;    // per tile: (ti << 16) | tj
+  // panel-row task lists per level (F21 <- F21 U11^-1, F12 <- L11^-1 F12)
+  std::vector<int32_t> ptask_ptr;  // nlevels+1
+  std::vector<int32_t> ptask_sn, ptask_r0;
+  // triangular solve tasks
+  std::vector<SolveTask> fwd, bwd;
+  std::vector<int32_t> fwd_tgt;    // target lists of forward tasks
+  std::vector<int32_t> fwd_expect; // nsn : units that scatter into each supernode
+  std::vector<int32_t> bwd_nchunk; // nsn : OFF tasks of each supernode in the backward solve
+  // statistics
+  int64_t nnz_L = 0;               // including the diagonal
+  double flops = 0.0;              // refactor flops
+  int max_front = 0;
+  int etree_height = 0;
+};
+
+// pattern: n x n CSR (old order, rows sorted, unique). Returns "" on success.
+std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const SymbolicOptions& opt,
+                    Symbolic& out);
+
+}  // namespace ers

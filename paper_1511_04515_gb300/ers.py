@@ -1,0 +1,299 @@
+"""Python binding of libers (include/ers.h): argument marshalling only.
+
+Every step of the transient runs in the library's CUDA kernels; this module converts
+numpy / scipy.sparse inputs into the C structures, passes PyTorch's CUDA stream through when
+asked, and raises ErsError on any non-OK status.  There is no CPU fallback: if libers.so is
+missing or no GPU is present, the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libers.so")
+
+STATUS = {0: "OK", 1: "INVALID", 2: "SINGULAR", 3: "NONFINITE", 4: "STEP_UNDERFLOW",
+          5: "KRYLOV", 6: "TIMEOUT", 7: "CUDA", 8: "OOM"}
+
+
+class ErsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ers status {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int32),
+                ("rowptr", C.POINTER(C.c_int32)), ("colidx", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
+class Mosfet(C.Structure):
+    _fields_ = [("type", C.c_int32), ("d", C.c_int32), ("g", C.c_int32), ("s", C.c_int32),
+                ("vt", C.c_double), ("k", C.c_double), ("lam", C.c_double)]
+
+
+class Pwl(C.Structure):
+    _fields_ = [("npts", C.c_int32), ("t", C.POINTER(C.c_double)), ("v", C.POINTER(C.c_double))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eps_krylov", C.c_double), ("E_rr", C.c_double), ("alpha", C.c_double),
+                ("beta", C.c_double), ("gamma", C.c_double), ("h_min", C.c_double),
+                ("h_max", C.c_double), ("h_init", C.c_double), ("vdd", C.c_double),
+                ("i_grow", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32),
+                ("combined_vector", C.c_int32), ("correction", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("rejects", C.c_int64), ("refactors", C.c_int64),
+                ("krylov_vectors", C.c_int64), ("solves", C.c_int64),
+                ("n", C.c_int32), ("nsn", C.c_int32), ("nlevels", C.c_int32),
+                ("etree_height", C.c_int32), ("max_front", C.c_int32),
+                ("nnz_L", C.c_int64), ("factor_doubles", C.c_int64),
+                ("arena_doubles", C.c_int64), ("refactor_flops", C.c_double),
+                ("kernel_launches", C.c_int64), ("solve_passes", C.c_int64),
+                ("solve_rhs", C.c_int64), ("solve_ms", C.c_double),
+                ("solve_bytes_per_pass", C.c_double), ("solve_fma_per_rhs", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_refactor",
+           "ers_step", "ers_run", "ers_get_state", "ers_set_state", "ers_get_state_dev",
+           "ers_set_state_dev", "ers_solve", "ers_spmv_C", "ers_mevp", "ers_phi_small",
+           "ers_stats", "ers_profile", "ers_analyze", "ers_last_error", "ers_destroy"]
+
+_lib = None
+
+
+def lib():
+    """Load libers.so (built by paper_1511_04515_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"{LIB_PATH} is missing: run paper_1511_04515_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    P, D, I32 = C.c_void_p, C.c_double, C.c_int32
+    pd = C.POINTER(C.c_double)
+    pi = C.POINTER(C.c_int32)
+    sig = {
+        "ers_default_opts": ([C.POINTER(Opts)], C.c_int),
+        "ers_create": ([C.POINTER(P), C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr),
+                        C.POINTER(Mosfet), I32, C.POINTER(Pwl), I32, C.POINTER(Opts)], C.c_int),
+        "ers_set_stream": ([P, P], C.c_int),
+        "ers_dc": ([P, pd], C.c_int),
+        "ers_refactor": ([P], C.c_int),
+        "ers_step": ([P, D, I32, pi, pd], C.c_int),
+        "ers_run": ([P, D, D, I32, pi, pi], C.c_int),
+        "ers_get_state": ([P, pd, pd, pd], C.c_int),
+        "ers_set_state": ([P, D, pd, D], C.c_int),
+        "ers_get_state_dev": ([P, P], C.c_int),
+        "ers_set_state_dev": ([P, D, P, D], C.c_int),
+        "ers_solve": ([P, pd, pd], C.c_int),
+        "ers_spmv_C": ([P, pd, pd], C.c_int),
+        "ers_mevp": ([P, pd, D, I32, pd, pi], C.c_int),
+        "ers_phi_small": ([P, pd, I32, I32, D, pd, pd], C.c_int),
+        "ers_stats": ([P, C.POINTER(Stats)], C.c_int),
+        "ers_profile": ([P, I32], C.c_int),
+        "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
+        "ers_last_error": ([P], C.c_char_p),
+        "ers_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class _CsrHold:
+    """Keeps the numpy arrays of a CSR alive while the C structure points at them."""
+
+    def __init__(self, mat, shape=None):
+        indptr = np.ascontiguousarray(mat.indptr, dtype=np.int32)
+        indices = np.ascontiguousarray(mat.indices, dtype=np.int32)
+        data = np.ascontiguousarray(mat.data, dtype=np.float64)
+        rows, cols = shape if shape is not None else mat.shape
+        self.arrays = (indptr, indices, data)
+        self.c = Csr(int(rows), int(cols), int(indices.size), _iptr(indptr), _iptr(indices),
+                     _dptr(data))
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().ers_default_opts(C.byref(o))
+    return o
+
+
+def make_opts(**kw) -> Opts:
+    o = default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def analyze(pattern) -> dict:
+    """Host-only symbolic analysis of a square CSR pattern (no GPU needed)."""
+    h = _CsrHold(pattern)
+    st = Stats()
+    n = pattern.shape[0]
+    perm = np.zeros(n, np.int32)
+    rc = lib().ers_analyze(C.byref(h.c), C.byref(st), _iptr(perm))
+    if rc != 0:
+        raise ErsError(rc, "symbolic analysis failed")
+    d = st.as_dict()
+    d["perm"] = perm
+    return d
+
+
+class Simulator:
+    """One circuit on one GPU: C x' + G_lin x + i_dev(x) = B u(t) (see include/ers.h)."""
+
+    def __init__(self, G, Cmat, B, dev=None, pwl: Sequence = (), opts: Optional[Opts] = None,
+                 stream=None):
+        L = lib()
+        n = G.shape[0]
+        self.n = n
+        self._G = _CsrHold(G)
+        self._C = _CsrHold(Cmat)
+        self._B = _CsrHold(B, (n, B.shape[1]))
+        p = B.shape[1]
+        ndev = 0 if dev is None else len(dev)
+        devs = (Mosfet * max(ndev, 1))()
+        for i in range(ndev):
+            d = dev[i]
+            devs[i] = Mosfet(int(d["type"]), int(d["d"]), int(d["g"]), int(d["s"]),
+                             float(d["vt"]), float(d["k"]), float(d["lam"]))
+        self._pwl_arrays = []
+        pw = (Pwl * max(p, 1))()
+        for q, (tt, vv) in enumerate(pwl):
+            tt = np.ascontiguousarray(tt, np.float64)
+            vv = np.ascontiguousarray(vv, np.float64)
+            self._pwl_arrays.append((tt, vv))
+            pw[q] = Pwl(int(tt.size), _dptr(tt), _dptr(vv))
+        self.opts = opts if opts is not None else default_opts()
+        self._ctx = C.c_void_p()
+        rc = L.ers_create(C.byref(self._ctx), C.byref(self._G.c), C.byref(self._C.c),
+                          C.byref(self._B.c), devs if ndev else None, ndev,
+                          pw if p else None, p, C.byref(self.opts))
+        if rc != 0:
+            msg = L.ers_last_error(self._ctx).decode() if self._ctx else ""
+            if self._ctx:
+                L.ers_destroy(self._ctx)
+            self._ctx = None
+            raise ErsError(rc, msg)
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_circuit(cls, circ, opts: Optional[Opts] = None, stream=None):
+        return cls(circ.G, circ.C, circ.B, circ.dev, circ.pwl, opts=opts, stream=stream)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ErsError(rc, lib().ers_last_error(self._ctx).decode())
+
+    def close(self):
+        if self._ctx:
+            lib().ers_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: torch.cuda.Stream, an int handle, or None (private stream)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(lib().ers_set_stream(self._ctx, C.c_void_p(handle) if handle else None))
+
+    def dc(self, x0=None):
+        arr = None if x0 is None else np.ascontiguousarray(x0, np.float64)
+        self._check(lib().ers_dc(self._ctx, _dptr(arr) if arr is not None else None))
+
+    def refactor(self):
+        self._check(lib().ers_refactor(self._ctx))
+
+    def step(self, h: float, m: int = 0):
+        mu = C.c_int32(0)
+        err = C.c_double(0.0)
+        self._check(lib().ers_step(self._ctx, float(h), int(m), C.byref(mu), C.byref(err)))
+        return mu.value, err.value
+
+    def run(self, t_end: float, tol: float = 1e-6, max_steps: int = 0):
+        ns = C.c_int32(0)
+        nr = C.c_int32(0)
+        self._check(lib().ers_run(self._ctx, float(t_end), float(tol), int(max_steps),
+                                  C.byref(ns), C.byref(nr)))
+        return ns.value, nr.value
+
+    def profile(self, enable: bool = True):
+        self._check(lib().ers_profile(self._ctx, int(bool(enable))))
+
+    def state(self):
+        x = np.zeros(self.n)
+        t = C.c_double(0.0)
+        h = C.c_double(0.0)
+        self._check(lib().ers_get_state(self._ctx, C.byref(t), _dptr(x), C.byref(h)))
+        return t.value, x, h.value
+
+    def set_state(self, t: float, x, h: float = 0.0):
+        x = np.ascontiguousarray(x, np.float64)
+        self._check(lib().ers_set_state(self._ctx, float(t), _dptr(x), float(h)))
+
+    def get_state_dev(self, ptr: int):
+        self._check(lib().ers_get_state_dev(self._ctx, C.c_void_p(ptr)))
+
+    def set_state_dev(self, t: float, ptr: int, h: float = 0.0):
+        self._check(lib().ers_set_state_dev(self._ctx, float(t), C.c_void_p(ptr), float(h)))
+
+    def solve(self, b):
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(self.n)
+        self._check(lib().ers_solve(self._ctx, _dptr(b), _dptr(x)))
+        return x
+
+    def spmv_C(self, v):
+        v = np.ascontiguousarray(v, np.float64)
+        y = np.zeros(self.n)
+        self._check(lib().ers_spmv_C(self._ctx, _dptr(v), _dptr(y)))
+        return y
+
+    def mevp(self, v, h: float, m: int = 0):
+        v = np.ascontiguousarray(v, np.float64)
+        out = np.zeros(self.n)
+        mu = C.c_int32(0)
+        self._check(lib().ers_mevp(self._ctx, _dptr(v), float(h), int(m), _dptr(out), C.byref(mu)))
+        return out, mu.value
+
+    def phi_small(self, H, h: float):
+        H = np.asfortranarray(H, np.float64)
+        m = H.shape[1]
+        y = np.zeros(m)
+        last = C.c_double(0.0)
+        self._check(lib().ers_phi_small(self._ctx, _dptr(H.ravel(order="F")), int(H.shape[0]), m,
+                                        float(h), _dptr(y), C.byref(last)))
+        return y, last.value
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(lib().ers_stats(self._ctx, C.byref(st)))
+        return st.as_dict()

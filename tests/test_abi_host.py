@@ -1,0 +1,102 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads, exports every
+symbol include/ers.h declares, and its host-only symbolic analysis is consistent."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from synth import circuits as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1511_04515_gb300 import build
+    build.build()
+    from paper_1511_04515_gb300 import ers
+    return ers
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ers.h")).read()
+    return sorted(set(re.findall(r"\b(ers_[A-Za-z_]+)\s*\(", src)))
+
+
+def test_header_declares_binding_exports(E):
+    assert declared_symbols() == sorted(E.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(E):
+    L = E.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_default_opts(E):
+    o = E.default_opts()
+    assert o.eps_krylov == 1e-7 and o.alpha == 0.5 and o.beta == 2.0 and o.i_grow == 5
+    assert o.m_max == 40 and o.gamma == 0.1
+
+
+def _pattern(c):
+    rows, cols = [], []
+    for d in c.dev:
+        for node in (d["d"], d["s"]):
+            if node < 0:
+                continue
+            for t in (d["d"], d["g"], d["s"]):
+                if t >= 0:
+                    rows.append(node)
+                    cols.append(t)
+    A = c.G.tocoo()
+    r = np.concatenate([A.row, rows, np.arange(c.n)])
+    cc = np.concatenate([A.col, cols, np.arange(c.n)])
+    M = sp.csr_matrix((np.ones(r.size), (r, cc)), shape=(c.n, c.n))
+    M.sum_duplicates()
+    M.sort_indices()
+    return M
+
+
+def _chol_nnz(M, perm):
+    """nnz of the Cholesky factor of the symmetrised, permuted pattern by dense elimination
+    on a boolean matrix (brute force, small cases only)."""
+    A = (M + M.T).toarray() != 0
+    A = A[np.ix_(perm, perm)]
+    n = A.shape[0]
+    nnz = 0
+    for k in range(n):
+        nb = np.nonzero(A[k + 1:, k])[0] + k + 1
+        nnz += 1 + nb.size
+        A[np.ix_(nb, nb)] = True
+    return nnz
+
+
+@pytest.mark.parametrize("circ", [S.rc_mesh_2d(9, 7, seed=1), S.random_rc(n=30, seed=2),
+                                  S.inverter_chain(stages=5, tree_nodes=12, seed=3),
+                                  S.rc_mesh_3d(6, 5, 4, seed=1, n_loads=5)])
+def test_symbolic_fill_matches_brute_force(E, circ):
+    M = _pattern(circ)
+    d = E.analyze(M)
+    perm = d["perm"]
+    assert sorted(perm.tolist()) == list(range(circ.n))
+    assert d["nnz_L"] == _chol_nnz(M, perm)
+    assert d["nsn"] >= 1 and d["nlevels"] >= 1
+
+
+def test_tree_ordering_has_no_fill(E):
+    """A tree (RC tree without devices) eliminates leaf-first with zero fill."""
+    circ = S.inverter_chain(stages=1, tree_nodes=60, seed=7)
+    M = _pattern(circ)
+    d = E.analyze(M)
+    sym = ((M + M.T) != 0).astype(int)
+    assert d["nnz_L"] == circ.n + (sym.nnz - circ.n) // 2
+
+
+def test_analyze_rejects_missing_diagonal(E):
+    M = sp.csr_matrix(np.array([[0.0, 1.0], [1.0, 1.0]]))
+    M.eliminate_zeros()
+    with pytest.raises(E.ErsError):
+        E.analyze(M)
