@@ -20,6 +20,7 @@ cudaError_t factor_kernel_attributes();
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+cudaError_t solve_kernel_attributes();
 // k_krylov.cu
 cudaError_t krylov_init_constants();
 cudaError_t launch_arnoldi_init(ers_ctx* c, const VecGroup& g, int adaptive);
@@ -529,6 +530,7 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const e
   CUB(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   c->own_stream = true;
   CUB(factor_kernel_attributes());
+  CUB(solve_kernel_attributes());
   CUB(krylov_init_constants());
   c->coop_blocks = coop_max_blocks(c->sm_count);
 
@@ -672,6 +674,8 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const e
   CUB(upload(&P.ptask_r0, S.ptask_r0));
   CUB(upload(&P.fwd, S.fwd));
   CUB(upload(&P.bwd, S.bwd));
+  CUB(upload(&P.fwd_small, S.fwd_small));
+  CUB(upload(&P.bwd_small, S.bwd_small));
   CUB(upload(&P.fwd_tgt, S.fwd_tgt));
   CUB(upload(&P.fwd_expect, S.fwd_expect));
   CUB(upload(&P.bwd_nchunk, S.bwd_nchunk));
@@ -1073,7 +1077,7 @@ void ers_destroy(ers_ctx* c) {
   for (void* p : {(void*)P.sn_start, (void*)P.sn_parent, (void*)P.rows, (void*)P.rel, (void*)P.rptr,
                   (void*)P.d_off, (void*)P.o_off, (void*)P.front_off, (void*)P.lvl_sn,
                   (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.asm_dst, (void*)P.tile_sn,
-                  (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd,
+                  (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd, (void*)P.fwd_small, (void*)P.bwd_small,
                   (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.LDi,
                   (void*)P.UDi, (void*)P.Lo, (void*)P.Uo, (void*)P.arena, (void*)P.sync})
     f(p);

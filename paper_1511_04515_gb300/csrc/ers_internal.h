@@ -61,7 +61,7 @@ struct DevicePlan {
   int32_t *lvl_sn = nullptr, *lvl_slot = nullptr, *ea_child = nullptr;
   int64_t* asm_dst = nullptr;
   int32_t *tile_sn = nullptr, *tile_ij = nullptr, *ptask_sn = nullptr, *ptask_r0 = nullptr;
-  SolveTask *fwd = nullptr, *bwd = nullptr;
+  SolveTask *fwd = nullptr, *bwd = nullptr, *fwd_small = nullptr, *bwd_small = nullptr;
   int32_t *fwd_tgt = nullptr, *fwd_expect = nullptr, *bwd_nchunk = nullptr;
   int nfwd = 0, nbwd = 0;
   // factor values

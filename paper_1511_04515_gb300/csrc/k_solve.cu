@@ -1,25 +1,33 @@
 // Sparse matrix-vector products and the supernodal triangular solves with the factors
 // of G_k (Algorithm 1: "Solve -G w = C v_j"; Alg. 2's setup solves).
 //
-// The solves are persistent, warp-granular and sync-free: every warp takes the next task
-// of a topologically ordered list (atomic counter), waits on a dependency word (bounded
-// spin), runs the task with its 32 lanes and publishes completion.  Because tasks are
-// taken in list order and only wait on earlier tasks, the scheme cannot deadlock.
-//   forward  (L y = b):  FUSED/DIAG wait until every unit scattering into the supernode is
-//                        done; y_s <- L11^-1 y_s; OFF/FUSED scatter y_R -= L21 y_s (FP64
-//                        atomics) and bump the counters of the supernodes they touched.
-//   backward (U x = y):  a supernode's rows R_off lie in its ancestors, and a parent is
-//                        finished only after its own parent, so waiting for the parent
-//                        suffices; x_s <- U11^-1 (x_s - U12 x_R).
-// Up to MAX_RHS right-hand sides (stride n) share each pass over the factors.
+// The solves are persistent and sync-free.  A CTA takes the next entry of a topologically
+// ordered work list (atomic counter), stages the entry's factor data in shared memory
+// BEFORE waiting on its dependency word (bounded spin), then runs it and publishes
+// completion.  Entries only wait on earlier entries, so the scheme cannot deadlock.
+//   GROUP: up to 8 small supernodes, one per warp (diagonal block + all rows);
+//   DIAG : a large supernode's diagonal block and its nearest row chunk (the rows of the
+//          next supernode up the tree), done by the whole CTA, so a chain of separator
+//          supernodes hands off once per link;
+//   OFF  : a further row chunk of a large supernode.
+//   forward  (L y = b):  a supernode starts once every unit scattering into its rows is
+//                        done; y_s <- L11^-1 y_s; y_R -= L21 y_s (FP64 atomics); the unit
+//                        then bumps the arrival counter of every supernode it touched.
+//   backward (U x = y):  the rows R_off of a supernode lie on its path to the root and a
+//                        supernode finishes only after its parent, so a unit waits for the
+//                        lowest supernode its rows touch; x_s <- U11^-1 (y_s - U12 x_R).
+// NRHS right-hand sides (stride n) share each pass over the factors.
 #include "ers_internal.h"
 #include "kcommon.cuh"
 
 namespace ers {
 
-constexpr int SOLVE_WARPS = 8;   // warps per block
+constexpr int SOLVE_THREADS = 256;
+constexpr int UNR = 8;           // independent loads per batch in the warp tasks
+constexpr int CHB = 64;          // rows of a CTA chunk (matches SymbolicOptions::solve_chunk)
+constexpr int LDP = CHB + 1;     // padded leading dimension of a staged panel (no bank conflicts)
 
-// y = A x for a CSR matrix (warp per row for long rows is not needed: rows here are short)
+// y = A x for a CSR matrix with short rows
 __global__ void k_spmv(int nrows, const int32_t* ptr, const int32_t* idx, const double* val,
                        const double* x, double* y, double alpha) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,213 +37,558 @@ __global__ void k_spmv(int nrows, const int32_t* ptr, const int32_t* idx, const 
   y[i] = alpha * acc;
 }
 
-// y_r = alpha * C v_r for several vectors (used to form the Arnoldi right-hand sides)
-__global__ void k_spmv_multi(int n, const int32_t* ptr, const int32_t* idx, const double* val,
-                             const double* const* xs, double* y, int64_t ystride, int nv,
-                             double alpha) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int v = 0; v < nv; ++v) {
-    const double* x = xs[v];
-    double acc = 0.0;
-    for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * x[idx[e]];
-    y[v * ystride + i] = alpha * acc;
-  }
-}
-
 struct SolveArgs {
   DevicePlan P;
   double* y;        // nrhs vectors, stride n (in place)
-  int nrhs;
   int n;
   unsigned* status;
 };
 
-// sync words layout (ints): [0] fwd task counter, [1] bwd task counter,
-// [2 + s] fwd arrivals, [2 + nsn + s] ready/done flags, [2 + 2 nsn + s] bwd arrivals
-__global__ void __launch_bounds__(32 * SOLVE_WARPS) k_trsv_fwd(SolveArgs A) {
-  __shared__ double ys[SOLVE_WARPS][MAX_RHS][64];
-  const DevicePlan& P = A.P;
-  int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  int32_t* sync = P.sync;
-  int32_t* arrive = sync + 2;
-  int32_t* ready = sync + 2 + P.nsn;
-  const int n = A.n, nrhs = A.nrhs;
-  while (true) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(sync, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= P.nfwd) break;
-    SolveTask T = P.fwd[t];
-    int s = T.sn;
-    int c0 = P.sn_start[s], w = P.sn_start[s + 1] - c0;
-    int r = (int)(P.rptr[s + 1] - P.rptr[s]);
-    int ok = 1;
-    if (lane == 0) {
-      if (T.kind == TASK_OFF) ok = wait_geq(ready + s, 1, A.status);
-      else ok = wait_geq(arrive + s, P.fwd_expect[s], A.status);
+// shared-memory layout of a CTA (doubles)
+constexpr int SM_D = 64 * 64;            // diagonal block
+constexpr int SM_P = LDP * 64;           // panel chunk, column-major with ld LDP
+constexpr int SM_V = MAX_RHS * 64;       // vectors
+constexpr int SM_PART = 4 * 64 * MAX_RHS;
+constexpr int SOLVE_SMEM = (SM_D + SM_P + 2 * SM_V + SM_PART) * 8;
+
+// z_q = sum_{j in tri(q)} M[q + j w] y_j for lanes q (lower: j <= q, upper: j >= q)
+template <int NRHS, bool LOWER>
+__device__ __forceinline__ void warp_tri_gemv(const double* M, int w, const double (*ys)[64],
+                                              double (*z)[NRHS], int lane) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int q = lane + 32 * h;
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) z[h][k] = 0.0;
+    if (q >= w) continue;
+    int j0 = LOWER ? 0 : q, j1 = LOWER ? q + 1 : w;
+    int j = j0;
+    for (; j + UNR <= j1; j += UNR) {
+      double m[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) m[u] = __ldg(M + q + (int64_t)(j + u) * w);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) z[h][k] += m[u] * ys[k][j + u];
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) continue;
-    __threadfence();
-    // load y_s
-    for (int q = lane; q < w; q += 32)
-      for (int k = 0; k < nrhs; ++k) ys[wq][k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
-    __syncwarp();
-    if (T.kind != TASK_OFF) {
-      // z = L11^-1 y_s (unit lower, column-major w x w)
-      const double* Li = P.LDi + P.d_off[s];
-      double z[2][MAX_RHS];
-      for (int h = 0; h < 2; ++h) {
-        int q = lane + 32 * h;
-        for (int k = 0; k < nrhs; ++k) z[h][k] = 0.0;
-        if (q < w)
-          for (int j = 0; j <= q; ++j) {
-            double l = Li[q + j * w];
-            for (int k = 0; k < nrhs; ++k) z[h][k] += l * ys[wq][k][j];
-          }
-      }
-      __syncwarp();
-      for (int h = 0; h < 2; ++h) {
-        int q = lane + 32 * h;
-        if (q < w)
-          for (int k = 0; k < nrhs; ++k) {
-            ys[wq][k][q] = z[h][k];
-            A.y[(int64_t)k * n + c0 + q] = z[h][k];
-          }
-      }
-      __syncwarp();
+    for (; j < j1; ++j) {
+      double m = __ldg(M + q + (int64_t)j * w);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) z[h][k] += m * ys[k][j];
     }
-    if (T.kind == TASK_DIAG) {
-      if (lane == 0) {
-        __threadfence();
-        st_release(ready + s, 1);
-      }
-      continue;
-    }
-    // scatter rows r0..r1: y[R[i]] -= sum_k Lo[i + k r] z_k
-    const double* Lo = P.Lo + P.o_off[s];
-    const int32_t* R = P.rows + P.rptr[s];
-    for (int i = T.r0 + lane; i < T.r1; i += 32) {
-      double acc[MAX_RHS];
-      for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
-      for (int j = 0; j < w; ++j) {
-        double l = __ldg(Lo + i + (int64_t)j * r);
-        for (int k = 0; k < nrhs; ++k) acc[k] += l * ys[wq][k][j];
-      }
-      int row = R[i];
-      for (int k = 0; k < nrhs; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
-    }
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      for (int q = 0; q < T.ntgt; ++q) red_release_add(arrive + P.fwd_tgt[T.tgt0 + q], 1);
-    }
-    __syncwarp();
   }
 }
 
-__global__ void __launch_bounds__(32 * SOLVE_WARPS) k_trsv_bwd(SolveArgs A) {
-  __shared__ double xs[SOLVE_WARPS][MAX_RHS][64];
+// one small supernode, forward, by one warp
+template <int NRHS>
+__device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*ys)[64]) {
   const DevicePlan& P = A.P;
-  int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  int32_t* arrive = P.sync + 2;
+  const int n = A.n;
+  const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+  const double* Li = P.LDi + T.d_off;
+  const double* Lo = P.Lo + T.o_off;
+  const int32_t* R = P.rows + T.row_off;
+  int ok = 1;
+  if (lane == 0) ok = wait_geq(arrive + s, T.wait_cnt, A.status);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  __threadfence();
+  for (int q = lane; q < w; q += 32)
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) ys[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+  __syncwarp();
+  double z[2][NRHS];
+  warp_tri_gemv<NRHS, true>(Li, w, ys, z, lane);
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int q = lane + 32 * h;
+    if (q < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        ys[k][q] = z[h][k];
+        A.y[(int64_t)k * n + c0 + q] = z[h][k];
+      }
+  }
+  __syncwarp();
+  for (int i = lane; i < r; i += 32) {
+    double acc[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+    const double* col = Lo + i;
+    int j = 0;
+    for (; j + UNR <= w; j += UNR) {
+      double l[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) l[u] = __ldg(col + (int64_t)(j + u) * r);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] += l[u] * ys[k][j + u];
+    }
+    for (; j < w; ++j) {
+      double l = __ldg(col + (int64_t)j * r);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] += l * ys[k][j];
+    }
+    int row = __ldg(R + i);
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0)
+    for (int q = 0; q < T.ntgt; ++q) red_release_add(arrive + P.fwd_tgt[T.tgt0 + q], 1);
+  __syncwarp();
+}
+
+// one small supernode, backward, by one warp
+template <int NRHS>
+__device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*xs)[64]) {
+  const DevicePlan& P = A.P;
+  int32_t* done = P.sync + 2 + P.nsn;
+  const int n = A.n;
+  const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+  const double* Ui = P.UDi + T.d_off;
+  const double* Uo = P.Uo + T.o_off;
+  const int32_t* R = P.rows + T.row_off;
+  int ok = 1;
+  if (lane == 0 && T.wait_sn >= 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  __threadfence();
+  for (int q = lane; q < w; q += 32)
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) xs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+  __syncwarp();
+  // xs_j -= sum_i Uo[i + j r] x[R[i]]
+  for (int i0 = 0; i0 < r; i0 += 32) {
+    int i = i0 + lane;
+    double xr[NRHS];
+    int row = i < r ? __ldg(R + i) : 0;
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) xr[k] = i < r ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
+    for (int j0 = 0; j0 < w; j0 += UNR) {
+      double u[UNR];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q)
+        u[q] = (i < r && j0 + q < w) ? __ldg(Uo + i + (int64_t)(j0 + q) * r) : 0.0;
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) {
+        if (j0 + q >= w) break;
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          double v = warp_sum(u[q] * xr[k]);
+          if (lane == 0) xs[k][j0 + q] -= v;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  double z[2][NRHS];
+  warp_tri_gemv<NRHS, false>(Ui, w, xs, z, lane);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int q = lane + 32 * h;
+    if (q < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) A.y[(int64_t)k * n + c0 + q] = z[h][k];
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release(done + s, 2);
+  __syncwarp();
+}
+
+// a far chunk of a large supernode, forward, one warp: lanes over rows,
+// y[R[i]] -= sum_j Lo[i + j r] z_j with z = y_s (written by the supernode's DIAG task)
+template <int NRHS>
+__device__ void fwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, double* buf) {
+  const DevicePlan& P = A.P;
+  int32_t* arrive = P.sync + 2;
+  int32_t* ready = P.sync + 2 + P.nsn;
+  const int n = A.n;
+  const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+  const double* Lo = P.Lo + T.o_off;
+  const int32_t* R = P.rows + T.row_off;
+  double (*zs)[64] = reinterpret_cast<double (*)[64]>(buf);
+  const int i = T.r0 + lane;
+  const bool act = i < T.r1;
+  const int row = act ? __ldg(R + i) : 0;
+  int ok = 1;
+  if (lane == 0) ok = wait_geq(ready + s, 1, A.status);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  __threadfence();
+  for (int q = lane; q < w; q += 32)
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) zs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+  __syncwarp();
+  double acc[NRHS];
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+  const double* col = Lo + i;
+  constexpr int B = 16;
+  for (int j0 = 0; j0 < w; j0 += B) {
+    double l[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) l[u] = (act && j0 + u < w) ? __ldg(col + (int64_t)(j0 + u) * r) : 0.0;
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j0 + u < w)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] += l[u] * zs[k][j0 + u];
+  }
+  if (act)
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
+  __threadfence();
+  __syncwarp();
+  if (lane == 0)
+    for (int q = 0; q < T.ntgt; ++q) red_release_add(arrive + P.fwd_tgt[T.tgt0 + q], 1);
+  __syncwarp();
+}
+
+// a far chunk, backward, one warp: lanes over columns,
+// y[c0 + j] -= sum_{i in chunk} Uo[i + j r] x[R[i]]
+template <int NRHS>
+__device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, double* buf) {
+  const DevicePlan& P = A.P;
+  int32_t* done = P.sync + 2 + P.nsn;
+  int32_t* arriveb = P.sync + 2 + 2 * P.nsn;
+  const int n = A.n;
+  const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+  const double* Uo = P.Uo + T.o_off;
+  const int32_t* R = P.rows + T.row_off;
+  double (*xr)[32] = reinterpret_cast<double (*)[32]>(buf);
+  const int rows = T.r1 - T.r0;
+  const int myrow = lane < rows ? __ldg(R + T.r0 + lane) : 0;
+  int ok = 1;
+  if (lane == 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) xr[k][lane] = lane < rows ? __ldcg(A.y + (int64_t)k * n + myrow) : 0.0;
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int j = lane + 32 * h;
+    if (j >= w) continue;
+    const double* col = Uo + (int64_t)j * r + T.r0;
+    double acc[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+    constexpr int B = 16;
+    for (int i0 = 0; i0 < rows; i0 += B) {
+      double u[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) u[q] = i0 + q < rows ? __ldg(col + i0 + q) : 0.0;
+#pragma unroll
+      for (int q = 0; q < B; ++q)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] += u[q] * xr[k][(i0 + q) & 31];
+    }
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + c0 + j, -acc[k]);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) red_release_add(arriveb + s, 1);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// One warp issues L2 prefetches for the factor data of a (non-group) task.
+__device__ __forceinline__ void prefetch_task(const SolveTask& T, const double* D,
+                                              const double* Pn, const int32_t* rows, int lane) {
+  if (T.kind == TASK_GROUP) return;
+  if (T.kind == TASK_DIAG) {
+    const char* d = reinterpret_cast<const char*>(D + T.d_off);
+    for (int64_t o = (int64_t)lane * 128; o < (int64_t)T.w * T.w * 8; o += 32 * 128)
+      prefetch_l2(d + o);
+  }
+  int len = T.r1 - T.r0;
+  if (len > 0) {
+    int lines = (len * 8 + 127) / 128 + 1;
+    const double* base = Pn + T.o_off;
+    for (int q = lane; q < T.w * lines; q += 32) {
+      int j = q / lines, l = q % lines;
+      int off = T.r0 + l * 16;
+      if (off < T.r) prefetch_l2(base + (int64_t)j * T.r + off);
+    }
+    if (lane == 0) prefetch_l2(rows + T.row_off + T.r0);
+  }
+}
+
+// Stage a w x w diagonal block and panel rows [r0, r1) (ld r) into shared memory.  Every
+// thread first issues all its loads (at most 16 + 16 independent requests), then stores.
+__device__ __forceinline__ void stage(const double* D, int w, const double* Pn, int r, int r0,
+                                      int r1, double* sD, double* sP, bool with_diag) {
+  const int tid = threadIdx.x;
+  constexpr int PER = (64 * 64) / SOLVE_THREADS;   // 16
+  const int rows = r1 - r0;
+  const int nd = with_diag ? w * w : 0, np = rows * w;
+  double vd[PER], vp[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    int e = tid + u * SOLVE_THREADS;
+    vd[u] = e < nd ? __ldg(D + e) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    int e = tid + u * SOLVE_THREADS;
+    int i = e % max(rows, 1), j = e / max(rows, 1);
+    vp[u] = e < np ? __ldg(Pn + r0 + i + (int64_t)j * r) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    int e = tid + u * SOLVE_THREADS;
+    if (e < nd) sD[e] = vd[u];
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    int e = tid + u * SOLVE_THREADS;
+    int i = e % max(rows, 1), j = e / max(rows, 1);
+    if (e < np) sP[i + j * LDP] = vp[u];
+  }
+}
+
+template <int NRHS>
+__global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_fwd(SolveArgs A) {
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sP = sD + SM_D;
+  double (*ys)[64] = reinterpret_cast<double (*)[64]>(sP + SM_P);
+  double (*zs)[64] = reinterpret_cast<double (*)[64]>(sP + SM_P + SM_V);
+  double* part = sP + SM_P + 2 * SM_V;   // [4][64][NRHS]
+  __shared__ int s_cur, s_ok;
+  const DevicePlan& P = A.P;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
+  int32_t* sync = P.sync;
+  int32_t* arrive = sync + 2;
+  int32_t* ready = sync + 2 + P.nsn;
+  const int n = A.n;
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_cur = atomicAdd(sync, 1);
+    __syncthreads();
+    int e = s_cur;
+    if (e >= P.nfwd) break;
+    SolveTask T = P.fwd[e];
+    if (T.kind == TASK_GROUP) {
+      if (wq < T.r0)
+        fwd_small<NRHS>(A, P.fwd_small[T.sn + wq], lane,
+                        reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64));
+      continue;
+    }
+    if (T.kind == TASK_BULK) {
+      if (wq < T.r0) fwd_chunk<NRHS>(A, P.fwd_small[T.sn + wq], lane, sm + wq * MAX_RHS * 64);
+      continue;
+    }
+    const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+    const int32_t* R = P.rows + T.row_off;
+    bool diag = T.kind == TASK_DIAG;
+    stage(P.LDi + T.d_off, w, P.Lo + T.o_off, r, T.r0, T.r1, sD, sP, diag);
+    if (tid == 0)
+      s_ok = diag ? wait_geq(arrive + s, T.wait_cnt, A.status) : wait_geq(ready + s, 1, A.status);
+    __syncthreads();
+    if (!s_ok) continue;
+    __threadfence();
+    if (tid < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) ys[k][tid] = __ldcg(A.y + (int64_t)k * n + c0 + tid);
+    __syncthreads();
+    const int q = tid & 63, g = tid >> 6;   // row / column-group of the 64 x 4 thread grid
+    if (diag) {
+      // z = L11^-1 y_s, columns split in 4 groups of 16
+      double acc[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+      if (q < w) {
+        int j1 = min(16 * g + 16, q + 1);
+        for (int j = 16 * g; j < j1; ++j) {
+          double m = sD[q + j * w];
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) acc[k] += m * ys[k][j];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) part[(g * 64 + q) * NRHS + k] = acc[k];
+      __syncthreads();
+      if (tid < w)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          double z = part[(0 * 64 + tid) * NRHS + k] + part[(1 * 64 + tid) * NRHS + k] +
+                     part[(2 * 64 + tid) * NRHS + k] + part[(3 * 64 + tid) * NRHS + k];
+          zs[k][tid] = z;
+          A.y[(int64_t)k * n + c0 + tid] = z;
+        }
+      __syncthreads();
+    } else {
+      if (tid < w)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) zs[k][tid] = ys[k][tid];
+      __syncthreads();
+    }
+    // chunk rows [r0, r1): y[R[i]] -= sum_j Lo[i + j r] z_j
+    int rows = T.r1 - T.r0;
+    {
+      double acc[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+      if (q < rows) {
+        int j1 = min(16 * g + 16, w);
+        for (int j = 16 * g; j < j1; ++j) {
+          double l = sP[q + j * LDP];
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) acc[k] += l * zs[k][j];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) part[(g * 64 + q) * NRHS + k] = acc[k];
+    }
+    __syncthreads();
+    if (tid < rows) {
+      int row = __ldg(R + T.r0 + tid);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        double v = part[(0 * 64 + tid) * NRHS + k] + part[(1 * 64 + tid) * NRHS + k] +
+                   part[(2 * 64 + tid) * NRHS + k] + part[(3 * 64 + tid) * NRHS + k];
+        atomicAdd(A.y + (int64_t)k * n + row, -v);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      if (diag) st_release(ready + s, 1);
+      for (int t = 0; t < T.ntgt; ++t) red_release_add(arrive + P.fwd_tgt[T.tgt0 + t], 1);
+    }
+  }
+}
+
+template <int NRHS>
+__global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_bwd(SolveArgs A) {
+  extern __shared__ double sm[];
+  double* sD = sm;
+  double* sP = sD + SM_D;
+  double (*xr)[64] = reinterpret_cast<double (*)[64]>(sP + SM_P);          // x at chunk rows
+  double (*xs)[64] = reinterpret_cast<double (*)[64]>(sP + SM_P + SM_V);   // x_s
+  double* part = sP + SM_P + 2 * SM_V;
+  __shared__ int s_cur, s_ok;
+  const DevicePlan& P = A.P;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
   int32_t* sync = P.sync;
   int32_t* done = sync + 2 + P.nsn;
   int32_t* arriveb = sync + 2 + 2 * P.nsn;
-  const int n = A.n, nrhs = A.nrhs;
+  const int n = A.n;
   while (true) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(sync + 1, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= P.nbwd) break;
-    SolveTask T = P.bwd[t];
-    int s = T.sn;
-    int c0 = P.sn_start[s], w = P.sn_start[s + 1] - c0;
-    int r = (int)(P.rptr[s + 1] - P.rptr[s]);
-    int p = P.sn_parent[s];
-    int ok = 1;
-    if (lane == 0) {
-      if (T.kind == TASK_DIAG) ok = wait_geq(arriveb + s, P.bwd_nchunk[s], A.status);
-      else if (p >= 0) ok = wait_geq(done + p, 2, A.status);
+    __syncthreads();
+    if (tid == 0) s_cur = atomicAdd(sync + 1, 1);
+    __syncthreads();
+    int e = s_cur;
+    if (e >= P.nbwd) break;
+    SolveTask T = P.bwd[e];
+    if (T.kind == TASK_GROUP) {
+      if (wq < T.r0)
+        bwd_small<NRHS>(A, P.bwd_small[T.sn + wq], lane,
+                        reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64));
+      continue;
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) continue;
+    if (T.kind == TASK_BULK) {
+      if (wq < T.r0) bwd_chunk<NRHS>(A, P.bwd_small[T.sn + wq], lane, sm + wq * MAX_RHS * 64);
+      continue;
+    }
+    const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
+    const int32_t* R = P.rows + T.row_off;
+    bool diag = T.kind == TASK_DIAG;
+    stage(P.UDi + T.d_off, w, P.Uo + T.o_off, r, T.r0, T.r1, sD, sP, diag);
+    if (tid == 0) {
+      int ok = 1;
+      if (T.wait_sn >= 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
+      if (ok && diag) ok = wait_geq(arriveb + s, T.wait_cnt, A.status);
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) continue;
     __threadfence();
-    if (T.kind != TASK_DIAG) {
-      // partial z_k = sum_{i in r0..r1} Uo[i + k r] x[R[i]]
-      const double* Uo = P.Uo + P.o_off[s];
-      const int32_t* R = P.rows + P.rptr[s];
-      double xr[8][MAX_RHS];
-      int nchunk = (T.r1 - T.r0 + 31) / 32;
-      // rows are processed 32 at a time; gather x[R[i]] once per row block
-      for (int k = 0; k < nrhs; ++k)
-        for (int q = lane; q < w; q += 32) xs[wq][k][q] = 0.0;
-      __syncwarp();
-      for (int cb = 0; cb < nchunk; cb += 8) {
-        int nb = min(8, nchunk - cb);
-        for (int b = 0; b < nb; ++b) {
-          int i = T.r0 + (cb + b) * 32 + lane;
-          for (int k = 0; k < nrhs; ++k)
-            xr[b][k] = i < T.r1 ? __ldcg(A.y + (int64_t)k * n + R[i]) : 0.0;
-        }
-        for (int j = 0; j < w; ++j) {
-          double acc[MAX_RHS];
-          for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
-          for (int b = 0; b < nb; ++b) {
-            int i = T.r0 + (cb + b) * 32 + lane;
-            double u = i < T.r1 ? __ldg(Uo + i + (int64_t)j * r) : 0.0;
-            for (int k = 0; k < nrhs; ++k) acc[k] += u * xr[b][k];
-          }
-          for (int k = 0; k < nrhs; ++k) {
-            double v = warp_sum(acc[k]);
-            if (lane == 0) xs[wq][k][j] += v;
-          }
+    int rows = T.r1 - T.r0;
+    if (tid < rows) {
+      int row = __ldg(R + T.r0 + tid);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) xr[k][tid] = __ldcg(A.y + (int64_t)k * n + row);
+    }
+    __syncthreads();
+    const int q = tid & 63, g = tid >> 6;   // column / row-group of the 64 x 4 thread grid
+    {
+      double acc[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+      if (q < w) {
+        int i1 = min(16 * g + 16, rows);
+        for (int i = 16 * g; i < i1; ++i) {
+          double u = sP[i + q * LDP];
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) acc[k] += u * xr[k][i];
         }
       }
-      __syncwarp();
-      if (T.kind == TASK_OFF) {
-        for (int q = lane; q < w; q += 32)
-          for (int k = 0; k < nrhs; ++k) atomicAdd(A.y + (int64_t)k * n + c0 + q, -xs[wq][k][q]);
-        __syncwarp();
-        if (lane == 0) {
-          __threadfence();
-          red_release_add(arriveb + s, 1);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) part[(g * 64 + q) * NRHS + k] = acc[k];
+    }
+    __syncthreads();
+    if (!diag) {
+      if (tid < w)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          double v = part[(0 * 64 + tid) * NRHS + k] + part[(1 * 64 + tid) * NRHS + k] +
+                     part[(2 * 64 + tid) * NRHS + k] + part[(3 * 64 + tid) * NRHS + k];
+          atomicAdd(A.y + (int64_t)k * n + c0 + tid, -v);
         }
-        __syncwarp();
-        continue;
-      }
-      // FUSED: x_s = y_s - z
-      for (int q = lane; q < w; q += 32)
-        for (int k = 0; k < nrhs; ++k)
-          xs[wq][k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q) - xs[wq][k][q];
-    } else {
-      for (int q = lane; q < w; q += 32)
-        for (int k = 0; k < nrhs; ++k) xs[wq][k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
-    }
-    __syncwarp();
-    // x_s <- U11^-1 x_s (upper, column-major)
-    const double* Ui = P.UDi + P.d_off[s];
-    double z[2][MAX_RHS];
-    for (int h = 0; h < 2; ++h) {
-      int q = lane + 32 * h;
-      for (int k = 0; k < nrhs; ++k) z[h][k] = 0.0;
-      if (q < w)
-        for (int j = q; j < w; ++j) {
-          double u = Ui[q + j * w];
-          for (int k = 0; k < nrhs; ++k) z[h][k] += u * xs[wq][k][j];
-        }
-    }
-    for (int h = 0; h < 2; ++h) {
-      int q = lane + 32 * h;
-      if (q < w)
-        for (int k = 0; k < nrhs; ++k) A.y[(int64_t)k * n + c0 + q] = z[h][k];
-    }
-    __syncwarp();
-    if (lane == 0) {
       __threadfence();
-      st_release(done + s, 2);
+      __syncthreads();
+      if (tid == 0) red_release_add(arriveb + s, 1);
+      continue;
     }
-    __syncwarp();
+    if (tid < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        double v = part[(0 * 64 + tid) * NRHS + k] + part[(1 * 64 + tid) * NRHS + k] +
+                   part[(2 * 64 + tid) * NRHS + k] + part[(3 * 64 + tid) * NRHS + k];
+        xs[k][tid] = __ldcg(A.y + (int64_t)k * n + c0 + tid) - v;
+      }
+    __syncthreads();
+    // x_s = U11^-1 xs, columns split in 4 groups of 16
+    {
+      double acc[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+      if (q < w) {
+        int j0 = max(16 * g, q), j1 = min(16 * g + 16, w);
+        for (int j = j0; j < j1; ++j) {
+          double m = sD[q + j * w];
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) acc[k] += m * xs[k][j];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) part[(g * 64 + q) * NRHS + k] = acc[k];
+    }
+    __syncthreads();
+    if (tid < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k)
+        A.y[(int64_t)k * n + c0 + tid] = part[(0 * 64 + tid) * NRHS + k] +
+                                         part[(1 * 64 + tid) * NRHS + k] +
+                                         part[(2 * 64 + tid) * NRHS + k] +
+                                         part[(3 * 64 + tid) * NRHS + k];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(done + s, 2);
   }
 }
 
@@ -245,13 +598,31 @@ void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const doubl
   c->stats.kernel_launches++;
 }
 
-// Solve G_k X = Y in place for nrhs vectors (stride n) of c->solve_buf or any buffer.
+template <int NRHS>
+static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
+  k_trsv_fwd<NRHS><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  k_trsv_bwd<NRHS><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+}
+
+cudaError_t solve_kernel_attributes() {
+  const void* fns[] = {(const void*)k_trsv_fwd<1>, (const void*)k_trsv_fwd<2>,
+                       (const void*)k_trsv_fwd<3>, (const void*)k_trsv_bwd<1>,
+                       (const void*)k_trsv_bwd<2>, (const void*)k_trsv_bwd<3>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Solve G_k X = Y in place for nrhs vectors (stride n).
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
   DevicePlan& P = c->plan;
+  if (nrhs < 1 || nrhs > MAX_RHS) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * (2 + 3 * (size_t)P.nsn), c->stream);
   if (e != cudaSuccess) return e;
-  SolveArgs A{P, y, nrhs, c->n, c->d_status};
-  int blocks = c->sm_count * 8;
+  SolveArgs A{P, y, c->n, c->d_status};
+  int blocks = c->sm_count * 3;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profile) {
     if (c->ev_free.empty()) {
@@ -263,8 +634,9 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
     }
     cudaEventRecord(ev.first, c->stream);
   }
-  k_trsv_fwd<<<blocks, 32 * SOLVE_WARPS, 0, c->stream>>>(A);
-  k_trsv_bwd<<<blocks, 32 * SOLVE_WARPS, 0, c->stream>>>(A);
+  if (nrhs == 1) launch_pair<1>(c, A, blocks);
+  else if (nrhs == 2) launch_pair<2>(c, A, blocks);
+  else launch_pair<3>(c, A, blocks);
   if (c->profile) {
     cudaEventRecord(ev.second, c->stream);
     c->ev_used.push_back(ev);

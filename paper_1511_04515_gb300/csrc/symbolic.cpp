@@ -419,6 +419,59 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     if (!merge) S.sn_start.push_back(j);
   }
   S.sn_start.push_back(n);
+  // relaxed amalgamation: fold a supernode into its parent when it is the parent's last
+  // child (so the columns stay contiguous), the merged width stays within max_width and
+  // the explicit zeros it adds stay small.  Long chains of narrow supernodes in the
+  // nested-dissection leaves otherwise make the elimination tree (and the number of
+  // dependent levels of the solves and the refactor) needlessly deep.
+  if (opt.relax_zeros > 0) {
+    int nf = (int)S.sn_start.size() - 1;
+    std::vector<int32_t> first(nf), width(nf), offr(nf), par_sn(nf, -1), snf(n);
+    for (int s = 0; s < nf; ++s) {
+      first[s] = S.sn_start[s];
+      width[s] = S.sn_start[s + 1] - S.sn_start[s];
+      offr[s] = (int32_t)(cc[first[s]] - width[s]);
+      for (int j = S.sn_start[s]; j < S.sn_start[s + 1]; ++j) snf[j] = s;
+    }
+    for (int s = 0; s < nf; ++s) {
+      int last = S.sn_start[s + 1] - 1;
+      if (par[last] >= 0) par_sn[s] = snf[par[last]];
+    }
+    // group g (start supernode) accumulates merged width, true nnz of its columns
+    std::vector<int32_t> gstart(nf);
+    std::vector<int64_t> gtrue(nf);
+    std::vector<int32_t> gwidth(nf);
+    std::vector<char> merged_into_next(nf, 0);
+    for (int s = 0; s < nf; ++s) {
+      gstart[s] = s;
+      gwidth[s] = width[s];
+      int64_t t = 0;
+      for (int j = S.sn_start[s]; j < S.sn_start[s + 1]; ++j) t += cc[j];
+      gtrue[s] = t;
+    }
+    for (int s = 0; s < nf; ++s) {
+      int p = par_sn[s];
+      if (p < 0 || p != s + 1) continue;                 // last child only (contiguous)
+      if (S.sn_start[s + 1] != first[p]) continue;
+      int64_t W = gwidth[s] + width[p];
+      if (W > opt.max_width) continue;
+      int64_t rp = offr[p];
+      int64_t stored = W * rp + W * (W + 1) / 2;
+      int64_t truth = gtrue[s];
+      for (int j = S.sn_start[p]; j < S.sn_start[p + 1]; ++j) truth += cc[j];
+      if (W > opt.relax_width && (stored - truth) * 100 > (int64_t)opt.relax_zeros * stored)
+        continue;
+      // merge group of s into p: p's group now starts where s's group started
+      merged_into_next[s] = 1;
+      gstart[p] = gstart[s];
+      gwidth[p] = (int32_t)W;
+      gtrue[p] = truth;
+    }
+    std::vector<int32_t> ns{0};
+    for (int s = 0; s < nf; ++s)
+      if (!merged_into_next[s]) ns.push_back(S.sn_start[s + 1]);
+    S.sn_start = ns;
+  }
   S.nsn = (int)S.sn_start.size() - 1;
   int nsn = S.nsn;
   S.sn_of.assign(n, 0);
@@ -446,8 +499,8 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
           if (i >= c1 && mk[i] != s) { mk[i] = s; lst.push_back(i); }
         }
       std::sort(lst.begin(), lst.end());
-      if ((int64_t)lst.size() + (c1 - c0) != cc[c0])
-        return "internal: supernode structure does not match column count";
+      if ((int64_t)lst.size() + (c1 - c0) < cc[c0])
+        return "internal: supernode structure smaller than its column count";
       S.rows.insert(S.rows.end(), lst.begin(), lst.end());
       S.rptr[s + 1] = (int64_t)S.rows.size();
       if (!lst.empty()) {
@@ -645,11 +698,12 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     }
   }
 
-  // 5. triangular-solve task lists -------------------------------------------------
+  // 5. triangular-solve work lists ---------------------------------------------------
   {
-    S.fwd.clear(); S.bwd.clear(); S.fwd_tgt.clear();
+    S.fwd.clear(); S.bwd.clear(); S.fwd_small.clear(); S.bwd_small.clear(); S.fwd_tgt.clear();
     S.fwd_expect.assign(nsn, 0);
     S.bwd_nchunk.assign(nsn, 0);
+    const int CH = opt.solve_chunk;
     auto add_targets = [&](int s, int r0, int r1, SolveTask& t) {
       t.tgt0 = (int32_t)S.fwd_tgt.size();
       int last = -1;
@@ -663,35 +717,121 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       }
       t.ntgt = (int32_t)S.fwd_tgt.size() - t.tgt0;
     };
-    for (int s = 0; s < nsn; ++s) {  // postorder: children before parents
-      int w = S.sn_start[s + 1] - S.sn_start[s];
-      int r = (int)(S.rptr[s + 1] - S.rptr[s]);
-      if ((int64_t)r * w <= opt.fused_limit) {
-        SolveTask t{TASK_FUSED, s, 0, r, 0, 0};
+    auto small = [&](int s) {
+      int64_t w = S.sn_start[s + 1] - S.sn_start[s];
+      int64_t r = S.rptr[s + 1] - S.rptr[s];
+      return w * (w + r) <= opt.fused_limit;
+    };
+    // warp tasks (small supernodes, far chunks) live in fwd_small / bwd_small; a CTA entry
+    // GROUP/BULK refers to up to 8 consecutive warp tasks of one level
+    auto flush = [](std::vector<SolveTask>& list, std::vector<SolveTask>& smalls, int& first,
+                    int kind) {
+      int cnt = (int)smalls.size() - first;
+      if (cnt <= 0) return;
+      list.push_back(SolveTask{kind, first, cnt, 0, 0, 0, -1, 0});
+      first = (int)smalls.size();
+    };
+    const int WC = opt.warp_chunk;
+    // Forward entries by height (leaves first), backward entries by depth (roots first):
+    // entries of one level are independent, so the CTAs holding consecutive entries can
+    // all make progress and the critical path is the tree height, not the list length.
+    std::vector<int32_t> depth(nsn, 0);
+    for (int s = nsn - 1; s >= 0; --s)
+      depth[s] = S.sn_parent[s] >= 0 ? depth[S.sn_parent[s]] + 1 : 0;
+    std::vector<int32_t> ford(nsn), bord(nsn);
+    std::iota(ford.begin(), ford.end(), 0);
+    std::iota(bord.begin(), bord.end(), 0);
+    std::stable_sort(ford.begin(), ford.end(), [&](int a, int b) { return S.level[a] < S.level[b]; });
+    std::stable_sort(bord.begin(), bord.end(), [&](int a, int b) { return depth[a] < depth[b]; });
+    // forward: per level, small supernodes (GROUP), DIAG entries, then far chunks (BULK)
+    for (size_t k0 = 0; k0 < ford.size();) {
+      size_t k1 = k0;
+      while (k1 < ford.size() && S.level[ford[k1]] == S.level[ford[k0]]) ++k1;
+      int first = (int)S.fwd_small.size();
+      for (size_t k = k0; k < k1; ++k) {
+        int s = ford[k];
+        if (!small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        SolveTask t{TASK_FUSED, s, 0, r, 0, 0, -1, 0};
         add_targets(s, 0, r, t);
-        S.fwd.push_back(t);
-      } else {
-        S.fwd.push_back(SolveTask{TASK_DIAG, s, 0, 0, 0, 0});
-        for (int r0 = 0; r0 < r; r0 += opt.solve_chunk) {
-          SolveTask t{TASK_OFF, s, r0, std::min(r, r0 + opt.solve_chunk), 0, 0};
+        S.fwd_small.push_back(t);
+        if ((int)S.fwd_small.size() - first == 8) flush(S.fwd, S.fwd_small, first, TASK_GROUP);
+      }
+      flush(S.fwd, S.fwd_small, first, TASK_GROUP);
+      for (size_t k = k0; k < k1; ++k) {
+        int s = ford[k];
+        if (small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        SolveTask d{TASK_DIAG, s, 0, std::min(r, CH), 0, 0, -1, 0};
+        add_targets(s, 0, d.r1, d);
+        S.fwd.push_back(d);
+      }
+      first = (int)S.fwd_small.size();
+      for (size_t k = k0; k < k1; ++k) {
+        int s = ford[k];
+        if (small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        for (int r0 = CH; r0 < r; r0 += WC) {
+          SolveTask t{TASK_OFF, s, r0, std::min(r, r0 + WC), 0, 0, -1, 0};
           add_targets(s, t.r0, t.r1, t);
-          S.fwd.push_back(t);
+          S.fwd_small.push_back(t);
+          if ((int)S.fwd_small.size() - first == 8) flush(S.fwd, S.fwd_small, first, TASK_BULK);
         }
       }
+      flush(S.fwd, S.fwd_small, first, TASK_BULK);
+      k0 = k1;
     }
-    for (int s = nsn - 1; s >= 0; --s) {  // reverse postorder: parents before children
-      int w = S.sn_start[s + 1] - S.sn_start[s];
-      int r = (int)(S.rptr[s + 1] - S.rptr[s]);
-      if ((int64_t)r * w <= opt.fused_limit) {
-        S.bwd.push_back(SolveTask{TASK_FUSED, s, 0, r, 0, 0});
-      } else {
-        for (int r0 = 0; r0 < r; r0 += opt.solve_chunk) {
-          S.bwd.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + opt.solve_chunk), 0, 0});
+    // backward: per depth, far chunks (BULK; they wait for ancestors only), then small
+    // supernodes (GROUP) and DIAG entries
+    for (size_t k0 = 0; k0 < bord.size();) {
+      size_t k1 = k0;
+      while (k1 < bord.size() && depth[bord[k1]] == depth[bord[k0]]) ++k1;
+      int first = (int)S.bwd_small.size();
+      for (size_t k = k0; k < k1; ++k) {
+        int s = bord[k];
+        if (small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        for (int r0 = CH; r0 < r; r0 += WC) {
+          int ws = S.sn_of[S.rows[S.rptr[s] + r0]];
+          S.bwd_small.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + WC), 0, 0, ws, 0});
           S.bwd_nchunk[s]++;
+          if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_BULK);
         }
-        S.bwd.push_back(SolveTask{TASK_DIAG, s, 0, 0, 0, 0});
       }
+      flush(S.bwd, S.bwd_small, first, TASK_BULK);
+      for (size_t k = k0; k < k1; ++k) {
+        int s = bord[k];
+        if (!small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        S.bwd_small.push_back(SolveTask{TASK_FUSED, s, 0, r, 0, 0, S.sn_parent[s], 0});
+        if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_GROUP);
+      }
+      flush(S.bwd, S.bwd_small, first, TASK_GROUP);
+      for (size_t k = k0; k < k1; ++k) {
+        int s = bord[k];
+        if (small(s)) continue;
+        int r = (int)(S.rptr[s + 1] - S.rptr[s]);
+        S.bwd.push_back(SolveTask{TASK_DIAG, s, 0, std::min(r, CH), 0, 0, S.sn_parent[s], 0});
+      }
+      k0 = k1;
     }
+    // descriptors: everything a task needs in one record
+    auto fill = [&](SolveTask& t, bool fwd) {
+      if (t.kind == TASK_GROUP || t.kind == TASK_BULK) return;
+      int s = t.sn;
+      t.c0 = S.sn_start[s];
+      t.w = S.sn_start[s + 1] - t.c0;
+      t.r = (int32_t)(S.rptr[s + 1] - S.rptr[s]);
+      t.d_off = S.d_off[s];
+      t.o_off = S.o_off[s];
+      t.row_off = S.rptr[s];
+      if (fwd) t.wait_cnt = (t.kind == TASK_OFF) ? 1 : S.fwd_expect[s];
+      else t.wait_cnt = (t.kind == TASK_DIAG) ? S.bwd_nchunk[s] : 0;
+    };
+    for (auto& t : S.fwd) fill(t, true);
+    for (auto& t : S.fwd_small) fill(t, true);
+    for (auto& t : S.bwd) fill(t, false);
+    for (auto& t : S.bwd_small) fill(t, false);
   }
   return "";
 }

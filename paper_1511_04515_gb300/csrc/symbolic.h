@@ -11,21 +11,33 @@
 namespace ers {
 
 struct SymbolicOptions {
-  int leaf_size = 64;        // nested-dissection parts at or below this size get minimum degree
+  int leaf_size = 32;        // nested-dissection parts at or below this size get minimum degree
   int max_width = 64;        // supernode width cap (columns)
-  int relax_zeros = 0;       // reserved: relaxed amalgamation (0 = fundamental supernodes)
-  int solve_chunk = 256;     // rows per off-diagonal solve task of a large supernode
-  int fused_limit = 2048;    // r*w at or below which one task does a supernode's whole solve
+  int relax_zeros = 20;      // relaxed amalgamation: max % explicit zeros (0 = fundamental only)
+  int relax_width = 16;      // merged supernodes up to this width are accepted regardless
+  int solve_chunk = 64;      // rows of the near chunk done by a large supernode's DIAG task
+  int warp_chunk = 32;       // rows of a far chunk (one warp; 8 chunks per BULK entry)
+  int fused_limit = 2048;    // w*(w+r) at or below which one warp does a supernode's solve
 };
 
-// Task of the warp-granular triangular-solve kernels.
-enum TaskKind : int32_t { TASK_FUSED = 0, TASK_DIAG = 1, TASK_OFF = 2 };
+// Work entry of the triangular-solve kernels.  A CTA takes one entry at a time:
+//   GROUP : up to 8 small supernodes (a..a+b-1 in the small-task list), one per warp;
+//   DIAG  : a large supernode's diagonal block plus its nearest row chunk [0, r1);
+//   OFF   : a further row chunk [r0, r1) of a large supernode (one warp);
+//   BULK  : up to 8 OFF chunks (a..a+b-1 in the chunk list), one per warp.
+enum TaskKind : int32_t { TASK_FUSED = 0, TASK_DIAG = 1, TASK_OFF = 2, TASK_GROUP = 3,
+                          TASK_BULK = 4 };
 
 struct SolveTask {
   int32_t kind;
-  int32_t sn;
-  int32_t r0, r1;       // row range inside R_off(sn) (OFF tasks; FUSED: 0..r)
+  int32_t sn;           // supernode (GROUP: first small task index)
+  int32_t r0, r1;       // row range inside R_off(sn) (GROUP: r0 = count)
   int32_t tgt0, ntgt;   // distinct target supernodes of the rows (forward counters)
+  int32_t wait_sn;      // backward: supernode whose completion the task waits for
+  int32_t wait_cnt;     // forward DIAG/FUSED: arrivals expected; backward DIAG: far chunks
+  int32_t c0, w, r;     // the supernode's first column, width and off-diagonal row count
+  int32_t pad;
+  int64_t d_off, o_off, row_off;  // offsets of its diagonal block, panels and row list
 };
 
 struct Symbolic {
@@ -70,10 +82,11 @@ struct Symbolic {
   std::vector<int32_t> ptask_ptr;  // nlevels+1
   std::vector<int32_t> ptask_sn, ptask_r0;
   // triangular solve tasks
-  std::vector<SolveTask> fwd, bwd;
+  std::vector<SolveTask> fwd, bwd;       // CTA entries, topological order
+  std::vector<SolveTask> fwd_small, bwd_small;  // warp tasks referenced by GROUP/BULK entries
   std::vector<int32_t> fwd_tgt;    // target lists of forward tasks
   std::vector<int32_t> fwd_expect; // nsn : units that scatter into each supernode
-  std::vector<int32_t> bwd_nchunk; // nsn : OFF tasks of each supernode in the backward solve
+  std::vector<int32_t> bwd_nchunk; // nsn : far OFF chunks of each supernode (backward)
   // statistics
   int64_t nnz_L = 0;               // including the diagonal
   double flops = 0.0;              // refactor flops

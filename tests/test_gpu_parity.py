@@ -7,10 +7,11 @@ test) and to the 32x32 RC mesh at the config's fixed m = 20.  When a fixed m exc
 dimension at which the Krylov space has converged, the last directions are rounding noise of
 the G_k solves and two correct FP64 implementations differ by as much as the algorithm's own
 rounding sensitivity.  Those cases use the derived bar
-    max(1e-9, 100 * s),  s = per-node change of the oracle's step when every one of its solves
-                             is perturbed by 1e-13 relative noise,
-where 100 covers the ratio between the real difference of two backward-stable LU solves
-(cond(G_k) * eps ~ 1e-11 .. 1e-10 here) and the 1e-13 probe."""
+    max(1e-9, s * cond(G_k) * eps / 1e-13),
+    s = per-node change of the oracle's step when every one of its solves is perturbed by
+        1e-13 relative noise (the change is linear in the noise level),
+i.e. the oracle's sensitivity scaled to the size of the difference between two
+backward-stable LU solves, cond(G_k) * eps."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -250,7 +251,9 @@ def test_er_step_nonlinear_fixed_m(ers, m):
     x = x0.copy()
     for k in range(4):
         ref = O.er_step(circ, x, t, 1e-12, m=m)
-        bar = max(REL, 100 * oracle_floor(circ, x, t, 1e-12, m))
+        lin = O.linearize(circ, x)
+        scale = np.linalg.cond(lin.Gk.toarray()) * np.finfo(float).eps / 1e-13
+        bar = max(REL, oracle_floor(circ, x, t, 1e-12, m) * scale)
         sim.set_state(t, x)
         mu, err = sim.step(1e-12, m)
         _, xg, _ = sim.state()
