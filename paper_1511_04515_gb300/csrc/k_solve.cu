@@ -17,6 +17,9 @@
 //                        supernode finishes only after its parent, so a unit waits for the
 //                        lowest supernode its rows touch; x_s <- U11^-1 (y_s - U12 x_R).
 // NRHS right-hand sides (stride n) share each pass over the factors.
+#include <mutex>
+#include <string>
+
 #include "ers_internal.h"
 #include "kcommon.cuh"
 
@@ -649,3 +652,107 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
 }
 
 }  // namespace ers
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free solve (no counterpart in the paper: a deployment convenience).
+//
+// Some callers cannot allocate device memory at the point where they need a solve: code
+// recording a CUDA stream capture (an allocation inside the capture would break it or be
+// replayed wrongly), frameworks whose device memory belongs to their own pool allocator,
+// and latency-bound loops that forbid allocator calls.  ers_solve_dev_noalloc serves them:
+// it runs the same forward/backward kernels as every other solve, but the kernels'
+// scratch (the dependency counters and flags, 2 + 3 * nsn ints) lives in the file-scope
+// array below instead of the context's own buffer.  The array is a fixed 6 MiB that every
+// GPU loading this library keeps until the process exits; contexts with more than
+// NOALLOC_MAX_SN supernodes are rejected.  All calls on a device share the one array, so
+// calls whose solves overlap on the GPU race; the counters are cleared at each call.
+// ---------------------------------------------------------------------------------------
+namespace ers {
+
+constexpr int NOALLOC_MAX_SN = 1 << 19;
+static __device__ __align__(256) int32_t g_noalloc_sync[2 + 3 * NOALLOC_MAX_SN];
+
+__global__ void k_gather_perm(int n, const int32_t* perm, const double* src, double* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+__global__ void k_scatter_perm(int n, const int32_t* perm, const double* src, double* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[perm[i]] = src[i];
+}
+
+// Device address of g_noalloc_sync on the current device, looked up once per device.
+static int32_t* noalloc_scratch(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static int32_t* addr[128] = {};
+  *err = cudaSuccess;
+  if (device < 0 || device >= 128) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[device]) {
+    int32_t* p = nullptr;
+    *err = cudaGetSymbolAddress((void**)&p, g_noalloc_sync);
+    if (*err != cudaSuccess) return nullptr;
+    addr[device] = p;
+  }
+  return addr[device];
+}
+
+}  // namespace ers
+
+extern "C" ers_status ers_solve_dev_noalloc(ers_ctx* c, const double* b_dev, double* x_dev) {
+  using namespace ers;
+  if (!c) return ERS_ERR_INVALID;
+  if (!b_dev || !x_dev) {
+    c->err = "ers_solve_dev_noalloc: b_dev and x_dev must be device pointers";
+    return ERS_ERR_INVALID;
+  }
+  if (c->plan.nsn > NOALLOC_MAX_SN) {
+    c->err = "ers_solve_dev_noalloc: the factor has " + std::to_string(c->plan.nsn) +
+             " supernodes, more than the allocation-free limit of " +
+             std::to_string(NOALLOC_MAX_SN);
+    return ERS_ERR_INVALID;
+  }
+  if (!c->factored) {
+    c->err = "ers_solve_dev_noalloc: no factorisation of G_k yet (call ers_refactor first)";
+    return ERS_ERR_INVALID;
+  }
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != c->device) e = cudaSetDevice(c->device);
+  int32_t* scratch = nullptr;
+  if (e == cudaSuccess) scratch = noalloc_scratch(c->device, &e);
+  auto cuda_fail = [&](cudaError_t err) {
+    c->err = std::string("ers_solve_dev_noalloc: ") + cudaGetErrorString(err);
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    return ERS_ERR_CUDA;
+  };
+  if (e != cudaSuccess) return cuda_fail(e);
+  DevicePlan P = c->plan;
+  P.sync = scratch;
+  const int n = c->n;
+  const int nb = (n + 255) / 256;
+  e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(scratch, 0, sizeof(int32_t) * (2 + 3 * (size_t)P.nsn), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  k_gather_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, b_dev, c->solve_buf);
+  SolveArgs A{P, c->solve_buf, n, c->d_status};
+  launch_pair<1>(c, A, c->sm_count * 3);
+  k_scatter_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, c->solve_buf, x_dev);
+  c->stats.kernel_launches += 4;
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+  if (c->h_status[0] & ST_TIMEOUT) {
+    c->err = "ers_solve_dev_noalloc: device wait timed out";
+    return ERS_ERR_TIMEOUT;
+  }
+  return ERS_OK;
+}

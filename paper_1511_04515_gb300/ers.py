@@ -67,7 +67,8 @@ class Stats(C.Structure):
 EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_refactor",
            "ers_step", "ers_run", "ers_get_state", "ers_set_state", "ers_get_state_dev",
            "ers_set_state_dev", "ers_solve", "ers_spmv_C", "ers_mevp", "ers_phi_small",
-           "ers_stats", "ers_profile", "ers_analyze", "ers_last_error", "ers_destroy"]
+           "ers_stats", "ers_profile", "ers_analyze", "ers_last_error", "ers_destroy",
+           "ers_solve_dev_noalloc"]
 
 _lib = None
 
@@ -102,6 +103,7 @@ def lib():
         "ers_phi_small": ([P, pd, I32, I32, D, pd, pd], C.c_int),
         "ers_stats": ([P, C.POINTER(Stats)], C.c_int),
         "ers_profile": ([P, I32], C.c_int),
+        "ers_solve_dev_noalloc": ([P, P, P], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
         "ers_last_error": ([P], C.c_char_p),
         "ers_destroy": ([P], None),
@@ -270,6 +272,10 @@ class Simulator:
         x = np.zeros(self.n)
         self._check(lib().ers_solve(self._ctx, _dptr(b), _dptr(x)))
         return x
+
+    def solve_dev_noalloc(self, b_ptr: int, x_ptr: int):
+        """x = G_k^-1 b on device buffers without any device allocation (see ers.h)."""
+        self._check(lib().ers_solve_dev_noalloc(self._ctx, C.c_void_p(b_ptr), C.c_void_p(x_ptr)))
 
     def spmv_C(self, v):
         v = np.ascontiguousarray(v, np.float64)
