@@ -204,9 +204,11 @@ def run_ours(a):
     proc, fh = clocks_start(local, clk_path)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("ers_timed")
     e0.record(stream)
     ns, nr = sim.run(t_end, a.tol, max_steps=a.steps)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
