@@ -96,6 +96,17 @@ typedef struct {
   double solve_fma_per_rhs;    /* FP64 FMAs of one solve pair per right-hand side     */
 } ers_stats_t;
 
+/* One circuit of a batch (ers_create_batch): the same data ers_create takes. */
+typedef struct {
+  const ers_csr* G;            /* n x n linear conductances */
+  const ers_csr* C;            /* n x n capacitances        */
+  const ers_csr* B;            /* n x p source incidence    */
+  const ers_mosfet* dev;       /* ndev devices (may be NULL if ndev = 0) */
+  int32_t ndev;
+  const ers_pwl* u;            /* p PWL inputs */
+  int32_t p;
+} ers_instance;
+
 /* Fill opts with the defaults listed above. */
 ers_status ers_default_opts(ers_opts* opts);
 
@@ -107,6 +118,25 @@ ers_status ers_default_opts(ers_opts* opts);
 ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, const ers_csr* B,
                       const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
                       const ers_opts* opts);
+
+/* Batched context over ninst independent circuits (Monte Carlo corners, parameter sweeps;
+ * the paper simulates one circuit at a time).  The instances are concatenated into one
+ * block-diagonal circuit: one symbolic analysis, one refactor and one solve pass per step
+ * cover all of them, while Algorithm 1 and 2 run per instance (own Krylov spaces and
+ * dimensions, step sizes, times, PWL corners and error tests).  State access: ers_dc,
+ * ers_set_state / ers_get_state act on the concatenated vector (instance k's nodes follow
+ * instance k-1's); ers_get_state_inst reads one instance. */
+ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
+                            const ers_opts* opts);
+
+/* Advance every instance of a batched context to t_end with Algorithm 2 (at most max_steps
+ * rounds when max_steps > 0; in a round every unfinished instance takes one accepted step).
+ * nsteps / nreject (ninst entries each, may be NULL) receive the per-instance counts. */
+ers_status ers_run_batch(ers_ctx* ctx, double t_end, double tol, int32_t max_steps,
+                         int32_t* nsteps, int32_t* nreject);
+
+/* Time, state (n_k doubles, the instance's own node order) and proposed step of instance k. */
+ers_status ers_get_state_inst(const ers_ctx* ctx, int32_t k, double* t, double* x, double* h);
 
 /* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL = a private stream
  * created at ers_create).  All device work of later calls is ordered on it. */

@@ -388,6 +388,17 @@ ers_status read_m(ers_ctx* c, int slot, int* m) {
   return ERS_OK;
 }
 
+}  // namespace
+
+namespace ers {
+ers_status ctx_fail(ers_ctx* c, ers_status st, const std::string& msg) { return fail(c, st, msg); }
+ers_status ctx_refactor(ers_ctx* c) { return do_refactor(c); }
+ers_status ctx_sync_status(ers_ctx* c) { return sync_status(c); }
+ers_status ctx_clear_status(ers_ctx* c) { return clear_status(c); }
+}  // namespace ers
+
+namespace {
+
 double host_absmax(ers_ctx* c, const double* x, ers_status* st) {
   unsigned long long* mx = (unsigned long long*)(c->red + 2 * MAX_RHS * 4096 + 72);
   cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream);
@@ -467,13 +478,14 @@ static ers_status build_union(ers_ctx* c, const ers_csr* G, const ers_mosfet* de
   return ERS_OK;
 }
 
-ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const ers_csr* B,
-                      const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
-                      const ers_opts* opts) {
-  if (!out) return ERS_ERR_INVALID;
-  *out = nullptr;
-  ers_ctx* c = new ers_ctx();
-  auto bail = [&](ers_status st) { *out = c; return st; };
+}  // extern "C"
+
+// Everything ers_create does, on a context the caller allocated (also used for batches,
+// whose instances arrive here concatenated into one block-diagonal circuit).
+ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, const ers_csr* B,
+                               const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
+                               const ers_opts* opts) {
+  auto bail = [&](ers_status st) { return st; };
   if (!G) return bail(fail(c, ERS_ERR_INVALID, "G_lin is NULL"));
   int n = G->n_rows;
   if (n <= 0) return bail(fail(c, ERS_ERR_INVALID, "n must be positive"));
@@ -713,8 +725,18 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const e
     c->stats.solve_fma_per_rhs = diag + off;
     c->stats.solve_bytes_per_pass = 8.0 * (diag + off) + 8.0 * rows + 4.0 * 2.0 * S.nsn;
   }
-  *out = c;
   return ERS_OK;
+}
+
+extern "C" {
+
+ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const ers_csr* B,
+                      const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
+                      const ers_opts* opts) {
+  if (!out) return ERS_ERR_INVALID;
+  ers_ctx* c = new ers_ctx();
+  *out = c;
+  return ers::create_context(c, G, C, B, dev, ndev, u, p, opts);
 }
 
 ers_status ers_set_stream(ers_ctx* c, void* stream) {
@@ -912,6 +934,8 @@ ers_status ers_set_state(ers_ctx* c, double t, const double* x, double h) {
   CU(cudaStreamSynchronize(c->stream));
   c->t = t;
   c->h = h;
+  std::fill(c->t_inst.begin(), c->t_inst.end(), t);
+  std::fill(c->hprop_inst.begin(), c->hprop_inst.end(), h);
   if (!c->linear) c->factored = false;
   return ERS_OK;
 }
@@ -1090,7 +1114,9 @@ void ers_destroy(ers_ctx* c) {
                   (void*)c->x, (void*)c->xk, (void*)c->xnew, (void*)c->F, (void*)c->rhs,
                   (void*)c->v1, (void*)c->w1, (void*)c->v2, (void*)c->ve, (void*)c->tmp,
                   (void*)c->solve_buf, (void*)c->V, (void*)c->H, (void*)c->ks, (void*)c->red,
-                  (void*)c->d_status, (void*)c->d_perm})
+                  (void*)c->d_status, (void*)c->d_perm, (void*)c->d_inst_of, (void*)c->d_seg_off,
+                  (void*)c->d_src_inst, (void*)c->bks, (void*)c->bH, (void*)c->bh, (void*)c->bt,
+                  (void*)c->bred, (void*)c->bmask, (void*)c->bcount})
     f(p);
   for (auto& ev : c->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }

@@ -1,0 +1,667 @@
+// Batched ER transient: many independent circuit instances (Monte Carlo corners, parameter
+// sweeps) in one context.  The instances are concatenated into one block-diagonal circuit, so
+// the device evaluation, the refactor of G_k (Alg. 2) and every supernodal solve pass cover
+// all instances in one launch each.  Everything that Algorithm 1 and 2 decide per circuit is
+// per instance: inner products and norms are segmented (the nested-dissection order keeps an
+// instance's nodes contiguous), every instance has its own Krylov spaces, dimension, step size,
+// time, PWL corners and error test.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ers_internal.h"
+#include "kcommon.cuh"
+#include "kdense.cuh"
+
+namespace ers {
+
+void launch_dev_eval(ers_ctx* c, const double* x, double* dev_I, int with_jac);
+void launch_node_F(ers_ctx* c, int mode, const double* dev_In, const double* xn, double* out);
+cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
+                 const double* x, double* y, double alpha);
+
+constexpr int BT = 512;   // threads of the per-instance kernels
+
+__device__ __forceinline__ double pwl_at(const double* t, const double* v, int np, double x) {
+  if (x <= t[0]) return v[0];
+  if (x >= t[np - 1]) return v[np - 1];
+  int lo = 0, hi = np - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (t[mid] <= x) lo = mid; else hi = mid;
+  }
+  return v[lo] + (x - t[lo]) / (t[hi] - t[lo]) * (v[hi] - v[lo]);
+}
+
+// per source: u = u(t_inst), slope = (u(t_inst + h_inst) - u) / h_inst (0 for idle instances)
+__global__ void k_bpwl(int p, const int32_t* ptr, const double* tt, const double* vv,
+                       const int32_t* src_inst, const double* t_arr, const double* h_arr,
+                       const int32_t* mask, double* u, double* slope) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= p) return;
+  int i = src_inst[q];
+  int o = ptr[q], np = ptr[q + 1] - ptr[q];
+  double t = t_arr[i], h = h_arr[i];
+  double u0 = pwl_at(tt + o, vv + o, np, t);
+  u[q] = u0;
+  slope[q] = (mask[i] && h > 0.0) ? (pwl_at(tt + o, vv + o, np, t + h) - u0) / h : 0.0;
+}
+
+struct BArgs {
+  int n, ninst, nb, j, adaptive, mode;
+  int slot[MAX_RHS];
+  double* V[MAX_RHS];
+  double* src[MAX_RHS];        // init: v ; mgs: solve output (overwritten by w)
+  KrylovState* ks;             // 3 * ninst
+  double* H;                   // 3 * ninst * (MAX_M+1) * MAX_M
+  const int32_t* seg;          // 2 * ninst: [start, end) of each instance
+  const int32_t* mask;         // ninst
+  const double* h;             // ninst
+  const int32_t *Gp, *Gi;
+  const double* Gv;
+  double eps;
+  int m_min, m_max;
+  unsigned* status;
+  PadeCoef pade;
+};
+
+__device__ __forceinline__ double* bH_of(const BArgs& A, int slot, int i) {
+  return A.H + ((int64_t)slot * A.ninst + i) * (MAX_M + 1) * MAX_M;
+}
+
+// ||G u||^2 over the rows of one segment
+__device__ __forceinline__ double seg_gnorm2(const BArgs& A, const double* u, int s0, int s1) {
+  double acc = 0.0;
+  for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+    double s = 0.0;
+    for (int e = A.Gp[i]; e < A.Gp[i + 1]; ++e) s += A.Gv[e] * u[A.Gi[e]];
+    acc += s * s;
+  }
+  return acc;
+}
+
+// beta = ||v_seg||, v_1 = v / beta, ||G v_1|| per (instance, space): one CTA each
+__global__ void __launch_bounds__(BT) k_binit(BArgs A) {
+  __shared__ double sh[BT / 32];
+  const int i = blockIdx.x, b = blockIdx.y, slot = A.slot[b];
+  KrylovState& K = A.ks[slot * A.ninst + i];
+  const int s0 = A.seg[2 * i], s1 = A.seg[2 * i + 1];
+  if (!A.mask[i]) {
+    if (threadIdx.x == 0) { K.beta = 0.0; K.done = 1; K.m = 0; K.built = 0; K.breakdown = 0; }
+    return;
+  }
+  const double* v = A.src[b];
+  double* V0 = A.V[b];
+  double acc = 0.0;
+  for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) acc += v[e] * v[e];
+  double beta = sqrt(block_sum(acc, sh));
+  double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) V0[e] = v[e] * inv;
+  double gv1 = 0.0;
+  if (A.adaptive) {
+    __syncthreads();
+    gv1 = sqrt(block_sum(seg_gnorm2(A, V0, s0, s1), sh));
+  }
+  if (threadIdx.x == 0) {
+    K.beta = beta;
+    K.gv1 = gv1;
+    K.built = 0;
+    K.m = 0;
+    K.best_m = 0;
+    K.best_res = INFINITY;
+    K.res = INFINITY;
+    K.breakdown = 0;
+    K.done = (beta > 0.0 && isfinite(beta)) ? 0 : 1;
+    if (!isfinite(beta)) atomicOr(A.status, ST_NONFINITE);
+  }
+}
+
+// modified Gram-Schmidt of w = -x (solve output) against v_1..v_{j+1} of one (instance, space)
+__global__ void __launch_bounds__(BT) k_bmgs(BArgs A) {
+  __shared__ double sh[BT / 32];
+  const int i = blockIdx.x, b = blockIdx.y, slot = A.slot[b];
+  KrylovState& K = A.ks[slot * A.ninst + i];
+  if (!A.mask[i] || K.done) return;
+  const int s0 = A.seg[2 * i], s1 = A.seg[2 * i + 1], n = A.n, j = A.j;
+  double* w = A.src[b];
+  const double* V = A.V[b];
+  double* H = bH_of(A, slot, i);
+  const int ldh = MAX_M + 1;
+  double nn = 0.0, dd = 0.0;
+  for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+    double x = -w[e];
+    w[e] = x;
+    nn += x * x;
+    dd += x * V[e];
+  }
+  double w0 = sqrt(block_sum(nn, sh));
+  double hcur = block_sum(dd, sh);
+  if (threadIdx.x == 0) H[0 + j * ldh] = hcur;
+  for (int it = 0; it <= j; ++it) {
+    const double* vi = V + (int64_t)it * n;
+    const double* vn = V + (int64_t)(it + 1) * n;
+    double acc = 0.0;
+    for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) {
+      double x = w[e] - hcur * vi[e];
+      w[e] = x;
+      acc += (it < j) ? x * vn[e] : x * x;
+    }
+    hcur = block_sum(acc, sh);
+    if (it < j && threadIdx.x == 0) H[(it + 1) + j * ldh] = hcur;
+  }
+  double hn = sqrt(hcur);
+  bool bd = !(hn > 1e-12 * w0);
+  double* vn = const_cast<double*>(V) + (int64_t)(j + 1) * n;
+  if (!bd) {
+    double inv = 1.0 / hn;
+    for (int e = s0 + threadIdx.x; e < s1; e += blockDim.x) vn[e] = w[e] * inv;
+  }
+  double gn = 0.0;
+  if (A.adaptive && !bd) {
+    __syncthreads();
+    gn = sqrt(block_sum(seg_gnorm2(A, vn, s0, s1), sh));
+  }
+  if (threadIdx.x == 0) {
+    H[(j + 1) + j * ldh] = hn;
+    K.w0 = w0;
+    K.built = j + 1;
+    K.gvnext[j] = gn;
+    if (!isfinite(hn)) atomicOr(A.status, ST_NONFINITE);
+    if (bd) { K.breakdown = 1; K.done = 1; K.m = j + 1; }
+  }
+}
+
+// Algorithm 1's dimension decision / exp(h_i H^-1) e_1 per (instance, space)
+__global__ void k_bsmall(BArgs A) {
+  extern __shared__ double smem[];
+  __shared__ int ipiv[MAX_M];
+  __shared__ double ybuf[MAX_M];
+  __shared__ double s_last;
+  const int i = blockIdx.x % A.ninst, b = blockIdx.x / A.ninst, slot = A.slot[b];
+  if (!A.mask[i]) return;
+  small_decide(A.mode, bH_of(A, slot, i), A.ks[slot * A.ninst + i], A.h[i], A.eps, A.m_min,
+               A.m_max, smem, ipiv, ybuf, &s_last, A.status, A.pade);
+}
+
+// how many (instance, space) pairs of the group are still iterating
+__global__ void k_bcount(BArgs A, int32_t* out) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < A.ninst * A.nb; q += blockDim.x) {
+    int i = q % A.ninst, b = q / A.ninst;
+    if (A.mask[i] && !A.ks[A.slot[b] * A.ninst + i].done) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *out = cnt;
+}
+
+// out[e] = a in[e] + sum_b c_b beta_{b,i} V_b (y_{b,i} - e_1)[e] + hfac * h_i * u0[e]
+// for the nodes e of instances i with mask[i] set (other nodes keep their value)
+struct BCombine {
+  int n, ninst, nb;
+  double* out;
+  const double* in;
+  double a;
+  const double* V[MAX_RHS];
+  int slot[MAX_RHS];
+  double c[MAX_RHS];
+  const KrylovState* ks;
+  const double* u0;
+  double hfac;
+  const double* h;
+  const int32_t* inst_of;
+  const int32_t* mask;
+};
+
+__global__ void __launch_bounds__(256) k_bcombine(BCombine A) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = A.inst_of[e];
+    if (!A.mask[i]) continue;
+    double v = A.in ? A.a * A.in[e] : 0.0;
+    for (int b = 0; b < A.nb; ++b) {
+      const KrylovState& K = A.ks[A.slot[b] * A.ninst + i];
+      int m = K.beta > 0.0 ? K.m : 0;
+      if (m == 0) continue;
+      const double* Vb = A.V[b];
+      double acc = (K.y[0] - 1.0) * Vb[e];
+      for (int k = 1; k < m; ++k) acc += K.y[k] * Vb[(int64_t)k * A.n + e];
+      v += A.c[b] * K.beta * acc;
+    }
+    if (A.u0) v += A.hfac * A.h[i] * A.u0[e];
+    A.out[e] = v;
+  }
+}
+
+// out[i] = max |x| over the nodes of instance i (0 when mask[i] is clear)
+__global__ void __launch_bounds__(256) k_bmax(int ninst, const int32_t* seg, const int32_t* mask,
+                                            const double* x, double* out) {
+  __shared__ double sh[8];
+  int i = blockIdx.x;
+  double mx = 0.0;
+  if (mask == nullptr || mask[i])
+    for (int e = seg[2 * i] + threadIdx.x; e < seg[2 * i + 1]; e += blockDim.x) {
+      double v = fabs(x[e]);
+      mx = isfinite(v) ? fmax(mx, v) : INFINITY;
+    }
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) out[i] = mx;
+}
+
+__global__ void k_bcopy(int n, const int32_t* inst_of, const int32_t* mask, const double* src,
+                        double* dst) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n && mask[inst_of[e]]) dst[e] = src[e];
+}
+
+__global__ void k_brhs_C(int n, int nv, const int32_t* ptr, const int32_t* idx,
+                         const double* val, const double* x0, const double* x1, const double* x2,
+                         double* y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* xs[3] = {x0, x1, x2};
+  for (int v = 0; v < nv; ++v) {
+    double acc = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * xs[v][idx[e]];
+    y[(int64_t)v * n + i] = acc;
+  }
+}
+
+__global__ void k_bbu(int n, const int32_t* ptr, const int32_t* idx, const double* val,
+                      const double* u, const double* F, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = F ? F[i] : 0.0;
+  for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * u[idx[e]];
+  out[i] = acc;
+}
+
+__global__ void k_bsub(int n, double* out, const double* x, const double* y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] - y[i];
+}
+
+}  // namespace ers
+
+using namespace ers;
+
+namespace {
+
+inline int nblk(int n, int b = 256) { return std::max(1, (n + b - 1) / b); }
+
+#define BCU(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return ctx_fail(c, e_ == cudaErrorMemoryAllocation ? ERS_ERR_OOM : ERS_ERR_CUDA,   \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+BArgs make_bargs(ers_ctx* c, int nb, const int* slots, double* const* src, int adaptive) {
+  BArgs A{};
+  A.n = c->n;
+  A.ninst = c->ninst;
+  A.nb = nb;
+  A.adaptive = adaptive;
+  for (int b = 0; b < nb; ++b) {
+    A.slot[b] = slots[b];
+    A.V[b] = c->V + (size_t)slots[b] * (MAX_M + 1) * c->n;
+    A.src[b] = src ? src[b] : nullptr;
+  }
+  A.ks = c->bks;
+  A.H = c->bH;
+  A.seg = c->d_seg_off;
+  A.mask = c->bmask;
+  A.h = c->bh;
+  A.Gp = c->G_ptr;
+  A.Gi = c->G_idx;
+  A.Gv = c->G_val;
+  A.eps = c->opts.eps_krylov;
+  A.m_min = c->opts.m_min;
+  A.m_max = c->opts.m_max;
+  A.status = c->d_status;
+  A.pade = pade_coefficients();
+  return A;
+}
+
+ers_status launch_bsmall(ers_ctx* c, BArgs A, int mode) {
+  A.mode = mode;
+  size_t mm = (size_t)c->opts.m_max;
+  size_t sm = (6 * mm * mm + 2 * mm) * 8;
+  k_bsmall<<<c->ninst * A.nb, 256, sm, c->stream>>>(A);
+  c->stats.kernel_launches++;
+  BCU(cudaGetLastError());
+  return ERS_OK;
+}
+
+// Algorithm 1 up to the MEVP for the spaces `slots` of every masked instance (adaptive m)
+ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src) {
+  const int mc = c->opts.m_max;
+  BArgs A = make_bargs(c, nb, slots, src, 1);
+  k_binit<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(A);
+  c->stats.kernel_launches++;
+  for (int j = 0; j < mc; ++j) {
+    if (j > 0) {
+      k_bcount<<<1, 256, 0, c->stream>>>(A, c->bcount);
+      int32_t cnt = 0;
+      BCU(cudaMemcpyAsync(&cnt, c->bcount, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+      BCU(cudaStreamSynchronize(c->stream));
+      c->stats.kernel_launches++;
+      if (cnt == 0) break;
+    }
+    double* V[3] = {A.V[0], nb > 1 ? A.V[1] : nullptr, nb > 2 ? A.V[2] : nullptr};
+    k_brhs_C<<<nblk(c->n), 256, 0, c->stream>>>(c->n, nb, c->C_ptr, c->C_idx, c->C_val,
+                                                 V[0] + (size_t)j * c->n,
+                                                 V[1] ? V[1] + (size_t)j * c->n : nullptr,
+                                                 V[2] ? V[2] + (size_t)j * c->n : nullptr,
+                                                 c->solve_buf);
+    c->stats.kernel_launches++;
+    BCU(launch_solve(c, c->solve_buf, nb));
+    BArgs M = A;
+    M.j = j;
+    for (int b = 0; b < nb; ++b) M.src[b] = c->solve_buf + (size_t)b * c->n;
+    k_bmgs<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(M);
+    c->stats.kernel_launches++;
+    c->stats.krylov_vectors += (int64_t)nb * c->ninst;
+    ers_status st = launch_bsmall(c, A, SMALL_RESID);
+    if (st != ERS_OK) return st;
+  }
+  return ERS_OK;
+}
+
+double next_bp(const std::vector<double>& bp, double t) {
+  auto it = std::upper_bound(bp.begin(), bp.end(), t * (1 + 1e-14) + 1e-30);
+  return it == bp.end() ? INFINITY : *it;
+}
+
+}  // namespace
+
+extern "C" {
+
+ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
+                            const ers_opts* opts) {
+  if (!out) return ERS_ERR_INVALID;
+  ers_ctx* c = new ers_ctx();
+  *out = c;
+  if (!inst || ninst < 1) return ctx_fail(c, ERS_ERR_INVALID, "need at least one instance");
+  // concatenate the instances into one block-diagonal circuit
+  std::vector<int32_t> gp{0}, gi, cp{0}, ci, bp{0}, bi;
+  std::vector<double> gv, cv, bv;
+  std::vector<ers_mosfet> devs;
+  std::vector<ers_pwl> pw;
+  std::vector<int32_t> orig{0}, src_inst;
+  int ntot = 0, ptot = 0;
+  for (int k = 0; k < ninst; ++k) {
+    const ers_instance& I = inst[k];
+    if (!I.G || !I.C || !I.B || I.G->n_rows <= 0 || I.C->n_rows != I.G->n_rows ||
+        I.B->n_rows != I.G->n_rows || I.p < 0 || I.B->n_cols != I.p || (I.p > 0 && !I.u) ||
+        I.ndev < 0 || (I.ndev > 0 && !I.dev))
+      return ctx_fail(c, ERS_ERR_INVALID, "instance " + std::to_string(k) + " is malformed");
+    int n = I.G->n_rows;
+    auto append = [&](const ers_csr* A, int col_off, std::vector<int32_t>& P,
+                      std::vector<int32_t>& X, std::vector<double>& Vv) {
+      for (int r = 0; r < A->n_rows; ++r) {
+        for (int e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
+          X.push_back(A->colidx[e] + col_off);
+          Vv.push_back(A->val[e]);
+        }
+        P.push_back((int32_t)X.size());
+      }
+    };
+    append(I.G, ntot, gp, gi, gv);
+    append(I.C, ntot, cp, ci, cv);
+    append(I.B, ptot, bp, bi, bv);
+    for (int d = 0; d < I.ndev; ++d) {
+      ers_mosfet m = I.dev[d];
+      if (m.d >= 0) m.d += ntot;
+      if (m.g >= 0) m.g += ntot;
+      if (m.s >= 0) m.s += ntot;
+      devs.push_back(m);
+    }
+    for (int q = 0; q < I.p; ++q) {
+      pw.push_back(I.u[q]);
+      src_inst.push_back(k);
+    }
+    ntot += n;
+    ptot += I.p;
+    orig.push_back(ntot);
+  }
+  ers_csr G{ntot, ntot, (int32_t)gi.size(), gp.data(), gi.data(), gv.data()};
+  ers_csr C{ntot, ntot, (int32_t)ci.size(), cp.data(), ci.data(), cv.data()};
+  ers_csr B{ntot, ptot, (int32_t)bi.size(), bp.data(), bi.data(), bv.data()};
+  ers_status st = create_context(c, &G, &C, &B, devs.empty() ? nullptr : devs.data(),
+                                 (int32_t)devs.size(), pw.empty() ? nullptr : pw.data(), ptot,
+                                 opts);
+  if (st != ERS_OK) return st;
+  // every instance must occupy one contiguous range of the internal order
+  const Symbolic& S = c->sym;
+  c->ninst = ninst;
+  c->orig_off = orig;
+  c->seg_off.assign(ninst + 1, 0);
+  std::vector<int32_t> inst_of(ntot);
+  for (int k = 0; k < ninst; ++k) {
+    int lo = ntot, hi = -1;
+    for (int v = orig[k]; v < orig[k + 1]; ++v) {
+      lo = std::min(lo, S.iperm[v]);
+      hi = std::max(hi, S.iperm[v]);
+    }
+    if (hi - lo + 1 != orig[k + 1] - orig[k])
+      return ctx_fail(c, ERS_ERR_INVALID, "internal: instance nodes are not contiguous");
+    for (int q = lo; q <= hi; ++q) inst_of[q] = k;
+    c->seg_off[k] = lo;
+  }
+  // device segment table in instance order: [start_k, start_k + n_k)
+  std::vector<int32_t> seg_lo(ninst), seg_hi(ninst);
+  for (int k = 0; k < ninst; ++k) {
+    seg_lo[k] = c->seg_off[k];
+    seg_hi[k] = c->seg_off[k] + (orig[k + 1] - orig[k]);
+  }
+  // kernels take seg[i], seg[i+1]: store as pairs (2 ninst ints) via an interleaved table
+  std::vector<int32_t> segtab(2 * ninst);
+  for (int k = 0; k < ninst; ++k) { segtab[2 * k] = seg_lo[k]; segtab[2 * k + 1] = seg_hi[k]; }
+  c->bp_inst.assign(ninst, {});
+  for (int q = 0; q < ptot; ++q) {
+    int k = src_inst[q];
+    for (int a = 0; a < pw[q].npts; ++a) c->bp_inst[k].push_back(pw[q].t[a]);
+  }
+  for (auto& v : c->bp_inst) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  c->t_inst.assign(ninst, 0.0);
+  c->hprop_inst.assign(ninst, 0.0);
+  c->steps_inst.assign(ninst, 0);
+  c->rejects_inst.assign(ninst, 0);
+  auto up = [&](auto** dst, const auto& v) -> cudaError_t {
+    using T = typename std::decay<decltype(v[0])>::type;
+    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, v.size()) * sizeof(T));
+    if (e == cudaSuccess && !v.empty())
+      e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+  };
+  BCU(up(&c->d_inst_of, inst_of));
+  BCU(up(&c->d_seg_off, segtab));
+  BCU(up(&c->d_src_inst, src_inst));
+  BCU(cudaMalloc((void**)&c->bks, sizeof(KrylovState) * 3 * (size_t)ninst));
+  BCU(cudaMemset(c->bks, 0, sizeof(KrylovState) * 3 * (size_t)ninst));
+  BCU(cudaMalloc((void**)&c->bH, sizeof(double) * 3 * (size_t)ninst * (MAX_M + 1) * MAX_M));
+  BCU(cudaMemset(c->bH, 0, sizeof(double) * 3 * (size_t)ninst * (MAX_M + 1) * MAX_M));
+  BCU(cudaMalloc((void**)&c->bh, sizeof(double) * ninst));
+  BCU(cudaMalloc((void**)&c->bt, sizeof(double) * ninst));
+  BCU(cudaMalloc((void**)&c->bred, sizeof(double) * ninst));
+  BCU(cudaMalloc((void**)&c->bmask, sizeof(int32_t) * ninst));
+  BCU(cudaMalloc((void**)&c->bcount, sizeof(int32_t)));
+  BCU(cudaFuncSetAttribute(k_bsmall, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
+  return ERS_OK;
+}
+
+ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps,
+                         int32_t* nsteps, int32_t* nreject) {
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  if (!(tol > 0.0)) return ctx_fail(c, ERS_ERR_INVALID, "tol must be positive");
+  const int ninst = c->ninst, n = c->n;
+  const ers_opts& o = c->opts;
+  const double h_max = o.h_max > 0 ? o.h_max : t_end / 100.0;
+  std::vector<double> h(ninst), E(ninst), err(ninst), xmax(ninst);
+  std::vector<int32_t> active(ninst), trying(ninst), retries(ninst);
+  std::vector<int> landed(ninst);
+  ers_status st = ctx_clear_status(c);
+  if (st != ERS_OK) return st;
+  int round = 0;
+  std::vector<int32_t> ones(ninst, 1);
+  while (max_steps <= 0 || round < max_steps) {
+    int nact = 0;
+    for (int i = 0; i < ninst; ++i) {
+      active[i] = c->t_inst[i] < t_end * (1 - 1e-12);
+      nact += active[i];
+      if (!active[i]) { h[i] = 0.0; continue; }
+      double nb = std::min(next_bp(c->bp_inst[i], c->t_inst[i]), t_end);
+      double hp = c->hprop_inst[i] > 0 ? c->hprop_inst[i] : (o.h_init > 0 ? o.h_init : h_max);
+      h[i] = std::min(std::min(hp, h_max), nb - c->t_inst[i]);
+      landed[i] = h[i] == nb - c->t_inst[i];
+      retries[i] = 0;
+    }
+    if (nact == 0) break;
+    // error budgets from ||x_i||_inf
+    BCU(cudaMemcpyAsync(c->bmask, ones.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+    k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->x, c->bred);
+    BCU(cudaMemcpyAsync(xmax.data(), c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
+    BCU(cudaMemcpyAsync(c->bh, h.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
+    BCU(cudaMemcpyAsync(c->bt, c->t_inst.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
+    BCU(cudaMemcpyAsync(c->bmask, active.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+    BCU(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < ninst; ++i) E[i] = o.E_rr > 0 ? o.E_rr : tol * std::max(1.0, xmax[i]);
+    if (!c->factored) {
+      st = ctx_refactor(c);
+      if (st != ERS_OK) return st;
+    }
+    // setup vectors (Eq. 12-13): v1 = x - G^-1 (F + B u), w1 = G^-1 B s, v2 = G^-1 C w1
+    k_bpwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, c->d_src_inst,
+                                              c->bt, c->bh, c->bmask, c->u, c->slope);
+    std::vector<double> hs(c->p);
+    BCU(cudaMemcpyAsync(hs.data(), c->slope, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream));
+    k_bbu<<<nblk(n), 256, 0, c->stream>>>(n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F, c->solve_buf);
+    k_bbu<<<nblk(n), 256, 0, c->stream>>>(n, c->B_ptr, c->B_idx, c->B_val, c->slope, nullptr,
+                                          c->solve_buf + n);
+    BCU(cudaStreamSynchronize(c->stream));
+    bool ramp = false;
+    for (double s : hs) ramp = ramp || s != 0.0;
+    BCU(launch_solve(c, c->solve_buf, ramp ? 2 : 1));
+    k_bsub<<<nblk(n), 256, 0, c->stream>>>(n, c->v1, c->x, c->solve_buf);
+    if (ramp) {
+      BCU(cudaMemcpyAsync(c->w1, c->solve_buf + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->w1, c->solve_buf, 1.0);
+      BCU(launch_solve(c, c->solve_buf, 1));
+      BCU(cudaMemcpyAsync(c->v2, c->solve_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    c->stats.kernel_launches += 5;
+    int slots[2] = {0, 1};
+    double* src[2] = {c->v1, c->v2};
+    const int nsol = ramp ? 2 : 1;
+    st = batch_bases(c, nsol, slots, src);
+    if (st != ERS_OK) return st;
+    trying = active;
+    while (true) {
+      BCU(cudaMemcpyAsync(c->bmask, trying.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+      BCU(cudaMemcpyAsync(c->bh, h.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
+      BCombine U{};
+      U.n = n; U.ninst = ninst; U.nb = nsol; U.out = c->xnew; U.in = c->x; U.a = 1.0;
+      for (int b = 0; b < nsol; ++b) {
+        U.V[b] = c->V + (size_t)slots[b] * (MAX_M + 1) * n;
+        U.slot[b] = slots[b];
+        U.c[b] = 1.0;
+      }
+      U.ks = c->bks; U.u0 = ramp ? c->w1 : nullptr; U.hfac = 1.0; U.h = c->bh;
+      U.inst_of = c->d_inst_of; U.mask = c->bmask;
+      k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(U);
+      c->stats.kernel_launches++;
+      std::fill(err.begin(), err.end(), 0.0);
+      if (c->ndev) {
+        // e_rr = -(e^{hJ} - I) G^-1 dF per instance (Eq. 15)
+        launch_dev_eval(c, c->xnew, c->dev_I + c->ndev, 0);
+        launch_node_F(c, 1, c->dev_I + c->ndev, c->xnew, c->solve_buf);
+        BCU(launch_solve(c, c->solve_buf, 1));
+        BCU(cudaMemcpyAsync(c->ve, c->solve_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        int es = 2;
+        double* esrc[1] = {c->ve};
+        st = batch_bases(c, 1, &es, esrc);
+        if (st != ERS_OK) return st;
+        BCombine Er{};
+        Er.n = n; Er.ninst = ninst; Er.nb = 1; Er.out = c->tmp; Er.in = nullptr; Er.a = 0.0;
+        Er.V[0] = c->V + (size_t)2 * (MAX_M + 1) * n; Er.slot[0] = 2; Er.c[0] = -1.0;
+        Er.ks = c->bks; Er.u0 = nullptr; Er.h = c->bh; Er.inst_of = c->d_inst_of; Er.mask = c->bmask;
+        k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(Er);
+        k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->tmp, c->bred);
+        BCU(cudaMemcpyAsync(err.data(), c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
+        c->stats.kernel_launches += 2;
+      }
+      st = ctx_sync_status(c);
+      if (st != ERS_OK) return st;
+      int left = 0;
+      for (int i = 0; i < ninst; ++i) {
+        if (!trying[i]) continue;
+        if (err[i] <= E[i]) { trying[i] = 0; continue; }
+        h[i] *= o.alpha;
+        retries[i]++;
+        c->rejects_inst[i]++;
+        landed[i] = 0;
+        if (h[i] < o.h_min) return ctx_fail(c, ERS_ERR_STEP_UNDERFLOW, "step size underflow in instance " + std::to_string(i));
+        left++;
+      }
+      if (!left) break;
+      // rejected instances: same bases and m, exp(h H^-1) at the new h (Alg. 2)
+      BCU(cudaMemcpyAsync(c->bmask, trying.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+      BCU(cudaMemcpyAsync(c->bh, h.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
+      BArgs R = make_bargs(c, nsol, slots, nullptr, 1);
+      st = launch_bsmall(c, R, SMALL_FINAL);
+      if (st != ERS_OK) return st;
+    }
+    BCU(cudaMemcpyAsync(c->bmask, active.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+    k_bcopy<<<nblk(n), 256, 0, c->stream>>>(n, c->d_inst_of, c->bmask, c->xnew, c->x);
+    c->stats.kernel_launches++;
+    for (int i = 0; i < ninst; ++i) {
+      if (!active[i]) continue;
+      double nb = std::min(next_bp(c->bp_inst[i], c->t_inst[i]), t_end);
+      c->t_inst[i] = landed[i] ? nb : c->t_inst[i] + h[i];
+      c->steps_inst[i]++;
+      c->hprop_inst[i] = retries[i] < o.i_grow ? std::min(o.beta * h[i], h_max) : h[i];
+    }
+    if (!c->linear) c->factored = false;
+    c->stats.steps++;
+    ++round;
+  }
+  BCU(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < ninst; ++i) {
+    if (nsteps) nsteps[i] = (int32_t)c->steps_inst[i];
+    if (nreject) nreject[i] = (int32_t)c->rejects_inst[i];
+  }
+  return ERS_OK;
+}
+
+ers_status ers_get_state_inst(const ers_ctx* cc, int32_t k, double* t, double* x, double* h) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c) return ERS_ERR_INVALID;
+  if (k < 0 || k >= c->ninst) return ctx_fail(c, ERS_ERR_INVALID, "instance index out of range");
+  if (c->bks) {
+    if (t) *t = c->t_inst[k];
+    if (h) *h = c->hprop_inst[k];
+  } else {
+    if (t) *t = c->t;
+    if (h) *h = c->h;
+  }
+  if (x) {
+    int lo = c->orig_off.empty() ? 0 : c->orig_off[k];
+    int hi = c->orig_off.empty() ? c->n : c->orig_off[k + 1];
+    std::vector<double> xp(c->n);
+    BCU(cudaMemcpyAsync(xp.data(), c->x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    BCU(cudaStreamSynchronize(c->stream));
+    for (int v = lo; v < hi; ++v) x[v - lo] = xp[c->sym.iperm[v]];
+  }
+  return ERS_OK;
+}
+
+}  // extern "C"

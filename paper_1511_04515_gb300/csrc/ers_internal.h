@@ -73,6 +73,18 @@ struct DevicePlan {
 
 }  // namespace ers
 
+struct ers_ctx;
+namespace ers {
+// shared by the translation units (defined in api.cu)
+ers_status create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, const ers_csr* B,
+                          const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
+                          const ers_opts* opts);
+ers_status ctx_fail(ers_ctx* c, ers_status st, const std::string& msg);
+ers_status ctx_refactor(ers_ctx* c);
+ers_status ctx_sync_status(ers_ctx* c);
+ers_status ctx_clear_status(ers_ctx* c);
+}  // namespace ers
+
 // the opaque context of the public C ABI
 struct ers_ctx {
   std::string err;
@@ -123,6 +135,21 @@ struct ers_ctx {
   bool factored = false;             // LU of G_k valid for the current x
   bool linear = true;
   ers_stats_t stats{};
+  // batch: instances concatenated into one block-diagonal circuit (ninst = 1 otherwise)
+  int ninst = 1;
+  std::vector<int32_t> seg_off;        // ninst + 1: node ranges in the internal (permuted) order
+  std::vector<int32_t> orig_off;       // ninst + 1: node ranges in the concatenated input order
+  std::vector<std::vector<double>> bp_inst;
+  std::vector<double> t_inst, hprop_inst;
+  std::vector<int64_t> steps_inst, rejects_inst;
+  int32_t* d_inst_of = nullptr;        // n: instance of each internal node
+  int32_t* d_seg_off = nullptr;        // ninst + 1
+  int32_t* d_src_inst = nullptr;       // p: instance of each source
+  ers::KrylovState* bks = nullptr;     // 3 * ninst
+  double* bH = nullptr;                // 3 * ninst * (MAX_M + 1) * MAX_M
+  double *bh = nullptr, *bt = nullptr, *bred = nullptr;  // ninst each
+  int32_t* bmask = nullptr;            // ninst
+  int32_t* bcount = nullptr;           // 1
   // profiling of the solve kernels (CUDA events on the context's stream)
   bool profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;

@@ -14,12 +14,12 @@
 //                     optionally with max |out|.
 #include "ers_internal.h"
 #include "kcommon.cuh"
+#include "kdense.cuh"
 
 namespace ers {
 
 constexpr int KB = 256;          // threads per block of the vector kernels
 
-__constant__ double c_pade[14];  // [13/13] Pade coefficients of exp
 
 struct CoopArgs {
   int n;
@@ -193,183 +193,8 @@ __global__ void __launch_bounds__(KB) k_mgs(CoopArgs A) {
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// small dense stage
-// ---------------------------------------------------------------------------------------
-__device__ void sm_matmul(double* C, const double* A, const double* B, int m) {
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e % m, jj = e / m;
-    double acc = 0.0;
-    for (int k = 0; k < m; ++k) acc += A[i + k * m] * B[k + jj * m];
-    C[e] = acc;
-  }
-  __syncthreads();
-}
-
-// LU with partial pivoting of M (m x m, in place); piv[k] = row swapped with k.
-__device__ void sm_lu(double* M, int* piv, int m) {
-  __shared__ int s_p;
-  for (int k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
-      int p = k;
-      double best = fabs(M[k + k * m]);
-      for (int i = k + 1; i < m; ++i)
-        if (fabs(M[i + k * m]) > best) { best = fabs(M[i + k * m]); p = i; }
-      s_p = p;
-      piv[k] = p;
-    }
-    __syncthreads();
-    int p = s_p;
-    if (p != k)
-      for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
-        double t = M[k + jj * m];
-        M[k + jj * m] = M[p + jj * m];
-        M[p + jj * m] = t;
-      }
-    __syncthreads();
-    double inv = 1.0 / M[k + k * m];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] *= inv;
-    __syncthreads();
-    int rem = m - k - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      int i = k + 1 + e % rem, jj = k + 1 + e / rem;
-      M[i + jj * m] -= M[i + k * m] * M[k + jj * m];
-    }
-    __syncthreads();
-  }
-}
-
-// Solve (LU) X = B column by column in place (B: m x m); column jj by one thread.
-__device__ void sm_lu_solve(const double* LU, const int* piv, double* B, int m) {
-  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
-    double* b = B + jj * m;
-    for (int k = 0; k < m; ++k)
-      if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
-    for (int i = 1; i < m; ++i) {
-      double acc = b[i];
-      for (int k = 0; k < i; ++k) acc -= LU[i + k * m] * b[k];
-      b[i] = acc;
-    }
-    for (int i = m - 1; i >= 0; --i) {
-      double acc = b[i];
-      for (int k = i + 1; k < m; ++k) acc -= LU[i + k * m] * b[k];
-      b[i] = acc / LU[i + i * m];
-    }
-  }
-  __syncthreads();
-}
-
-// y = exp(h H^-1) e_1 for the leading m x m block of H (ld ldh); last = e_m^T H^-1 y.
-// Scaling and squaring of the diagonal [13/13] Pade approximant (theta_13 = 5.37).
-// Returns true when y and last are finite.  smem: 6 m^2 doubles + scratch.
-__device__ bool phi_small(const double* H, int ldh, int m, double h, double* y, double* last,
-                          double* smem, int* ipiv) {
-  double* M0 = smem;
-  double* M1 = M0 + m * m;
-  double* M2 = M1 + m * m;
-  double* M3 = M2 + m * m;
-  double* M4 = M3 + m * m;
-  double* M5 = M4 + m * m;
-  double* lastrow = M5 + m * m;   // m
-  double* vec = lastrow + m;      // m
-  __shared__ int s_s;
-  __shared__ double s_norm;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e % m, jj = e / m;
-    M0[e] = H[i + jj * ldh];
-    M1[e] = (i == jj) ? h : 0.0;
-  }
-  __syncthreads();
-  sm_lu(M0, ipiv, m);
-  sm_lu_solve(M0, ipiv, M1, m);          // M1 = X = h H^-1
-  for (int k = threadIdx.x; k < m; k += blockDim.x) lastrow[k] = M1[(m - 1) + k * m] / h;
-  if (threadIdx.x == 0) {
-    double nrm = 0.0;
-    for (int jj = 0; jj < m; ++jj) {
-      double cs = 0.0;
-      for (int i = 0; i < m; ++i) cs += fabs(M1[i + jj * m]);
-      nrm = fmax(nrm, cs);
-    }
-    s_norm = nrm;
-    int s = 0;
-    if (nrm > 5.371920351148152) s = (int)ceil(log2(nrm / 5.371920351148152));
-    if (!isfinite(nrm)) s = 0;
-    s_s = min(s, 1000);
-  }
-  __syncthreads();
-  int s = s_s;
-  if (!isfinite(s_norm)) {
-    if (threadIdx.x == 0) *last = NAN;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) y[k] = NAN;
-    __syncthreads();
-    return false;
-  }
-  double sc = ldexp(1.0, -s);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) M1[e] *= sc;
-  __syncthreads();
-  sm_matmul(M2, M1, M1, m);   // A2
-  sm_matmul(M3, M2, M2, m);   // A4
-  sm_matmul(M4, M3, M2, m);   // A6
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
-    M0[e] = c_pade[13] * M4[e] + c_pade[11] * M3[e] + c_pade[9] * M2[e];
-  __syncthreads();
-  sm_matmul(M5, M4, M0, m);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e % m, jj = e / m;
-    M5[e] += c_pade[7] * M4[e] + c_pade[5] * M3[e] + c_pade[3] * M2[e] + (i == jj ? c_pade[1] : 0.0);
-  }
-  __syncthreads();
-  sm_matmul(M0, M1, M5, m);   // U
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
-    M5[e] = c_pade[12] * M4[e] + c_pade[10] * M3[e] + c_pade[8] * M2[e];
-  __syncthreads();
-  sm_matmul(M1, M4, M5, m);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e % m, jj = e / m;
-    double V = M1[e] + c_pade[6] * M4[e] + c_pade[4] * M3[e] + c_pade[2] * M2[e] +
-               (i == jj ? c_pade[0] : 0.0);
-    M2[e] = V - M0[e];
-    M3[e] = V + M0[e];
-  }
-  __syncthreads();
-  sm_lu(M2, ipiv, m);
-  sm_lu_solve(M2, ipiv, M3, m);   // R = (V - U)^-1 (V + U)
-  double* R = M3;
-  double* Tm = M4;
-  for (int q = 0; q + 1 < s; ++q) {
-    sm_matmul(Tm, R, R, m);
-    double* t = R; R = Tm; Tm = t;
-  }
-  // y = R (R e_1) when s >= 1, else R e_1
-  for (int i = threadIdx.x; i < m; i += blockDim.x) vec[i] = R[i];
-  __syncthreads();
-  if (s >= 1) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double acc = 0.0;
-      for (int k = 0; k < m; ++k) acc += R[i + k * m] * vec[k];
-      y[i] = acc;
-    }
-  } else {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = vec[i];
-  }
-  __syncthreads();
-  __shared__ int s_fin;
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
-    bool fin = true;
-    for (int k = 0; k < m; ++k) {
-      acc += lastrow[k] * y[k];
-      fin = fin && isfinite(y[k]);
-    }
-    *last = acc;
-    s_fin = fin && isfinite(acc);
-  }
-  __syncthreads();
-  return s_fin;
-}
-
-
 struct SmallArgs {
+  PadeCoef pade;
   int mode;
   int nb;
   int slot[MAX_RHS];
@@ -387,86 +212,15 @@ __global__ void k_small(SmallArgs A) {
   __shared__ int ipiv[MAX_M];
   __shared__ double ybuf[MAX_M];
   __shared__ double s_last;
-  const int ldh = MAX_M + 1;
   if (A.mode == SMALL_TEST) {
-    bool fin = phi_small(A.Htest, A.ldh_test, A.m_test, A.h, ybuf, &s_last, smem, ipiv);
-    (void)fin;
+    phi_small(A.Htest, A.ldh_test, A.m_test, A.h, ybuf, &s_last, smem, ipiv, A.pade);
     for (int k = threadIdx.x; k < A.m_test; k += blockDim.x) A.y_out[k] = ybuf[k];
     if (threadIdx.x == 0) *A.last_out = s_last;
     return;
   }
   int b = blockIdx.x;
-  KrylovState& K = A.ks[A.slot[b]];
-  const double* H = A.H[b];
-  __shared__ int s_done, s_m, s_built, s_bd, s_m_in;
-  if (threadIdx.x == 0) {
-    s_done = K.done; s_m = K.m; s_built = K.built; s_bd = K.breakdown;
-    s_m_in = (K.beta > 0.0);
-  }
-  __syncthreads();
-  if (!s_m_in) return;   // zero vector: MEVP = 0
-  auto write_y = [&](int m) {
-    for (int k = threadIdx.x; k < m; k += blockDim.x) K.y[k] = ybuf[k];
-    if (threadIdx.x == 0) { K.last = s_last; K.m = m; }
-  };
-  // dimension at a breakdown: built, or built-1 when the last direction was noise
-  auto finalize_breakdown = [&]() {
-    int m = s_built;
-    bool fin = phi_small(H, ldh, m, A.h, ybuf, &s_last, smem, ipiv);
-    if (!fin && m > 1) {
-      m -= 1;
-      fin = phi_small(H, ldh, m, A.h, ybuf, &s_last, smem, ipiv);
-    }
-    if (!fin && threadIdx.x == 0) atomicOr(A.status, ST_KRYLOV);
-    write_y(m);
-  };
-  if (A.mode == SMALL_FINAL) {
-    bool fin = phi_small(H, ldh, s_m, A.h, ybuf, &s_last, smem, ipiv);
-    if (!fin && threadIdx.x == 0) atomicOr(A.status, ST_KRYLOV);
-    write_y(s_m);
-    return;
-  }
-  if (A.mode == SMALL_FIXED_END) {
-    if (s_bd) { finalize_breakdown(); return; }
-    bool fin = phi_small(H, ldh, s_built, A.h, ybuf, &s_last, smem, ipiv);
-    if (!fin && threadIdx.x == 0) atomicOr(A.status, ST_KRYLOV);
-    write_y(s_built);
-    if (threadIdx.x == 0) K.done = 1;
-    return;
-  }
-  // SMALL_RESID: called after every Arnoldi iteration in adaptive mode
-  if (s_done && !s_bd) return;   // already converged earlier
-  if (s_bd) {
-    if (s_m == s_built) { finalize_breakdown(); if (threadIdx.x == 0) K.breakdown = 2; }
-    return;
-  }
-  int jj = s_built;
-  if (jj >= A.m_min) {
-    bool fin = phi_small(H, ldh, jj, A.h, ybuf, &s_last, smem, ipiv);
-    __shared__ int s_conv;
-    if (threadIdx.x == 0) {
-      double res = H[jj + (jj - 1) * ldh] * K.gvnext[jj - 1] * fabs(s_last) / K.gv1;
-      if (!fin) res = INFINITY;
-      K.res = res;
-      if (isfinite(res) && res < K.best_res) { K.best_res = res; K.best_m = jj; }
-      s_conv = isfinite(res) && res < A.eps;
-    }
-    __syncthreads();
-    if (s_conv) {
-      write_y(jj);
-      if (threadIdx.x == 0) K.done = 1;
-      return;
-    }
-  }
-  if (jj >= A.m_max) {
-    // never converged: the dimension with the smallest finite residual
-    int m = K.best_m > 0 ? K.best_m : jj;
-    __syncthreads();
-    bool fin = phi_small(H, ldh, m, A.h, ybuf, &s_last, smem, ipiv);
-    if (!fin && threadIdx.x == 0) atomicOr(A.status, ST_KRYLOV);
-    write_y(m);
-    if (threadIdx.x == 0) K.done = 1;
-  }
+  small_decide(A.mode, A.H[b], A.ks[A.slot[b]], A.h, A.eps, A.m_min, A.m_max, smem, ipiv, ybuf,
+               &s_last, A.status, A.pade);
 }
 
 // out = a*in + sum_b c_b beta_b V_b (y_b - e_1) + d0 u0 + d1 u1; optional max|out| into
@@ -538,20 +292,6 @@ __global__ void __launch_bounds__(KB) k_absmax(int n, const double* x, unsigned 
 // host launchers
 // ---------------------------------------------------------------------------------------
 cudaError_t krylov_init_constants() {
-  // [q/q] Pade approximant of exp: c_k = (2q-k)! q! / ((2q)! k! (q-k)!), q = 13
-  double c[14];
-  const int q = 13;
-  for (int k = 0; k <= q; ++k) {
-    double v = 1.0;
-    for (int i = 1; i <= q; ++i) v *= (double)i;            // q!
-    for (int i = 1; i <= 2 * q - k; ++i) v *= (double)i;    // (2q-k)!
-    for (int i = 1; i <= 2 * q; ++i) v /= (double)i;        // (2q)!
-    for (int i = 1; i <= k; ++i) v /= (double)i;            // k!
-    for (int i = 1; i <= q - k; ++i) v /= (double)i;        // (q-k)!
-    c[k] = v;
-  }
-  cudaError_t e = cudaMemcpyToSymbol(c_pade, c, sizeof(c));
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (6 * MAX_M * MAX_M + 2 * MAX_M) * 8);
 }
@@ -603,6 +343,7 @@ cudaError_t launch_mgs(ers_ctx* c, const VecGroup& g, int j, int adaptive) {
 
 cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int m_max) {
   SmallArgs A{};
+  A.pade = pade_coefficients();
   A.mode = mode;
   A.nb = g.nb;
   for (int b = 0; b < g.nb; ++b) { A.slot[b] = g.slot[b]; A.H[b] = g.H[b]; }
@@ -612,7 +353,8 @@ cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int 
   A.m_min = c->opts.m_min;
   A.m_max = m_max;
   A.status = c->d_status;
-  size_t sm = (6 * (size_t)MAX_M * MAX_M + 2 * MAX_M) * 8;
+  size_t mm = (size_t)c->opts.m_max;
+  size_t sm = (6 * mm * mm + 2 * mm) * 8;
   k_small<<<g.nb, KB, sm, c->stream>>>(A);
   c->stats.kernel_launches++;
   return cudaGetLastError();
@@ -621,6 +363,7 @@ cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int 
 cudaError_t launch_small_test(ers_ctx* c, const double* H, int ldh, int m, double h, double* y,
                               double* last) {
   SmallArgs A{};
+  A.pade = pade_coefficients();
   A.mode = SMALL_TEST;
   A.h = h;
   A.Htest = H;

@@ -1,0 +1,283 @@
+// Small dense stage of the invert-Krylov MEVP (Sec. IV, Eq. 14 and Eq. 16), shared by the
+// single-circuit and the batched kernels: exp(h H_m^-1) e_1 by scaling and squaring of the
+// diagonal [13/13] Pade approximant in shared memory, e_m^T H_m^-1 exp(h H_m^-1) e_1, and the
+// Krylov-dimension decision of Algorithm 1.
+#pragma once
+#include "ers_internal.h"
+
+namespace ers {
+
+struct PadeCoef {
+  double c[14];
+};
+
+// [q/q] Pade approximant of exp: c_k = (2q-k)! q! / ((2q)! k! (q-k)!), q = 13
+inline PadeCoef pade_coefficients() {
+  PadeCoef P;
+  const int q = 13;
+  for (int k = 0; k <= q; ++k) {
+    double v = 1.0;
+    for (int i = 1; i <= q; ++i) v *= (double)i;            // q!
+    for (int i = 1; i <= 2 * q - k; ++i) v *= (double)i;    // (2q-k)!
+    for (int i = 1; i <= 2 * q; ++i) v /= (double)i;        // (2q)!
+    for (int i = 1; i <= k; ++i) v /= (double)i;            // k!
+    for (int i = 1; i <= q - k; ++i) v /= (double)i;        // (q-k)!
+    P.c[k] = v;
+  }
+  return P;
+}
+
+__device__ inline void sm_matmul(double* C, const double* A, const double* B, int m) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, jj = e / m;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc += A[i + k * m] * B[k + jj * m];
+    C[e] = acc;
+  }
+  __syncthreads();
+}
+
+// LU with partial pivoting of M (m x m, in place); piv[k] = row swapped with k.
+__device__ inline void sm_lu(double* M, int* piv, int m) {
+  __shared__ int s_p;
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(M[k + k * m]);
+      for (int i = k + 1; i < m; ++i)
+        if (fabs(M[i + k * m]) > best) { best = fabs(M[i + k * m]); p = i; }
+      s_p = p;
+      piv[k] = p;
+    }
+    __syncthreads();
+    int p = s_p;
+    if (p != k)
+      for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+        double t = M[k + jj * m];
+        M[k + jj * m] = M[p + jj * m];
+        M[p + jj * m] = t;
+      }
+    __syncthreads();
+    double inv = 1.0 / M[k + k * m];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] *= inv;
+    __syncthreads();
+    int rem = m - k - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      int i = k + 1 + e % rem, jj = k + 1 + e / rem;
+      M[i + jj * m] -= M[i + k * m] * M[k + jj * m];
+    }
+    __syncthreads();
+  }
+}
+
+// Solve (LU) X = B column by column in place (B: m x m); column jj by one thread.
+__device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, int m) {
+  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+    double* b = B + jj * m;
+    for (int k = 0; k < m; ++k)
+      if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
+    for (int i = 1; i < m; ++i) {
+      double acc = b[i];
+      for (int k = 0; k < i; ++k) acc -= LU[i + k * m] * b[k];
+      b[i] = acc;
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = b[i];
+      for (int k = i + 1; k < m; ++k) acc -= LU[i + k * m] * b[k];
+      b[i] = acc / LU[i + i * m];
+    }
+  }
+  __syncthreads();
+}
+
+// y = exp(h H^-1) e_1 for the leading m x m block of H (ld ldh); last = e_m^T H^-1 y.
+// Scaling and squaring of the diagonal [13/13] Pade approximant (theta_13 = 5.37).
+// Returns true when y and last are finite.  smem: 6 m^2 doubles + scratch.
+__device__ inline bool phi_small(const double* H, int ldh, int m, double h, double* y,
+                                 double* last, double* smem, int* ipiv, const PadeCoef& pade) {
+  const double* c_pade = pade.c;
+  double* M0 = smem;
+  double* M1 = M0 + m * m;
+  double* M2 = M1 + m * m;
+  double* M3 = M2 + m * m;
+  double* M4 = M3 + m * m;
+  double* M5 = M4 + m * m;
+  double* lastrow = M5 + m * m;   // m
+  double* vec = lastrow + m;      // m
+  __shared__ int s_s;
+  __shared__ double s_norm;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, jj = e / m;
+    M0[e] = H[i + jj * ldh];
+    M1[e] = (i == jj) ? h : 0.0;
+  }
+  __syncthreads();
+  sm_lu(M0, ipiv, m);
+  sm_lu_solve(M0, ipiv, M1, m);          // M1 = X = h H^-1
+  for (int k = threadIdx.x; k < m; k += blockDim.x) lastrow[k] = M1[(m - 1) + k * m] / h;
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int jj = 0; jj < m; ++jj) {
+      double cs = 0.0;
+      for (int i = 0; i < m; ++i) cs += fabs(M1[i + jj * m]);
+      nrm = fmax(nrm, cs);
+    }
+    s_norm = nrm;
+    int s = 0;
+    if (nrm > 5.371920351148152) s = (int)ceil(log2(nrm / 5.371920351148152));
+    if (!isfinite(nrm)) s = 0;
+    s_s = min(s, 1000);
+  }
+  __syncthreads();
+  int s = s_s;
+  if (!isfinite(s_norm)) {
+    if (threadIdx.x == 0) *last = NAN;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) y[k] = NAN;
+    __syncthreads();
+    return false;
+  }
+  double sc = ldexp(1.0, -s);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) M1[e] *= sc;
+  __syncthreads();
+  sm_matmul(M2, M1, M1, m);   // A2
+  sm_matmul(M3, M2, M2, m);   // A4
+  sm_matmul(M4, M3, M2, m);   // A6
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
+    M0[e] = c_pade[13] * M4[e] + c_pade[11] * M3[e] + c_pade[9] * M2[e];
+  __syncthreads();
+  sm_matmul(M5, M4, M0, m);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, jj = e / m;
+    M5[e] += c_pade[7] * M4[e] + c_pade[5] * M3[e] + c_pade[3] * M2[e] + (i == jj ? c_pade[1] : 0.0);
+  }
+  __syncthreads();
+  sm_matmul(M0, M1, M5, m);   // U
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
+    M5[e] = c_pade[12] * M4[e] + c_pade[10] * M3[e] + c_pade[8] * M2[e];
+  __syncthreads();
+  sm_matmul(M1, M4, M5, m);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, jj = e / m;
+    double V = M1[e] + c_pade[6] * M4[e] + c_pade[4] * M3[e] + c_pade[2] * M2[e] +
+               (i == jj ? c_pade[0] : 0.0);
+    M2[e] = V - M0[e];
+    M3[e] = V + M0[e];
+  }
+  __syncthreads();
+  sm_lu(M2, ipiv, m);
+  sm_lu_solve(M2, ipiv, M3, m);   // R = (V - U)^-1 (V + U)
+  double* R = M3;
+  double* Tm = M4;
+  for (int q = 0; q + 1 < s; ++q) {
+    sm_matmul(Tm, R, R, m);
+    double* t = R; R = Tm; Tm = t;
+  }
+  // y = R (R e_1) when s >= 1, else R e_1
+  for (int i = threadIdx.x; i < m; i += blockDim.x) vec[i] = R[i];
+  __syncthreads();
+  if (s >= 1) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double acc = 0.0;
+      for (int k = 0; k < m; ++k) acc += R[i + k * m] * vec[k];
+      y[i] = acc;
+    }
+  } else {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = vec[i];
+  }
+  __syncthreads();
+  __shared__ int s_fin;
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    bool fin = true;
+    for (int k = 0; k < m; ++k) {
+      acc += lastrow[k] * y[k];
+      fin = fin && isfinite(y[k]);
+    }
+    *last = acc;
+    s_fin = fin && isfinite(acc);
+  }
+  __syncthreads();
+  return s_fin;
+}
+
+
+
+// The decision of Algorithm 1 for one Krylov space after its latest Arnoldi iteration
+// (mode RESID), at the end of a fixed-dimension run (FIXED_END), or for an existing basis at
+// a new h (FINAL).  Writes y = exp(h H_m^-1) e_1 and m into the space's state.
+__device__ inline void small_decide(int mode, const double* H, KrylovState& K, double h,
+                                    double eps, int m_min, int m_max, double* smem, int* ipiv,
+                                    double* ybuf, double* s_last, unsigned* status,
+                                    const PadeCoef& pade) {
+  const int ldh = MAX_M + 1;
+  __shared__ int s_done, s_m, s_built, s_bd, s_m_in, s_conv;
+  if (threadIdx.x == 0) {
+    s_done = K.done; s_m = K.m; s_built = K.built; s_bd = K.breakdown;
+    s_m_in = (K.beta > 0.0);
+  }
+  __syncthreads();
+  if (!s_m_in) return;   // zero vector: MEVP = 0
+  auto write_y = [&](int m) {
+    for (int k = threadIdx.x; k < m; k += blockDim.x) K.y[k] = ybuf[k];
+    if (threadIdx.x == 0) { K.last = *s_last; K.m = m; }
+  };
+  // dimension at a breakdown: built, or built-1 when the last direction was noise
+  auto finalize_breakdown = [&]() {
+    int m = s_built;
+    bool fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    if (!fin && m > 1) {
+      m -= 1;
+      fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    }
+    if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
+    write_y(m);
+  };
+  if (mode == SMALL_FINAL) {
+    bool fin = phi_small(H, ldh, s_m, h, ybuf, s_last, smem, ipiv, pade);
+    if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
+    write_y(s_m);
+    return;
+  }
+  if (mode == SMALL_FIXED_END) {
+    if (s_bd) { finalize_breakdown(); return; }
+    bool fin = phi_small(H, ldh, s_built, h, ybuf, s_last, smem, ipiv, pade);
+    if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
+    write_y(s_built);
+    if (threadIdx.x == 0) K.done = 1;
+    return;
+  }
+  // SMALL_RESID: called after every Arnoldi iteration in adaptive mode
+  if (s_done && !s_bd) return;   // already converged earlier
+  if (s_bd) {
+    if (s_m == s_built) { finalize_breakdown(); if (threadIdx.x == 0) K.breakdown = 2; }
+    return;
+  }
+  int jj = s_built;
+  if (jj >= m_min) {
+    bool fin = phi_small(H, ldh, jj, h, ybuf, s_last, smem, ipiv, pade);
+    if (threadIdx.x == 0) {
+      double res = H[jj + (jj - 1) * ldh] * K.gvnext[jj - 1] * fabs(*s_last) / K.gv1;
+      if (!fin) res = INFINITY;
+      K.res = res;
+      if (isfinite(res) && res < K.best_res) { K.best_res = res; K.best_m = jj; }
+      s_conv = isfinite(res) && res < eps;
+    }
+    __syncthreads();
+    if (s_conv) {
+      write_y(jj);
+      if (threadIdx.x == 0) K.done = 1;
+      return;
+    }
+  }
+  if (jj >= m_max) {
+    // never converged: the dimension with the smallest finite residual
+    int m = K.best_m > 0 ? K.best_m : jj;
+    __syncthreads();
+    bool fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
+    write_y(m);
+    if (threadIdx.x == 0) K.done = 1;
+  }
+}
+
+}  // namespace ers

@@ -49,6 +49,12 @@ class Opts(C.Structure):
                 ("combined_vector", C.c_int32), ("correction", C.c_int32)]
 
 
+class Instance(C.Structure):
+    _fields_ = [("G", C.POINTER(Csr)), ("C", C.POINTER(Csr)), ("B", C.POINTER(Csr)),
+                ("dev", C.POINTER(Mosfet)), ("ndev", C.c_int32), ("u", C.POINTER(Pwl)),
+                ("p", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rejects", C.c_int64), ("refactors", C.c_int64),
                 ("krylov_vectors", C.c_int64), ("solves", C.c_int64),
@@ -68,7 +74,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_step", "ers_run", "ers_get_state", "ers_set_state", "ers_get_state_dev",
            "ers_set_state_dev", "ers_solve", "ers_spmv_C", "ers_mevp", "ers_phi_small",
            "ers_stats", "ers_profile", "ers_analyze", "ers_last_error", "ers_destroy",
-           "ers_solve_dev_noalloc"]
+           "ers_solve_dev_noalloc", "ers_create_batch", "ers_run_batch", "ers_get_state_inst"]
 
 _lib = None
 
@@ -104,6 +110,9 @@ def lib():
         "ers_stats": ([P, C.POINTER(Stats)], C.c_int),
         "ers_profile": ([P, I32], C.c_int),
         "ers_solve_dev_noalloc": ([P, P, P], C.c_int),
+        "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, C.POINTER(Opts)], C.c_int),
+        "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
+        "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
         "ers_last_error": ([P], C.c_char_p),
         "ers_destroy": ([P], None),
@@ -303,3 +312,68 @@ class Simulator:
         st = Stats()
         self._check(lib().ers_stats(self._ctx, C.byref(st)))
         return st.as_dict()
+
+
+def _circuit_parts(circ):
+    G = _CsrHold(circ.G)
+    Cm = _CsrHold(circ.C)
+    n = circ.G.shape[0]
+    B = _CsrHold(circ.B, (n, circ.B.shape[1]))
+    dev = circ.dev
+    ndev = 0 if dev is None else len(dev)
+    devs = (Mosfet * max(ndev, 1))()
+    for i in range(ndev):
+        d = dev[i]
+        devs[i] = Mosfet(int(d["type"]), int(d["d"]), int(d["g"]), int(d["s"]),
+                         float(d["vt"]), float(d["k"]), float(d["lam"]))
+    p = circ.B.shape[1]
+    arrays = []
+    pw = (Pwl * max(p, 1))()
+    for q, (tt, vv) in enumerate(circ.pwl):
+        tt = np.ascontiguousarray(tt, np.float64)
+        vv = np.ascontiguousarray(vv, np.float64)
+        arrays.append((tt, vv))
+        pw[q] = Pwl(int(tt.size), _dptr(tt), _dptr(vv))
+    return dict(G=G, C=Cm, B=B, devs=devs, ndev=ndev, pw=pw, p=p, arrays=arrays, n=n)
+
+
+class BatchSimulator(Simulator):
+    """Many independent circuits in one context (ers_create_batch): one refactor and one
+    solve pass per step cover all of them; each keeps its own Algorithm-2 controller."""
+
+    def __init__(self, circuits, opts: Optional[Opts] = None, stream=None):
+        L = lib()
+        self._parts = [_circuit_parts(c) for c in circuits]
+        self.sizes = [pt["n"] for pt in self._parts]
+        self.n = int(sum(self.sizes))
+        self.ninst = len(circuits)
+        inst = (Instance * self.ninst)()
+        for k, pt in enumerate(self._parts):
+            inst[k] = Instance(C.pointer(pt["G"].c), C.pointer(pt["C"].c), C.pointer(pt["B"].c),
+                               pt["devs"] if pt["ndev"] else None, pt["ndev"],
+                               pt["pw"] if pt["p"] else None, pt["p"])
+        self.opts = opts if opts is not None else default_opts()
+        self._ctx = C.c_void_p()
+        rc = L.ers_create_batch(C.byref(self._ctx), inst, self.ninst, C.byref(self.opts))
+        if rc != 0:
+            msg = L.ers_last_error(self._ctx).decode() if self._ctx else ""
+            if self._ctx:
+                L.ers_destroy(self._ctx)
+            self._ctx = None
+            raise ErsError(rc, msg)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def run_batch(self, t_end: float, tol: float = 1e-6, max_steps: int = 0):
+        ns = np.zeros(self.ninst, np.int32)
+        nr = np.zeros(self.ninst, np.int32)
+        self._check(lib().ers_run_batch(self._ctx, float(t_end), float(tol), int(max_steps),
+                                        _iptr(ns), _iptr(nr)))
+        return ns, nr
+
+    def state_inst(self, k: int):
+        x = np.zeros(self.sizes[k])
+        t = C.c_double(0.0)
+        h = C.c_double(0.0)
+        self._check(lib().ers_get_state_inst(self._ctx, int(k), C.byref(t), _dptr(x), C.byref(h)))
+        return t.value, x, h.value
