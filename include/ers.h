@@ -138,6 +138,99 @@ ers_status ers_run_batch(ers_ctx* ctx, double t_end, double tol, int32_t max_ste
 /* Time, state (n_k doubles, the instance's own node order) and proposed step of instance k. */
 ers_status ers_get_state_inst(const ers_ctx* ctx, int32_t k, double* t, double* x, double* h);
 
+/* ---- Learned step controller (the paper's controller is the plain rule of Alg. 2: reject ->
+ * h = alpha h with the same Krylov spaces, accept -> h = beta h while the step saw fewer than
+ * i_grow rejections).  The learned form keeps the error test of Eq. 15 as the judge: a network
+ * proposes the next (h, m) of each instance from its last 8 accepted steps; a rejected
+ * proposal falls back to the plain rule (h = alpha h, same spaces).  The proposed m is the
+ * Krylov dimension from which the residual test of Eq. 16 is evaluated; the basis still grows
+ * until that test passes, so a proposal changes cost, never the accuracy bar. ---- */
+
+/* One accepted step of one instance. */
+typedef struct {
+  double h;        /* accepted step size */
+  double h_max;    /* step-size cap of the run */
+  double err;      /* ||e_rr||_inf of the accepted step (Eq. 15) */
+  double E;        /* error budget E_rr of the step */
+  double dF;       /* ||F(x_{k+1}) - F(x_k) - J_k (x_{k+1} - x_k)||_inf (0 for linear circuits) */
+  int32_t m;       /* largest Krylov dimension used by the step's solution spaces */
+  int32_t m_max;   /* dimension cap of the run */
+  int32_t landed;  /* 1 = h was cut to land on a PWL corner or t_end */
+  int32_t retries; /* rejections before acceptance */
+} ers_step_record;
+
+#define ERS_CTRL_HISTORY 8     /* accepted steps the network sees */
+#define ERS_CTRL_FEATURES 32   /* 4 features per step */
+
+/* Features of the network input from the last min(count, 8) records (recs[count-1] is the
+ * latest; missing older steps repeat the oldest one).  For step j back (j = 0 latest):
+ *   f[4j+0] = clamp(log10(h / h_max), -6, 0) / 3
+ *   f[4j+1] = m / m_max
+ *   f[4j+2] = clamp(log10(err / E), -6, 1) / 3        (err = 0 reads as -6)
+ *   f[4j+3] = (clamp(log10 dF, -12, 0) + 6) / 6       (dF = 0 reads as -12)
+ * Host-only; count >= 1. */
+ers_status ers_ctrl_features(const ers_step_record* recs, int32_t count, float* out);
+
+/* Training target of the step after recs[count-1] given the next record `next`:
+ *   t[0] = clamp(log2(next.h / h_k) + log2(clamp(0.8 sqrt(next.E / next.err), 1, 2)), -3, 2)
+ *          (the step the plain controller accepted, widened by the headroom its error left)
+ *   t[1] = next.m / next.m_max
+ * Returns ERS_ERR_INVALID for a `next` that landed on a corner (its h says nothing about the
+ * error).  Host-only. */
+ers_status ers_ctrl_target(const ers_step_record* recs, int32_t count, const ers_step_record* next,
+                           float* t);
+
+/* Network of the learned controller: 32 -> 64 -> 64 -> 64 -> 2, ReLU, BF16 weights and
+ * activations with FP32 accumulation on the tensor cores, FP32 master weights, Adam.
+ * Parameter vector (FP32, ers_mlp_nparam() entries): W1 (64x32 row-major), b1, W2 (64x64),
+ * b2, W3 (64x64), b3, W4 (2x64), b4.  Outputs: y[0] = log2(h_next / h_k), y[1] = m_next/m_max. */
+typedef struct ers_mlp ers_mlp;
+int32_t ers_mlp_nparam(void);
+/* He-initialised weights (seeded), zero biases, zero Adam moments. */
+ers_status ers_mlp_create(ers_mlp** out, uint64_t seed);
+ers_status ers_mlp_set_params(ers_mlp* mlp, const float* params);
+ers_status ers_mlp_get_params(const ers_mlp* mlp, float* params);
+/* Y (n x 2) = network(X (n x 32)); host buffers, row-major. */
+ers_status ers_mlp_forward(ers_mlp* mlp, const float* X, int32_t n, float* Y);
+/* Same with device buffers, enqueued on `stream` (a cudaStream_t; NULL = the network's own). */
+ers_status ers_mlp_forward_dev(ers_mlp* mlp, const float* X_dev, int32_t n, float* Y_dev,
+                               void* stream);
+/* Gradient (ers_mlp_nparam() floats, may be NULL) and value of the loss
+ * L = (1/n) sum_s ||y_s - T_s||^2 over the n samples (host buffers). */
+ers_status ers_mlp_grad(ers_mlp* mlp, const float* X, const float* T, int32_t n, float* grad,
+                        float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the gradient of L over
+ * the n samples; loss receives L before the step. */
+ers_status ers_mlp_adam_step(ers_mlp* mlp, const float* X, const float* T, int32_t n, float lr,
+                             float* loss);
+/* `epochs` passes over the n samples in a seeded random order, one Adam step per minibatch of
+ * `batch` samples; final_loss = L of the last minibatch before its step. */
+ers_status ers_mlp_train(ers_mlp* mlp, const float* X, const float* T, int32_t n, int32_t epochs,
+                         int32_t batch, float lr, uint64_t seed, float* final_loss);
+const char* ers_mlp_last_error(const ers_mlp* mlp);
+void ers_mlp_destroy(ers_mlp* mlp);
+
+/* Use `mlp` (not owned; must outlive the runs, NULL = plain controller) as the step proposer of
+ * a batched context.  parts selects which proposals are used: ERS_CTRL_H (the next step size;
+ * otherwise the plain rule's), ERS_CTRL_M (the first dimension of the residual test; otherwise
+ * m_min), or both. */
+#define ERS_CTRL_H 1
+#define ERS_CTRL_M 2
+ers_status ers_batch_set_controller(ers_ctx* ctx, ers_mlp* mlp, int32_t parts);
+/* Keep every accepted step's record (enable = 1) instead of the last 8; clears the records. */
+ers_status ers_batch_trace(ers_ctx* ctx, int32_t enable);
+/* Records of instance k: *count receives how many are kept; up to cap are copied to out. */
+ers_status ers_batch_records(const ers_ctx* ctx, int32_t k, ers_step_record* out, int32_t cap,
+                             int32_t* count);
+/* Training samples from the kept records of every instance: one per accepted step k whose
+ * successor did not land on a corner (features of steps <= k, target from step k+1).  X: cap x
+ * 32, T: cap x 2 (may be NULL to count); *count receives the number of samples available. */
+ers_status ers_batch_samples(const ers_ctx* ctx, float* X, float* T, int32_t cap, int32_t* count);
+/* Controller counters of the batched runs so far: proposals made by the network, proposals
+ * rejected by the error test (each falls back to the plain rule), Krylov vectors built. */
+ers_status ers_batch_ctrl_stats(const ers_ctx* ctx, int64_t* proposals, int64_t* rejected,
+                                int64_t* krylov_vectors);
+
 /* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL = a private stream
  * created at ers_create).  All device work of later calls is ordered on it. */
 ers_status ers_set_stream(ers_ctx* ctx, void* stream);

@@ -193,7 +193,9 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
     otherwise iterations stop at the first j >= m_min whose residual (Eq. 16) at h is
     below eps, or at m_max (Algorithm 1's loop bound m_c).  When the test never passes,
     the MEVP uses the dimension with the smallest finite residual: the last directions of a
-    long run can be rounding noise whose spurious Ritz values make exp(h H^{-1}) overflow."""
+    long run can be rounding noise whose spurious Ritz values make exp(h H^{-1}) overflow.
+    If no tested dimension had a finite residual, it uses the largest dimension whose
+    exp(h H^{-1}) e_1 is finite."""
     n = v.shape[0]
     beta = float(np.linalg.norm(v))
     mc = fixed_m if fixed_m > 0 else m_max
@@ -235,6 +237,13 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
     else:
         if fixed_m == 0:
             basis.m = best_j   # never converged: the dimension with the smallest residual
+            if not np.isfinite(best_res):
+                # no tested dimension had a finite residual: the largest dimension whose
+                # exp(h H^{-1}) e_1 is finite
+                with np.errstate(all="ignore"):
+                    while basis.m > 1 and not np.all(np.isfinite(
+                            exp_hinv_e1(H[:basis.m, :basis.m], h)[0])):
+                        basis.m -= 1
     basis.V = V[:, :basis.built + 1]
     basis.H = H[:basis.built + 1, :basis.built]
     return basis

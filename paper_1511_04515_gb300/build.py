@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libers.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["symbolic.cpp", "k_factor.cu", "k_solve.cu", "k_krylov.cu", "api.cu", "batch.cu"]
+SOURCES = ["symbolic.cpp", "controller.cpp", "k_factor.cu", "k_solve.cu", "k_krylov.cu", "api.cu",
+           "batch.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", f"-I{INCLUDE}",
           f"-I{CSRC}"]

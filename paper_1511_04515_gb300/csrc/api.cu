@@ -1116,7 +1116,9 @@ void ers_destroy(ers_ctx* c) {
                   (void*)c->solve_buf, (void*)c->V, (void*)c->H, (void*)c->ks, (void*)c->red,
                   (void*)c->d_status, (void*)c->d_perm, (void*)c->d_inst_of, (void*)c->d_seg_off,
                   (void*)c->d_src_inst, (void*)c->bks, (void*)c->bH, (void*)c->bh, (void*)c->bt,
-                  (void*)c->bred, (void*)c->bmask, (void*)c->bcount})
+                  (void*)c->bred, (void*)c->bmask, (void*)c->bcount,
+                  (void*)c->d_mstart, (void*)c->d_mused, (void*)c->bdf, (void*)c->d_feat,
+                  (void*)c->d_pred, (void*)c->d_kv, (void*)c->d_where})
     f(p);
   for (auto& ev : c->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }

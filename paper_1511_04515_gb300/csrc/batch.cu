@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "controller.h"
 #include "ers_internal.h"
 #include "kcommon.cuh"
 #include "kdense.cuh"
@@ -58,13 +59,26 @@ struct BArgs {
   const int32_t* seg;          // 2 * ninst: [start, end) of each instance
   const int32_t* mask;         // ninst
   const double* h;             // ninst
+  const int32_t* mstart;       // ninst: first dimension of the residual test (NULL = m_min)
   const int32_t *Gp, *Gi;
   const double* Gv;
   double eps;
   int m_min, m_max;
   unsigned* status;
+  unsigned long long* kv;      // count of directions built
+  unsigned* where;             // first non-finite result: [flag, status bit, instance, slot * 256 + j]
   PadeCoef pade;
 };
+
+// record where the first non-finite value of a batched run appeared (first writer wins)
+__device__ __forceinline__ void note_nonfinite(unsigned* where, unsigned bit, int inst, int slot,
+                                               int j) {
+  if (atomicCAS(where, 0u, 1u) == 0u) {
+    where[1] = bit;
+    where[2] = (unsigned)inst;
+    where[3] = (unsigned)(slot * 256 + j);
+  }
+}
 
 __device__ __forceinline__ double* bH_of(const BArgs& A, int slot, int i) {
   return A.H + ((int64_t)slot * A.ninst + i) * (MAX_M + 1) * MAX_M;
@@ -113,7 +127,10 @@ __global__ void __launch_bounds__(BT) k_binit(BArgs A) {
     K.res = INFINITY;
     K.breakdown = 0;
     K.done = (beta > 0.0 && isfinite(beta)) ? 0 : 1;
-    if (!isfinite(beta)) atomicOr(A.status, ST_NONFINITE);
+    if (!isfinite(beta)) {
+      atomicOr(A.status, ST_NONFINITE);
+      note_nonfinite(A.where, ST_NONFINITE, i, slot, 0);
+    }
   }
 }
 
@@ -167,7 +184,11 @@ __global__ void __launch_bounds__(BT) k_bmgs(BArgs A) {
     K.w0 = w0;
     K.built = j + 1;
     K.gvnext[j] = gn;
-    if (!isfinite(hn)) atomicOr(A.status, ST_NONFINITE);
+    atomicAdd(A.kv, 1ull);
+    if (!isfinite(hn)) {
+      atomicOr(A.status, ST_NONFINITE);
+      note_nonfinite(A.where, ST_NONFINITE, i, slot, j + 1);
+    }
     if (bd) { K.breakdown = 1; K.done = 1; K.m = j + 1; }
   }
 }
@@ -180,8 +201,30 @@ __global__ void k_bsmall(BArgs A) {
   __shared__ double s_last;
   const int i = blockIdx.x % A.ninst, b = blockIdx.x / A.ninst, slot = A.slot[b];
   if (!A.mask[i]) return;
-  small_decide(A.mode, bH_of(A, slot, i), A.ks[slot * A.ninst + i], A.h[i], A.eps, A.m_min,
-               A.m_max, smem, ipiv, ybuf, &s_last, A.status, A.pade);
+  if (A.mode == SMALL_RESID && A.mstart) {
+    // a proposed dimension: no residual test (Eq. 16) below it, unless the basis broke down
+    const KrylovState& K = A.ks[slot * A.ninst + i];
+    if (!K.done && !K.breakdown && K.built < min(A.mstart[i], A.m_max)) return;
+  }
+  KrylovState& K = A.ks[slot * A.ninst + i];
+  small_decide(A.mode, bH_of(A, slot, i), K, A.h[i], A.eps, A.m_min, A.m_max,
+               A.mstart ? A.mstart[i] : A.m_min, smem, ipiv, ybuf, &s_last, A.status, A.pade);
+  __syncthreads();
+  if (threadIdx.x == 0 && K.done && K.m > 0) {
+    bool fin = isfinite(K.last);
+    for (int k = 0; k < K.m; ++k) fin = fin && isfinite(K.y[k]);
+    if (!fin) note_nonfinite(A.where, ST_KRYLOV, i, slot, K.built);
+  }
+}
+
+// largest dimension chosen by the spaces of each instance
+// (spaces 0 .. nb-1)
+__global__ void k_bmused(int ninst, int nb, const KrylovState* ks, int32_t* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  int m = 0;
+  for (int b = 0; b < nb; ++b) m = max(m, ks[b * ninst + i].m);
+  out[i] = m;
 }
 
 // how many (instance, space) pairs of the group are still iterating
@@ -323,6 +366,9 @@ BArgs make_bargs(ers_ctx* c, int nb, const int* slots, double* const* src, int a
   A.m_max = c->opts.m_max;
   A.status = c->d_status;
   A.pade = pade_coefficients();
+  A.mstart = c->ctrl ? c->d_mstart : nullptr;
+  A.kv = c->d_kv;
+  A.where = c->d_where;
   return A;
 }
 
@@ -336,14 +382,17 @@ ers_status launch_bsmall(ers_ctx* c, BArgs A, int mode) {
   return ERS_OK;
 }
 
-// Algorithm 1 up to the MEVP for the spaces `slots` of every masked instance (adaptive m)
-ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src) {
+// Algorithm 1 up to the MEVP for the spaces `slots` of every masked instance (adaptive m).
+// No space can finish before it has `first_test` directions (the smallest dimension at which
+// a residual test runs) unless it breaks down, and a broken-down space only skips work, so the
+// host polls for completion from that iteration on.
+ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src, int first_test) {
   const int mc = c->opts.m_max;
   BArgs A = make_bargs(c, nb, slots, src, 1);
   k_binit<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(A);
   c->stats.kernel_launches++;
   for (int j = 0; j < mc; ++j) {
-    if (j > 0) {
+    if (j > 0 && j >= first_test) {
       k_bcount<<<1, 256, 0, c->stream>>>(A, c->bcount);
       int32_t cnt = 0;
       BCU(cudaMemcpyAsync(&cnt, c->bcount, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -364,11 +413,22 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src)
     for (int b = 0; b < nb; ++b) M.src[b] = c->solve_buf + (size_t)b * c->n;
     k_bmgs<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(M);
     c->stats.kernel_launches++;
-    c->stats.krylov_vectors += (int64_t)nb * c->ninst;
     ers_status st = launch_bsmall(c, A, SMALL_RESID);
     if (st != ERS_OK) return st;
   }
   return ERS_OK;
+}
+
+// a failed status of a batched run, with the first non-finite location added to the message
+ers_status batch_fail_where(ers_ctx* c, ers_status st) {
+  unsigned w[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(w, c->d_where, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess && w[0]) {
+    const char* what = w[1] == ST_KRYLOV ? "exp(h H^-1) e_1" : "Krylov vector";
+    c->err += std::string(" (first non-finite ") + what + ": instance " + std::to_string(w[2]) +
+              ", space " + std::to_string(w[3] / 256) + ", dimension " +
+              std::to_string(w[3] % 256) + ")";
+  }
+  return st;
 }
 
 double next_bp(const std::vector<double>& bp, double t) {
@@ -493,6 +553,18 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
   BCU(cudaMalloc((void**)&c->bred, sizeof(double) * ninst));
   BCU(cudaMalloc((void**)&c->bmask, sizeof(int32_t) * ninst));
   BCU(cudaMalloc((void**)&c->bcount, sizeof(int32_t)));
+  BCU(cudaMalloc((void**)&c->d_mstart, sizeof(int32_t) * ninst));
+  BCU(cudaMalloc((void**)&c->d_kv, sizeof(unsigned long long)));
+  BCU(cudaMalloc((void**)&c->d_where, 4 * sizeof(unsigned)));
+  BCU(cudaMemset(c->d_where, 0, 4 * sizeof(unsigned)));
+  BCU(cudaMemset(c->d_kv, 0, sizeof(unsigned long long)));
+  BCU(cudaMalloc((void**)&c->d_mused, sizeof(int32_t) * ninst));
+  BCU(cudaMalloc((void**)&c->bdf, sizeof(double) * ninst));
+  BCU(cudaMalloc((void**)&c->d_feat, sizeof(float) * ERS_CTRL_FEATURES * (size_t)ninst));
+  BCU(cudaMalloc((void**)&c->d_pred, sizeof(float) * 2 * (size_t)ninst));
+  c->recs.assign(ninst, {});
+  c->mstart_inst.assign(ninst, c->opts.m_min);
+  c->proposed_inst.assign(ninst, 0);
   BCU(cudaFuncSetAttribute(k_bsmall, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
   return ERS_OK;
@@ -506,15 +578,18 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   const int ninst = c->ninst, n = c->n;
   const ers_opts& o = c->opts;
   const double h_max = o.h_max > 0 ? o.h_max : t_end / 100.0;
-  std::vector<double> h(ninst), E(ninst), err(ninst), xmax(ninst);
-  std::vector<int32_t> active(ninst), trying(ninst), retries(ninst);
+  std::vector<double> h(ninst), E(ninst), err(ninst), xmax(ninst), dF(ninst), dF_acc(ninst);
+  std::vector<double> err_acc(ninst);
+  std::vector<int32_t> active(ninst), trying(ninst), retries(ninst), mused(ninst);
   std::vector<int> landed(ninst);
+  std::vector<float> feat, pred;
   ers_status st = ctx_clear_status(c);
   if (st != ERS_OK) return st;
+  BCU(cudaMemsetAsync(c->d_where, 0, 4 * sizeof(unsigned), c->stream));
   int round = 0;
   std::vector<int32_t> ones(ninst, 1);
   while (max_steps <= 0 || round < max_steps) {
-    int nact = 0;
+    int nact = 0, first_test = o.m_max;
     for (int i = 0; i < ninst; ++i) {
       active[i] = c->t_inst[i] < t_end * (1 - 1e-12);
       nact += active[i];
@@ -524,6 +599,8 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       h[i] = std::min(std::min(hp, h_max), nb - c->t_inst[i]);
       landed[i] = h[i] == nb - c->t_inst[i];
       retries[i] = 0;
+      if (!c->ctrl) c->mstart_inst[i] = o.m_min;
+      first_test = std::min(first_test, std::max(c->mstart_inst[i], o.m_min));
     }
     if (nact == 0) break;
     // error budgets from ||x_i||_inf
@@ -533,6 +610,9 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     BCU(cudaMemcpyAsync(c->bh, h.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
     BCU(cudaMemcpyAsync(c->bt, c->t_inst.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
     BCU(cudaMemcpyAsync(c->bmask, active.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
+    if (c->ctrl)
+      BCU(cudaMemcpyAsync(c->d_mstart, c->mstart_inst.data(), sizeof(int32_t) * ninst,
+                          cudaMemcpyHostToDevice, c->stream));
     BCU(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < ninst; ++i) E[i] = o.E_rr > 0 ? o.E_rr : tol * std::max(1.0, xmax[i]);
     if (!c->factored) {
@@ -562,8 +642,11 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     int slots[2] = {0, 1};
     double* src[2] = {c->v1, c->v2};
     const int nsol = ramp ? 2 : 1;
-    st = batch_bases(c, nsol, slots, src);
+    st = batch_bases(c, nsol, slots, src, first_test);
     if (st != ERS_OK) return st;
+    k_bmused<<<nblk(ninst), 256, 0, c->stream>>>(ninst, nsol, c->bks, c->d_mused);
+    BCU(cudaMemcpyAsync(mused.data(), c->d_mused, sizeof(int32_t) * ninst, cudaMemcpyDeviceToHost, c->stream));
+    c->stats.kernel_launches++;
     trying = active;
     while (true) {
       BCU(cudaMemcpyAsync(c->bmask, trying.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
@@ -580,15 +663,18 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(U);
       c->stats.kernel_launches++;
       std::fill(err.begin(), err.end(), 0.0);
+      std::fill(dF.begin(), dF.end(), 0.0);
       if (c->ndev) {
         // e_rr = -(e^{hJ} - I) G^-1 dF per instance (Eq. 15)
         launch_dev_eval(c, c->xnew, c->dev_I + c->ndev, 0);
         launch_node_F(c, 1, c->dev_I + c->ndev, c->xnew, c->solve_buf);
+        k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->solve_buf, c->bdf);
+        BCU(cudaMemcpyAsync(dF.data(), c->bdf, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
         BCU(launch_solve(c, c->solve_buf, 1));
         BCU(cudaMemcpyAsync(c->ve, c->solve_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
         int es = 2;
         double* esrc[1] = {c->ve};
-        st = batch_bases(c, 1, &es, esrc);
+        st = batch_bases(c, 1, &es, esrc, o.m_min);
         if (st != ERS_OK) return st;
         BCombine Er{};
         Er.n = n; Er.ninst = ninst; Er.nb = 1; Er.out = c->tmp; Er.in = nullptr; Er.a = 0.0;
@@ -597,14 +683,20 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
         k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(Er);
         k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->tmp, c->bred);
         BCU(cudaMemcpyAsync(err.data(), c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
-        c->stats.kernel_launches += 2;
+        c->stats.kernel_launches += 3;
       }
       st = ctx_sync_status(c);
-      if (st != ERS_OK) return st;
+      if (st != ERS_OK) return batch_fail_where(c, st);
       int left = 0;
       for (int i = 0; i < ninst; ++i) {
         if (!trying[i]) continue;
-        if (err[i] <= E[i]) { trying[i] = 0; continue; }
+        if (err[i] <= E[i]) {
+          trying[i] = 0;
+          err_acc[i] = err[i];
+          dF_acc[i] = dF[i];
+          continue;
+        }
+        if (retries[i] == 0 && c->proposed_inst[i]) c->ctrl_rejected++;
         h[i] *= o.alpha;
         retries[i]++;
         c->rejects_inst[i]++;
@@ -623,22 +715,134 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     BCU(cudaMemcpyAsync(c->bmask, active.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
     k_bcopy<<<nblk(n), 256, 0, c->stream>>>(n, c->d_inst_of, c->bmask, c->xnew, c->x);
     c->stats.kernel_launches++;
+    std::vector<int> ask;
     for (int i = 0; i < ninst; ++i) {
       if (!active[i]) continue;
       double nb = std::min(next_bp(c->bp_inst[i], c->t_inst[i]), t_end);
       c->t_inst[i] = landed[i] ? nb : c->t_inst[i] + h[i];
       c->steps_inst[i]++;
+      // plain controller of Alg. 2
       c->hprop_inst[i] = retries[i] < o.i_grow ? std::min(o.beta * h[i], h_max) : h[i];
+      c->proposed_inst[i] = 0;
+      ers_step_record r{};
+      r.h = h[i];
+      r.h_max = h_max;
+      r.err = err_acc[i];
+      r.E = E[i];
+      r.dF = dF_acc[i];
+      r.m = mused[i];
+      r.m_max = o.m_max;
+      r.landed = landed[i];
+      r.retries = retries[i];
+      auto& R = c->recs[i];
+      R.push_back(r);
+      if (!c->trace && R.size() > 2 * ERS_CTRL_HISTORY)
+        R.erase(R.begin(), R.end() - ERS_CTRL_HISTORY);
+      if (c->ctrl && c->t_inst[i] < t_end * (1 - 1e-12)) ask.push_back(i);
+    }
+    if (!ask.empty()) {
+      // learned controller: the network proposes (h, m) of the next step of each instance
+      const int na = (int)ask.size();
+      feat.resize((size_t)na * ERS_CTRL_FEATURES);
+      pred.resize((size_t)na * 2);
+      for (int q = 0; q < na; ++q) {
+        const auto& R = c->recs[ask[q]];
+        ctrl_features(R.data(), (int)R.size(), &feat[(size_t)q * ERS_CTRL_FEATURES]);
+      }
+      BCU(cudaMemcpyAsync(c->d_feat, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, c->stream));
+      st = ers_mlp_forward_dev(c->ctrl, c->d_feat, na, c->d_pred, c->stream);
+      if (st != ERS_OK) return ctx_fail(c, st, std::string("controller network: ") + ers_mlp_last_error(c->ctrl));
+      BCU(cudaMemcpyAsync(pred.data(), c->d_pred, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, c->stream));
+      BCU(cudaStreamSynchronize(c->stream));
+      c->stats.kernel_launches++;
+      for (int q = 0; q < na; ++q) {
+        int i = ask[q];
+        double hn;
+        int ms;
+        ctrl_propose(&pred[2 * q], h[i], h_max, o.m_min, o.m_max, &hn, &ms);
+        if (c->ctrl_parts & ERS_CTRL_H) {
+          c->hprop_inst[i] = hn;
+          c->proposed_inst[i] = 1;
+          c->ctrl_proposals++;
+        }
+        c->mstart_inst[i] = (c->ctrl_parts & ERS_CTRL_M) ? ms : o.m_min;
+      }
     }
     if (!c->linear) c->factored = false;
     c->stats.steps++;
     ++round;
   }
+  unsigned long long kv = 0;
+  BCU(cudaMemcpyAsync(&kv, c->d_kv, sizeof(kv), cudaMemcpyDeviceToHost, c->stream));
   BCU(cudaStreamSynchronize(c->stream));
+  c->stats.krylov_vectors = (int64_t)kv;
   for (int i = 0; i < ninst; ++i) {
     if (nsteps) nsteps[i] = (int32_t)c->steps_inst[i];
     if (nreject) nreject[i] = (int32_t)c->rejects_inst[i];
   }
+  return ERS_OK;
+}
+
+ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts) {
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  if (mlp && (parts & ~(ERS_CTRL_H | ERS_CTRL_M)) != 0)
+    return ctx_fail(c, ERS_ERR_INVALID, "unknown controller parts");
+  c->ctrl = (parts & (ERS_CTRL_H | ERS_CTRL_M)) ? mlp : nullptr;
+  c->ctrl_parts = parts;
+  std::fill(c->proposed_inst.begin(), c->proposed_inst.end(), 0);
+  std::fill(c->mstart_inst.begin(), c->mstart_inst.end(), c->opts.m_min);
+  return ERS_OK;
+}
+
+ers_status ers_batch_trace(ers_ctx* c, int32_t enable) {
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  c->trace = enable != 0;
+  for (auto& R : c->recs) R.clear();
+  return ERS_OK;
+}
+
+ers_status ers_batch_records(const ers_ctx* cc, int32_t k, ers_step_record* out, int32_t cap,
+                             int32_t* count) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  if (k < 0 || k >= c->ninst) return ctx_fail(c, ERS_ERR_INVALID, "instance index out of range");
+  const auto& R = c->recs[k];
+  if (count) *count = (int32_t)R.size();
+  if (out)
+    for (int32_t q = 0; q < std::min<int32_t>(cap, (int32_t)R.size()); ++q) out[q] = R[q];
+  return ERS_OK;
+}
+
+ers_status ers_batch_samples(const ers_ctx* cc, float* X, float* T, int32_t cap, int32_t* count) {
+  ers_ctx* c = const_cast<ers_ctx*>(cc);
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  int64_t ns = 0;
+  for (const auto& R : c->recs) {
+    for (size_t k = 0; k + 1 < R.size(); ++k) {
+      float t[2];
+      if (!ctrl_target(R.data(), (int)k + 1, R[k + 1], t)) continue;
+      if (X && T && ns < cap) {
+        ctrl_features(R.data(), (int)k + 1, X + ns * ERS_CTRL_FEATURES);
+        T[2 * ns] = t[0];
+        T[2 * ns + 1] = t[1];
+      }
+      ++ns;
+    }
+  }
+  if (count) *count = (int32_t)std::min<int64_t>(ns, INT32_MAX);
+  return ERS_OK;
+}
+
+ers_status ers_batch_ctrl_stats(const ers_ctx* c, int64_t* proposals, int64_t* rejected,
+                                int64_t* krylov_vectors) {
+  if (!c) return ERS_ERR_INVALID;
+  if (proposals) *proposals = c->ctrl_proposals;
+  if (rejected) *rejected = c->ctrl_rejected;
+  if (krylov_vectors) *krylov_vectors = c->stats.krylov_vectors;
   return ERS_OK;
 }
 

@@ -150,6 +150,20 @@ struct ers_ctx {
   double *bh = nullptr, *bt = nullptr, *bred = nullptr;  // ninst each
   int32_t* bmask = nullptr;            // ninst
   int32_t* bcount = nullptr;           // 1
+  unsigned long long* d_kv = nullptr;  // Krylov vectors built by the batched Arnoldi kernels
+  unsigned* d_where = nullptr;         // first non-finite value of a batched run (4 words)
+  int ctrl_parts = 0;                  // ERS_CTRL_H | ERS_CTRL_M: which proposals are used
+  // learned step controller of batched runs
+  ers_mlp* ctrl = nullptr;             // not owned; nullptr = plain controller
+  bool trace = false;                  // keep every record (else the last ERS_CTRL_HISTORY)
+  std::vector<std::vector<ers_step_record>> recs;   // per instance, accepted steps
+  std::vector<int32_t> mstart_inst;    // first dimension of the residual test per instance
+  std::vector<uint8_t> proposed_inst;  // next step of the instance is a network proposal
+  int64_t ctrl_proposals = 0, ctrl_rejected = 0;
+  int32_t* d_mstart = nullptr;         // ninst
+  int32_t* d_mused = nullptr;          // ninst
+  double* bdf = nullptr;               // ninst
+  float *d_feat = nullptr, *d_pred = nullptr;   // ninst x 32, ninst x 2
   // profiling of the solve kernels (CUDA events on the context's stream)
   bool profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;

@@ -219,7 +219,7 @@ __global__ void k_small(SmallArgs A) {
     return;
   }
   int b = blockIdx.x;
-  small_decide(A.mode, A.H[b], A.ks[A.slot[b]], A.h, A.eps, A.m_min, A.m_max, smem, ipiv, ybuf,
+  small_decide(A.mode, A.H[b], A.ks[A.slot[b]], A.h, A.eps, A.m_min, A.m_max, A.m_min, smem, ipiv, ybuf,
                &s_last, A.status, A.pade);
 }
 

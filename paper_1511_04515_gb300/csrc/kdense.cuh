@@ -205,9 +205,16 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
 // The decision of Algorithm 1 for one Krylov space after its latest Arnoldi iteration
 // (mode RESID), at the end of a fixed-dimension run (FIXED_END), or for an existing basis at
 // a new h (FINAL).  Writes y = exp(h H_m^-1) e_1 and m into the space's state.
+//
+// m_first (>= m_min) is the first dimension whose residual is tested; the plain rule has
+// m_first = m_min.  A larger m_first (a proposed dimension) skips the tests below it; if the
+// first test there is not finite, or the basis breaks down before it, the skipped dimensions
+// are tested in increasing order and the first that passes is used, which is the dimension
+// the plain rule picks: past its converged dimension a basis gathers rounding-noise
+// directions whose spurious Ritz values make exp(h H^-1) overflow.
 __device__ inline void small_decide(int mode, const double* H, KrylovState& K, double h,
-                                    double eps, int m_min, int m_max, double* smem, int* ipiv,
-                                    double* ybuf, double* s_last, unsigned* status,
+                                    double eps, int m_min, int m_max, int m_first, double* smem,
+                                    int* ipiv, double* ybuf, double* s_last, unsigned* status,
                                     const PadeCoef& pade) {
   const int ldh = MAX_M + 1;
   __shared__ int s_done, s_m, s_built, s_bd, s_m_in, s_conv;
@@ -220,6 +227,31 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
   auto write_y = [&](int m) {
     for (int k = threadIdx.x; k < m; k += blockDim.x) K.y[k] = ybuf[k];
     if (threadIdx.x == 0) { K.last = *s_last; K.m = m; }
+  };
+  // residual test (Eq. 16) at dimension jj <= built; true (and y written, space done) if it
+  // passes.  Tracks the smallest finite residual.
+  auto test_dim = [&](int jj) -> bool {
+    bool fin = phi_small(H, ldh, jj, h, ybuf, s_last, smem, ipiv, pade);
+    if (threadIdx.x == 0) {
+      double res = H[jj + (jj - 1) * ldh] * K.gvnext[jj - 1] * fabs(*s_last) / K.gv1;
+      if (!fin) res = INFINITY;
+      K.res = res;
+      if (isfinite(res) && res < K.best_res) { K.best_res = res; K.best_m = jj; }
+      s_conv = isfinite(res) && res < eps;
+    }
+    __syncthreads();
+    if (s_conv) {
+      write_y(jj);
+      if (threadIdx.x == 0) K.done = 1;
+    }
+    __syncthreads();
+    return s_conv;
+  };
+  // the skipped dimensions [m_min, hi] in increasing order
+  auto scan_skipped = [&](int hi) -> bool {
+    for (int jj = m_min; jj <= hi; ++jj)
+      if (test_dim(jj)) return true;
+    return false;
   };
   // dimension at a breakdown: built, or built-1 when the last direction was noise
   auto finalize_breakdown = [&]() {
@@ -247,33 +279,34 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
     return;
   }
   // SMALL_RESID: called after every Arnoldi iteration in adaptive mode
+  m_first = max(m_first, m_min);
   if (s_done && !s_bd) return;   // already converged earlier
   if (s_bd) {
-    if (s_m == s_built) { finalize_breakdown(); if (threadIdx.x == 0) K.breakdown = 2; }
+    if (s_m == s_built) {
+      if (m_first > m_min && s_built <= m_first && scan_skipped(s_built - 1)) {
+        if (threadIdx.x == 0) K.breakdown = 2;
+        return;
+      }
+      finalize_breakdown();
+      if (threadIdx.x == 0) K.breakdown = 2;
+    }
     return;
   }
   int jj = s_built;
-  if (jj >= m_min) {
-    bool fin = phi_small(H, ldh, jj, h, ybuf, s_last, smem, ipiv, pade);
-    if (threadIdx.x == 0) {
-      double res = H[jj + (jj - 1) * ldh] * K.gvnext[jj - 1] * fabs(*s_last) / K.gv1;
-      if (!fin) res = INFINITY;
-      K.res = res;
-      if (isfinite(res) && res < K.best_res) { K.best_res = res; K.best_m = jj; }
-      s_conv = isfinite(res) && res < eps;
-    }
-    __syncthreads();
-    if (s_conv) {
-      write_y(jj);
-      if (threadIdx.x == 0) K.done = 1;
-      return;
-    }
+  if (jj >= m_first || jj >= m_max) {
+    if (jj >= m_min && test_dim(jj)) return;
+    if (jj == m_first && m_first > m_min && !isfinite(K.res) && scan_skipped(jj - 1)) return;
   }
   if (jj >= m_max) {
-    // never converged: the dimension with the smallest finite residual
+    // never converged: the dimension with the smallest finite residual; when no tested
+    // dimension had one, the largest dimension whose exp(h H^-1) e_1 is finite
     int m = K.best_m > 0 ? K.best_m : jj;
     __syncthreads();
     bool fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    while (!fin && m > 1) {
+      --m;
+      fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    }
     if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
     write_y(m);
     if (threadIdx.x == 0) K.done = 1;

@@ -55,6 +55,16 @@ class Instance(C.Structure):
                 ("p", C.c_int32)]
 
 
+class StepRecord(C.Structure):
+    _fields_ = [("h", C.c_double), ("h_max", C.c_double), ("err", C.c_double), ("E", C.c_double),
+                ("dF", C.c_double), ("m", C.c_int32), ("m_max", C.c_int32),
+                ("landed", C.c_int32), ("retries", C.c_int32)]
+
+
+CTRL_HISTORY = 8
+CTRL_FEATURES = 32
+
+
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rejects", C.c_int64), ("refactors", C.c_int64),
                 ("krylov_vectors", C.c_int64), ("solves", C.c_int64),
@@ -74,7 +84,12 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_step", "ers_run", "ers_get_state", "ers_set_state", "ers_get_state_dev",
            "ers_set_state_dev", "ers_solve", "ers_spmv_C", "ers_mevp", "ers_phi_small",
            "ers_stats", "ers_profile", "ers_analyze", "ers_last_error", "ers_destroy",
-           "ers_solve_dev_noalloc", "ers_create_batch", "ers_run_batch", "ers_get_state_inst"]
+           "ers_solve_dev_noalloc", "ers_create_batch", "ers_run_batch", "ers_get_state_inst",
+           "ers_ctrl_features", "ers_ctrl_target", "ers_mlp_nparam", "ers_mlp_create",
+           "ers_mlp_set_params", "ers_mlp_get_params", "ers_mlp_forward", "ers_mlp_forward_dev",
+           "ers_mlp_grad", "ers_mlp_adam_step", "ers_mlp_train", "ers_mlp_last_error",
+           "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
+           "ers_batch_samples", "ers_batch_ctrl_stats"]
 
 _lib = None
 
@@ -90,6 +105,7 @@ def lib():
     P, D, I32 = C.c_void_p, C.c_double, C.c_int32
     pd = C.POINTER(C.c_double)
     pi = C.POINTER(C.c_int32)
+    pf = C.POINTER(C.c_float)
     sig = {
         "ers_default_opts": ([C.POINTER(Opts)], C.c_int),
         "ers_create": ([C.POINTER(P), C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr),
@@ -114,6 +130,25 @@ def lib():
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
+        "ers_ctrl_features": ([C.POINTER(StepRecord), I32, pf], C.c_int),
+        "ers_ctrl_target": ([C.POINTER(StepRecord), I32, C.POINTER(StepRecord), pf], C.c_int),
+        "ers_mlp_nparam": ([], I32),
+        "ers_mlp_create": ([C.POINTER(P), C.c_uint64], C.c_int),
+        "ers_mlp_set_params": ([P, pf], C.c_int),
+        "ers_mlp_get_params": ([P, pf], C.c_int),
+        "ers_mlp_forward": ([P, pf, I32, pf], C.c_int),
+        "ers_mlp_forward_dev": ([P, P, I32, P, P], C.c_int),
+        "ers_mlp_grad": ([P, pf, pf, I32, pf, pf], C.c_int),
+        "ers_mlp_adam_step": ([P, pf, pf, I32, C.c_float, pf], C.c_int),
+        "ers_mlp_train": ([P, pf, pf, I32, I32, I32, C.c_float, C.c_uint64, pf], C.c_int),
+        "ers_mlp_last_error": ([P], C.c_char_p),
+        "ers_mlp_destroy": ([P], None),
+        "ers_batch_set_controller": ([P, P, I32], C.c_int),
+        "ers_batch_trace": ([P, I32], C.c_int),
+        "ers_batch_records": ([P, I32, C.POINTER(StepRecord), I32, pi], C.c_int),
+        "ers_batch_samples": ([P, pf, pf, I32, pi], C.c_int),
+        "ers_batch_ctrl_stats": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)], C.c_int),
         "ers_last_error": ([P], C.c_char_p),
         "ers_destroy": ([P], None),
     }
@@ -131,6 +166,123 @@ def _dptr(a: np.ndarray):
 
 def _iptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _records(recs) -> C.Array:
+    """Sequence of dicts / tuples (h, h_max, err, E, dF, m, m_max, landed, retries) -> array."""
+    arr = (StepRecord * max(len(recs), 1))()
+    for q, r in enumerate(recs):
+        if isinstance(r, dict):
+            arr[q] = StepRecord(**r)
+        else:
+            arr[q] = StepRecord(*r)
+    return arr
+
+
+def ctrl_features(recs) -> np.ndarray:
+    """Network input of the learned controller from a step history (host-only, see ers.h)."""
+    arr = _records(recs)
+    out = np.zeros(CTRL_FEATURES, np.float32)
+    rc = lib().ers_ctrl_features(arr, len(recs), _fptr(out))
+    if rc != 0:
+        raise ErsError(rc, "ers_ctrl_features")
+    return out
+
+
+def ctrl_target(recs, nxt):
+    """Training target (2 floats) of the step after recs[-1], or None if unusable."""
+    arr = _records(recs)
+    nx = _records([nxt])
+    out = np.zeros(2, np.float32)
+    rc = lib().ers_ctrl_target(arr, len(recs), nx, _fptr(out))
+    return out if rc == 0 else None
+
+
+class Mlp:
+    """The learned controller's network (ers_mlp_*): BF16 tensor-core forward/backward and Adam."""
+
+    def __init__(self, seed: int = 0):
+        L = lib()
+        self.nparam = int(L.ers_mlp_nparam())
+        self._h = C.c_void_p()
+        rc = L.ers_mlp_create(C.byref(self._h), int(seed))
+        if rc != 0:
+            msg = L.ers_mlp_last_error(self._h).decode() if self._h else ""
+            if self._h:
+                L.ers_mlp_destroy(self._h)
+            self._h = None
+            raise ErsError(rc, msg)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise ErsError(rc, lib().ers_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib().ers_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(self.nparam, np.float32)
+        self._check(lib().ers_mlp_get_params(self._h, _fptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.nparam
+        self._check(lib().ers_mlp_set_params(self._h, _fptr(p)))
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, CTRL_FEATURES)
+        Y = np.zeros((X.shape[0], 2), np.float32)
+        self._check(lib().ers_mlp_forward(self._h, _fptr(X), X.shape[0], _fptr(Y)))
+        return Y
+
+    def forward_dev(self, x_ptr: int, n: int, y_ptr: int, stream=None):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(lib().ers_mlp_forward_dev(self._h, C.c_void_p(x_ptr), int(n),
+                                              C.c_void_p(y_ptr),
+                                              C.c_void_p(handle) if handle else None))
+
+    def grad(self, X, T):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, CTRL_FEATURES)
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, 2)
+        g = np.zeros(self.nparam, np.float32)
+        loss = C.c_float(0.0)
+        self._check(lib().ers_mlp_grad(self._h, _fptr(X), _fptr(T), X.shape[0], _fptr(g),
+                                       C.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, X, T, lr: float = 1e-3) -> float:
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, CTRL_FEATURES)
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, 2)
+        loss = C.c_float(0.0)
+        self._check(lib().ers_mlp_adam_step(self._h, _fptr(X), _fptr(T), X.shape[0], float(lr),
+                                            C.byref(loss)))
+        return loss.value
+
+    def train(self, X, T, epochs: int = 50, batch: int = 256, lr: float = 1e-3,
+              seed: int = 0) -> float:
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, CTRL_FEATURES)
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, 2)
+        loss = C.c_float(0.0)
+        self._check(lib().ers_mlp_train(self._h, _fptr(X), _fptr(T), X.shape[0], int(epochs),
+                                        int(batch), float(lr), int(seed), C.byref(loss)))
+        return loss.value
 
 
 class _CsrHold:
@@ -370,6 +522,37 @@ class BatchSimulator(Simulator):
         self._check(lib().ers_run_batch(self._ctx, float(t_end), float(tol), int(max_steps),
                                         _iptr(ns), _iptr(nr)))
         return ns, nr
+
+    def set_controller(self, mlp: Optional["Mlp"], parts: int = 3):
+        """Learned (h, m) proposer (None = the plain controller of Alg. 2); parts: 1 = use the
+        proposed step size, 2 = the proposed first residual-test dimension, 3 = both."""
+        self._mlp = mlp
+        self._check(lib().ers_batch_set_controller(self._ctx, mlp.handle if mlp else None,
+                                                   int(parts)))
+
+    def trace(self, enable: bool = True):
+        self._check(lib().ers_batch_trace(self._ctx, int(bool(enable))))
+
+    def records(self, k: int) -> list:
+        cnt = C.c_int32(0)
+        self._check(lib().ers_batch_records(self._ctx, int(k), None, 0, C.byref(cnt)))
+        arr = (StepRecord * max(cnt.value, 1))()
+        self._check(lib().ers_batch_records(self._ctx, int(k), arr, cnt.value, C.byref(cnt)))
+        return [{f: getattr(arr[q], f) for f, _ in StepRecord._fields_} for q in range(cnt.value)]
+
+    def samples(self):
+        cnt = C.c_int32(0)
+        self._check(lib().ers_batch_samples(self._ctx, None, None, 0, C.byref(cnt)))
+        X = np.zeros((max(cnt.value, 1), CTRL_FEATURES), np.float32)
+        T = np.zeros((max(cnt.value, 1), 2), np.float32)
+        self._check(lib().ers_batch_samples(self._ctx, _fptr(X), _fptr(T), cnt.value,
+                                            C.byref(cnt)))
+        return X[:cnt.value], T[:cnt.value]
+
+    def ctrl_stats(self) -> dict:
+        a, b, k = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        self._check(lib().ers_batch_ctrl_stats(self._ctx, C.byref(a), C.byref(b), C.byref(k)))
+        return {"proposals": a.value, "rejected": b.value, "krylov_vectors": k.value}
 
     def state_inst(self, k: int):
         x = np.zeros(self.sizes[k])
