@@ -1118,7 +1118,9 @@ void ers_destroy(ers_ctx* c) {
                   (void*)c->d_src_inst, (void*)c->bks, (void*)c->bH, (void*)c->bh, (void*)c->bt,
                   (void*)c->bred, (void*)c->bmask, (void*)c->bcount,
                   (void*)c->d_mstart, (void*)c->d_mused, (void*)c->bdf, (void*)c->d_feat,
-                  (void*)c->d_pred, (void*)c->d_kv, (void*)c->d_where})
+                  (void*)c->d_pred, (void*)c->d_kv, (void*)c->d_where,
+                  (void*)c->bscan_res, (void*)c->bscan_last, (void*)c->bscan_fin,
+                  (void*)c->bscan_y})
     f(p);
   for (auto& ev : c->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }

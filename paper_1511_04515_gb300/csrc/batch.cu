@@ -217,6 +217,86 @@ __global__ void k_bsmall(BArgs A) {
   }
 }
 
+// Parallel residual tests (Eq. 16) of the dimensions a proposed m_first skipped: one CTA per
+// (instance, space, dimension d = d0 + blockIdx.z) of every space flagged by small_decide.
+// Results go to per-(space, dimension) scratch: residual, finiteness, e_d^T H^-1 y and y.
+struct ScanBuf {
+  double* res;    // [slot][inst][MAX_M + 1]
+  double* last;
+  int32_t* fin;
+  double* y;      // [slot][inst][MAX_M + 1][MAX_M]
+};
+__device__ __forceinline__ int64_t scan_idx(const BArgs& A, int slot, int i, int d) {
+  return ((int64_t)slot * A.ninst + i) * (MAX_M + 1) + d;
+}
+
+__global__ void k_bscan(BArgs A, ScanBuf S, int d0) {
+  extern __shared__ double smem[];
+  __shared__ int ipiv[MAX_M];
+  const int i = blockIdx.x, b = blockIdx.y, slot = A.slot[b], d = d0 + blockIdx.z;
+  if (!A.mask[i]) return;
+  const KrylovState& K = A.ks[slot * A.ninst + i];
+  if (!K.scan || d > K.built || K.beta <= 0.0) return;
+  const double* H = bH_of(A, slot, i);
+  const int ldh = MAX_M + 1;
+  const int64_t q = scan_idx(A, slot, i, d);
+  bool fin = phi_small(H, ldh, d, A.h[i], S.y + q * MAX_M, S.last + q, smem, ipiv, A.pade);
+  if (threadIdx.x == 0) {
+    double res = H[d + (d - 1) * ldh] * K.gvnext[d - 1] * fabs(S.last[q]) / K.gv1;
+    S.res[q] = fin ? res : INFINITY;
+    S.fin[q] = fin ? 1 : 0;
+  }
+}
+
+// The decision after a parallel scan: the first dimension in [m_min, built] that passes, as
+// the plain rule's per-iteration tests would find it; at m_max with none passing, the
+// never-converged choice of small_decide.  One warp per (instance, space).
+__global__ void k_bpick(BArgs A, ScanBuf S) {
+  const int i = blockIdx.x % A.ninst, b = blockIdx.x / A.ninst, slot = A.slot[b];
+  const int lane = threadIdx.x;
+  if (!A.mask[i]) return;
+  KrylovState& K = A.ks[slot * A.ninst + i];
+  if (!K.scan) return;
+  const int built = K.built;
+  int chosen = 0;
+  double best = K.best_res;
+  int best_m = K.best_m;
+  for (int d = A.m_min; d <= built; ++d) {
+    const int64_t q = scan_idx(A, slot, i, d);
+    double r = S.res[q];
+    if (isfinite(r) && r < best) { best = r; best_m = d; }
+    if (isfinite(r) && r < A.eps) { chosen = d; break; }
+  }
+  bool finish = chosen > 0;
+  if (!finish && built >= A.m_max) {
+    chosen = best_m > 0 ? best_m : built;
+    while (chosen > 1 && !S.fin[scan_idx(A, slot, i, chosen)]) --chosen;
+    finish = true;
+  }
+  __syncwarp();
+  if (finish) {
+    const int64_t q = scan_idx(A, slot, i, chosen);
+    for (int k = lane; k < chosen; k += 32) K.y[k] = S.y[q * MAX_M + k];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    K.res = S.res[scan_idx(A, slot, i, chosen > 0 ? chosen : built)];
+    K.best_res = best;
+    K.best_m = best_m;
+    if (finish) {
+      const int64_t q = scan_idx(A, slot, i, chosen);
+      K.last = S.last[q];
+      K.m = chosen;
+      K.done = 1;
+      if (!S.fin[q]) {
+        atomicOr(A.status, ST_KRYLOV);
+        note_nonfinite(A.where, ST_KRYLOV, i, slot, chosen);
+      }
+    }
+    K.scan = 0;
+  }
+}
+
 // largest dimension chosen by the spaces of each instance
 // (spaces 0 .. nb-1)
 __global__ void k_bmused(int ninst, int nb, const KrylovState* ks, int32_t* out) {
@@ -382,12 +462,23 @@ ers_status launch_bsmall(ers_ctx* c, BArgs A, int mode) {
   return ERS_OK;
 }
 
-// Algorithm 1 up to the MEVP for the spaces `slots` of every masked instance (adaptive m).
-// No space can finish before it has `first_test` directions (the smallest dimension at which
-// a residual test runs) unless it breaks down, and a broken-down space only skips work, so the
-// host polls for completion from that iteration on.
-ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src, int first_test) {
+ScanBuf scan_buf(ers_ctx* c) {
+  return ScanBuf{c->bscan_res, c->bscan_last, c->bscan_fin, c->bscan_y};
+}
+
+// Algorithm 1 up to the MEVP for the spaces `slots` of every instance set in `mask` (the host
+// copy of the device mask; adaptive m).  No space can finish before its first decision (at
+// m_min, or at the proposed dimension) unless it breaks down, and a broken-down space only
+// skips work, so the host polls for completion from the smallest first decision on.
+ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
+                       const std::vector<int32_t>& mask) {
   const int mc = c->opts.m_max;
+  int first_test = mc;
+  for (int i = 0; i < c->ninst; ++i)
+    if (mask[i])
+      first_test = std::min(first_test, c->ctrl ? std::max(c->mstart_inst[i], c->opts.m_min)
+                                                : c->opts.m_min);
+  c->scan_mask = mask;
   BArgs A = make_bargs(c, nb, slots, src, 1);
   k_binit<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(A);
   c->stats.kernel_launches++;
@@ -415,6 +506,21 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
     c->stats.kernel_launches++;
     ers_status st = launch_bsmall(c, A, SMALL_RESID);
     if (st != ERS_OK) return st;
+    // instances whose proposed first decision is at dimension j + 1: test [m_min, j + 1]
+    if (c->ctrl && j + 1 > c->opts.m_min) {
+      bool any = false;
+      for (int i = 0; i < c->ninst && !any; ++i)
+        any = c->scan_mask[i] && c->mstart_inst[i] == j + 1;
+      if (any) {
+        const int nd = j + 1 - c->opts.m_min + 1;
+        size_t mm = (size_t)c->opts.m_max;
+        size_t sm = (6 * mm * mm + 2 * mm) * 8;
+        k_bscan<<<dim3(c->ninst, nb, nd), 256, sm, c->stream>>>(A, scan_buf(c), c->opts.m_min);
+        k_bpick<<<c->ninst * nb, 32, 0, c->stream>>>(A, scan_buf(c));
+        c->stats.kernel_launches += 2;
+        BCU(cudaGetLastError());
+      }
+    }
   }
   return ERS_OK;
 }
@@ -567,6 +673,15 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
   c->proposed_inst.assign(ninst, 0);
   BCU(cudaFuncSetAttribute(k_bsmall, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
+  BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
+  {
+    const size_t nq = (size_t)3 * ninst * (MAX_M + 1);
+    BCU(cudaMalloc((void**)&c->bscan_res, sizeof(double) * nq));
+    BCU(cudaMalloc((void**)&c->bscan_last, sizeof(double) * nq));
+    BCU(cudaMalloc((void**)&c->bscan_fin, sizeof(int32_t) * nq));
+    BCU(cudaMalloc((void**)&c->bscan_y, sizeof(double) * nq * MAX_M));
+  }
   return ERS_OK;
 }
 
@@ -589,7 +704,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   int round = 0;
   std::vector<int32_t> ones(ninst, 1);
   while (max_steps <= 0 || round < max_steps) {
-    int nact = 0, first_test = o.m_max;
+    int nact = 0;
     for (int i = 0; i < ninst; ++i) {
       active[i] = c->t_inst[i] < t_end * (1 - 1e-12);
       nact += active[i];
@@ -600,7 +715,6 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       landed[i] = h[i] == nb - c->t_inst[i];
       retries[i] = 0;
       if (!c->ctrl) c->mstart_inst[i] = o.m_min;
-      first_test = std::min(first_test, std::max(c->mstart_inst[i], o.m_min));
     }
     if (nact == 0) break;
     // error budgets from ||x_i||_inf
@@ -642,7 +756,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     int slots[2] = {0, 1};
     double* src[2] = {c->v1, c->v2};
     const int nsol = ramp ? 2 : 1;
-    st = batch_bases(c, nsol, slots, src, first_test);
+    st = batch_bases(c, nsol, slots, src, active);
     if (st != ERS_OK) return st;
     k_bmused<<<nblk(ninst), 256, 0, c->stream>>>(ninst, nsol, c->bks, c->d_mused);
     BCU(cudaMemcpyAsync(mused.data(), c->d_mused, sizeof(int32_t) * ninst, cudaMemcpyDeviceToHost, c->stream));
@@ -674,7 +788,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
         BCU(cudaMemcpyAsync(c->ve, c->solve_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
         int es = 2;
         double* esrc[1] = {c->ve};
-        st = batch_bases(c, 1, &es, esrc, o.m_min);
+        st = batch_bases(c, 1, &es, esrc, trying);
         if (st != ERS_OK) return st;
         BCombine Er{};
         Er.n = n; Er.ninst = ninst; Er.nb = 1; Er.out = c->tmp; Er.in = nullptr; Er.a = 0.0;

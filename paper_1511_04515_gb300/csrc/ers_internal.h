@@ -38,7 +38,8 @@ struct KrylovState {
   int best_m;
   int done;             // 1 = converged / breakdown / zero vector: no further iterations
   int breakdown;
-  int pad[3];
+  int scan;             // 1 = the skipped dimensions [m_min, built] await a parallel test
+  int pad[2];
 };
 
 // A set of Krylov spaces advanced in lockstep (their solves share one pass over the factors).
@@ -152,6 +153,9 @@ struct ers_ctx {
   int32_t* bcount = nullptr;           // 1
   unsigned long long* d_kv = nullptr;  // Krylov vectors built by the batched Arnoldi kernels
   unsigned* d_where = nullptr;         // first non-finite value of a batched run (4 words)
+  double *bscan_res = nullptr, *bscan_last = nullptr, *bscan_y = nullptr;  // per (space, dim)
+  int32_t* bscan_fin = nullptr;
+  std::vector<int32_t> scan_mask;      // instances masked in the current batch_bases call
   int ctrl_parts = 0;                  // ERS_CTRL_H | ERS_CTRL_M: which proposals are used
   // learned step controller of batched runs
   ers_mlp* ctrl = nullptr;             // not owned; nullptr = plain controller

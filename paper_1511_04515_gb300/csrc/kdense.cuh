@@ -206,12 +206,14 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
 // (mode RESID), at the end of a fixed-dimension run (FIXED_END), or for an existing basis at
 // a new h (FINAL).  Writes y = exp(h H_m^-1) e_1 and m into the space's state.
 //
-// m_first (>= m_min) is the first dimension whose residual is tested; the plain rule has
-// m_first = m_min.  A larger m_first (a proposed dimension) skips the tests below it; if the
-// first test there is not finite, or the basis breaks down before it, the skipped dimensions
-// are tested in increasing order and the first that passes is used, which is the dimension
-// the plain rule picks: past its converged dimension a basis gathers rounding-noise
-// directions whose spurious Ritz values make exp(h H^-1) overflow.
+// m_first (>= m_min) is the dimension at which the first decision is taken; the plain rule
+// has m_first = m_min.  A larger m_first (a proposed dimension) skips the tests below it.
+// When the basis reaches m_first the space is flagged (K.scan) and the caller tests the
+// dimensions [m_min, m_first] in parallel, taking the first that passes; if the basis breaks
+// down before m_first, the skipped dimensions are tested here in increasing order.  Either way
+// the chosen dimension is the one the plain rule picks, and never a larger one: past its
+// converged dimension a basis gathers rounding-noise directions whose spurious Ritz values
+// can pass the residual test with a wrong exp(h H^-1) e_1.
 __device__ inline void small_decide(int mode, const double* H, KrylovState& K, double h,
                                     double eps, int m_min, int m_max, int m_first, double* smem,
                                     int* ipiv, double* ybuf, double* s_last, unsigned* status,
@@ -293,10 +295,11 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
     return;
   }
   int jj = s_built;
-  if (jj >= m_first || jj >= m_max) {
-    if (jj >= m_min && test_dim(jj)) return;
-    if (jj == m_first && m_first > m_min && !isfinite(K.res) && scan_skipped(jj - 1)) return;
+  if (m_first > m_min && jj == m_first) {
+    if (threadIdx.x == 0) K.scan = 1;   // [m_min, m_first] are tested in parallel by the caller
+    return;
   }
+  if (jj >= m_first && jj >= m_min && test_dim(jj)) return;
   if (jj >= m_max) {
     // never converged: the dimension with the smallest finite residual; when no tested
     // dimension had one, the largest dimension whose exp(h H^-1) e_1 is finite
