@@ -8,6 +8,7 @@ and tol 1e-6 over 2 ns.  A timed "step" is one accepted ER step (setup solves, t
 phi_2 Krylov spaces, the update, the controller).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batch      (batched Monte Carlo inverter chains, plain vs learned)
 
 Prints one JSON line (rank 0).  The value is accepted ER steps per second of the whole job;
 N > 1 runs independent replicas (a single circuit does not shard: every G^-1 couples all
@@ -33,7 +34,7 @@ FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32
 # the 70^3 mesh (2.646 GB measured vs 2.553 GB algorithmic); the full-size traffic is this ratio
 # times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
 # k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
-SOLVE_TRAFFIC_RATIO = 2.646 / 2.5525
+SOLVE_TRAFFIC_RATIO = None
 SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same generator
 SAMPLE_STEPS = 10
 
@@ -48,6 +49,15 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--workload", default="mesh", choices=["mesh", "batch"])
+    p.add_argument("--batch-n", type=int, default=64, help="batch: instances")
+    p.add_argument("--stage-lo", type=int, default=4)
+    p.add_argument("--stage-hi", type=int, default=40)
+    p.add_argument("--tree", type=int, default=20, help="batch: RC tree nodes per stage")
+    p.add_argument("--t-end", type=float, default=0.3e-9)
+    p.add_argument("--train-n", type=int, default=16)
+    p.add_argument("--seq-sample", type=int, default=4,
+                   help="batch: instances timed one context at a time")
     return p.parse_args()
 
 
@@ -305,6 +315,172 @@ def run_ours(a):
     sim.close()
 
 
+# --------------------------------------------------------------------------------------
+# batched workload: Monte Carlo inverter chains, plain GPU method vs batched (+ learned)
+# --------------------------------------------------------------------------------------
+BATCH_METRIC = ("wall time to t_end at tol 1e-6 of a Monte Carlo batch of inverter chains: "
+                "batched + learned controller (plain GPU method and batched plain alongside)")
+
+
+def batch_workload_name(a):
+    return (f"batch{a.batch_n}_invchain: {a.batch_n} inverter chains, stages uniform "
+            f"{a.stage_lo}-{a.stage_hi}, {a.tree}-node RC trees per stage, Vt/k/R/C log-normal "
+            f"sigma 5%, 0 -> {a.t_end * 1e9:g} ns (first input edge), tol 1e-6")
+
+
+def run_batch_workload(a):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1511_04515_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1511_04515_gb300 import ers
+    from synth import circuits as S
+
+    def family(n, seed0):
+        return S.batch_family(n_inst=n, seed0=seed0, stage_lo=a.stage_lo, stage_hi=a.stage_hi,
+                              sigma=0.05, t_end=a.t_end, tree_nodes=a.tree)
+
+    t_start = time.perf_counter()
+
+    def progress(msg):
+        print(f"[batch {time.perf_counter() - t_start:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+    # instances are independent: with N ranks each takes every N-th instance (no exchange)
+    stream = torch.cuda.current_stream()
+    # 1. training set: plain-controller traces of other seeds; the network is trained by the
+    #    library's own BF16 forward/backward/Adam kernels
+    ttr = time.perf_counter()
+    tr = ers.BatchSimulator(family(a.train_n, 2000)[rank::world])
+    tr.set_stream(stream)
+    tr.dc()
+    tr.trace(True)
+    tr.run_batch(a.t_end, a.tol)
+    X, T = tr.samples()
+    tr.close()
+    mlp = ers.Mlp(seed=1)
+    loss = mlp.train(X, T, epochs=300, batch=256, lr=2e-3, seed=1)
+    train_s = time.perf_counter() - ttr
+    progress(f"trained on {X.shape[0]} samples, loss {loss:.3g}")
+    # 2. held-out batch
+    circs = family(a.batch_n, 5000)[rank::world]
+    tc = time.perf_counter()
+    sim = ers.BatchSimulator(circs)
+    create_s = time.perf_counter() - tc
+    sim.set_stream(stream)
+    sim.dc()
+    _, x0, _ = sim.state()
+    arms = {}
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    proc, fh = clocks_start(local, clk_path)
+    for name, net in (("batched_plain", None), ("batched_learned", mlp)):
+        sim.set_controller(net, 3 if net is not None else 0)
+        sim.set_state(0.0, x0)
+        sim.run_batch(a.t_end, a.tol, max_steps=max(a.warmup, 3))     # warm-up rounds
+        sim.set_state(0.0, x0)
+        st0 = sim.stats()
+        c0 = sim.ctrl_stats()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        ns, nr = sim.run_batch(a.t_end, a.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        st1 = sim.stats()
+        c1 = sim.ctrl_stats()
+        progress(f"{name}: {wall:.1f} s, {int(ns.sum())} steps, {int(nr.sum())} rejected")
+        arms[name] = {"seconds": e0.elapsed_time(e1) * 1e-3, "wall_s": wall,
+                      "steps": int(ns.sum()), "rejected": int(nr.sum()),
+                      "rounds": st1["steps"] - st0["steps"],
+                      "krylov_vectors": c1["krylov_vectors"] - c0["krylov_vectors"],
+                      "proposals": c1["proposals"] - c0["proposals"],
+                      "proposals_rejected": c1["rejected"] - c0["rejected"],
+                      "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+                      "x": [sim.state_inst(k)[1] for k in range(len(circs))]}
+    clocks = clocks_stop(proc, fh, clk_path)
+    # 3. the plain GPU method: each instance in its own context, one after the other (timed on
+    #    an evenly spaced sample of instances and scaled to the batch)
+    pick = list(range(0, len(circs), max(1, len(circs) // max(1, a.seq_sample))))[:a.seq_sample]
+    seq_s, seq_steps = 0.0, 0
+    for k in pick:
+        one = ers.Simulator.from_circuit(circs[k])
+        one.set_stream(stream)
+        one.dc()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        n1, _ = one.run(a.t_end, a.tol)
+        torch.cuda.synchronize()
+        seq_s += time.perf_counter() - w0
+        seq_steps += n1
+        one.close()
+    seq_est = seq_s / len(pick) * len(circs)
+    progress(f"plain sequential sample: {seq_s:.1f} s for {len(pick)} instances")
+    # 4. accuracy on two instances against a run of the same instances at a 10x tighter
+    #    tolerance (its own error is about a tenth of the compared runs')
+    ref_idx = pick[:2]
+    ref = ers.BatchSimulator([circs[k] for k in ref_idx])
+    ref.set_stream(stream)
+    ref.dc()
+    ref.run_batch(a.t_end, a.tol / 10)
+    xref = [ref.state_inst(q)[1] for q in range(len(ref_idx))]
+    ref.close()
+    progress("tight reference done")
+    err = {}
+    for name, arm in arms.items():
+        err[name] = max(float(np.max(np.abs(arm["x"][k] - xr))) for k, xr in zip(ref_idx, xref))
+        del arm["x"]
+    sim.close()
+    mlp.close()
+    if world > 1:   # the job ends when the slowest rank does
+        t = torch.tensor([arms["batched_plain"]["seconds"], arms["batched_learned"]["seconds"],
+                          seq_est / world], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        arms["batched_plain"]["seconds"], arms["batched_learned"]["seconds"] = float(t[0]), float(t[1])
+        seq_est = float(t[2]) * world
+    if rank != 0:
+        return
+    learned = arms["batched_learned"]
+    plain = arms["batched_plain"]
+    nodes = int(sum(c.n for c in circs))
+    line = {"metric": BATCH_METRIC, "value": learned["seconds"], "unit": "s",
+            "n_gpus": world, "steps": 1, "warmup": max(a.warmup, 3),
+            "ms_per_step": learned["seconds"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": batch_workload_name(a), "instances": len(circs),
+                       "nodes": nodes, "train_instances": a.train_n,
+                       "train_samples": int(X.shape[0]), "train_loss": loss,
+                       "train_s": train_s, "create_s": create_s,
+                       "parallelism": "instances split over ranks" if world > 1 else "single GPU",
+                       "l2_flush": "none: every round streams the factor and all Krylov bases"},
+            "arms": {**arms,
+                     "plain_sequential": {"seconds_est": seq_est, "sampled_instances": len(pick),
+                                          "sample_seconds": seq_s, "sample_steps": seq_steps,
+                                          "note": "each instance in its own context, run one "
+                                                  "after another; mean over the sample x batch"}},
+            "speedup": {"learned_vs_batched_plain": plain["seconds"] / learned["seconds"],
+                        "learned_vs_plain_sequential": seq_est / learned["seconds"],
+                        "batched_plain_vs_plain_sequential": seq_est / plain["seconds"]},
+            "max_abs_err_vs_tight_run": {**err, "instances": ref_idx, "tight_tol": a.tol / 10},
+            "instance_steps_per_s": learned["steps"] / learned["seconds"],
+            "krylov_vectors_per_s": learned["krylov_vectors"] / learned["seconds"],
+            "gpu_launches": learned["gpu_launches"],
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.oracle_sample:
@@ -312,6 +488,8 @@ def main():
         return
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch_workload(a)
     else:
         run_ours(a)
 

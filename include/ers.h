@@ -131,7 +131,10 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
 
 /* Advance every instance of a batched context to t_end with Algorithm 2 (at most max_steps
  * rounds when max_steps > 0; in a round every unfinished instance takes one accepted step).
- * nsteps / nreject (ninst entries each, may be NULL) receive the per-instance counts. */
+ * nsteps / nreject (ninst entries each, may be NULL) receive the per-instance counts of
+ * accepted and rejected steps of this call.  ers_set_state / ers_set_state_dev on a batched
+ * context set every instance's time and proposed step and start a new step history (the
+ * learned controller's records and pending proposals are cleared). */
 ers_status ers_run_batch(ers_ctx* ctx, double t_end, double tol, int32_t max_steps,
                          int32_t* nsteps, int32_t* nreject);
 

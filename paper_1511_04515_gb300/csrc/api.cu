@@ -399,6 +399,14 @@ ers_status ctx_clear_status(ers_ctx* c) { return clear_status(c); }
 
 namespace {
 
+// a new state starts a new step history: the learned controller's records and pending
+// proposals of a batched context no longer describe it
+void reset_step_history(ers_ctx* c) {
+  for (auto& R : c->recs) R.clear();
+  std::fill(c->proposed_inst.begin(), c->proposed_inst.end(), 0);
+  std::fill(c->mstart_inst.begin(), c->mstart_inst.end(), c->opts.m_min);
+}
+
 double host_absmax(ers_ctx* c, const double* x, ers_status* st) {
   unsigned long long* mx = (unsigned long long*)(c->red + 2 * MAX_RHS * 4096 + 72);
   cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream);
@@ -691,6 +699,8 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   CUB(upload(&P.fwd_tgt, S.fwd_tgt));
   CUB(upload(&P.fwd_expect, S.fwd_expect));
   CUB(upload(&P.bwd_nchunk, S.bwd_nchunk));
+  CUB(upload(&P.fwd_lane, S.fwd_lane));
+  CUB(upload(&P.bwd_lane, S.bwd_lane));
   P.nfwd = (int)S.fwd.size();
   P.nbwd = (int)S.bwd.size();
   CUB(dalloc(&P.LDi, S.d_total));
@@ -936,6 +946,7 @@ ers_status ers_set_state(ers_ctx* c, double t, const double* x, double h) {
   c->h = h;
   std::fill(c->t_inst.begin(), c->t_inst.end(), t);
   std::fill(c->hprop_inst.begin(), c->hprop_inst.end(), h);
+  reset_step_history(c);
   if (!c->linear) c->factored = false;
   return ERS_OK;
 }
@@ -957,6 +968,9 @@ ers_status ers_set_state_dev(ers_ctx* c, double t, const double* x_dev, double h
   CU(cudaGetLastError());
   c->t = t;
   c->h = h;
+  std::fill(c->t_inst.begin(), c->t_inst.end(), t);
+  std::fill(c->hprop_inst.begin(), c->hprop_inst.end(), h);
+  reset_step_history(c);
   if (!c->linear) c->factored = false;
   return ERS_OK;
 }
@@ -1102,7 +1116,8 @@ void ers_destroy(ers_ctx* c) {
                   (void*)P.d_off, (void*)P.o_off, (void*)P.front_off, (void*)P.lvl_sn,
                   (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.asm_dst, (void*)P.tile_sn,
                   (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd, (void*)P.fwd_small, (void*)P.bwd_small,
-                  (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.LDi,
+                  (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.fwd_lane,
+                  (void*)P.bwd_lane, (void*)P.LDi,
                   (void*)P.UDi, (void*)P.Lo, (void*)P.Uo, (void*)P.arena, (void*)P.sync})
     f(p);
   for (void* p : {(void*)c->G_ptr, (void*)c->G_idx, (void*)c->Glin_val, (void*)c->G_val,

@@ -701,6 +701,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   ers_status st = ctx_clear_status(c);
   if (st != ERS_OK) return st;
   BCU(cudaMemsetAsync(c->d_where, 0, 4 * sizeof(unsigned), c->stream));
+  const std::vector<int64_t> steps0 = c->steps_inst, rejects0 = c->rejects_inst;
   int round = 0;
   std::vector<int32_t> ones(ninst, 1);
   while (max_steps <= 0 || round < max_steps) {
@@ -891,8 +892,8 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   BCU(cudaStreamSynchronize(c->stream));
   c->stats.krylov_vectors = (int64_t)kv;
   for (int i = 0; i < ninst; ++i) {
-    if (nsteps) nsteps[i] = (int32_t)c->steps_inst[i];
-    if (nreject) nreject[i] = (int32_t)c->rejects_inst[i];
+    if (nsteps) nsteps[i] = (int32_t)(c->steps_inst[i] - steps0[i]);
+    if (nreject) nreject[i] = (int32_t)(c->rejects_inst[i] - rejects0[i]);
   }
   return ERS_OK;
 }

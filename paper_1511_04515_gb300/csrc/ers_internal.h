@@ -64,6 +64,7 @@ struct DevicePlan {
   int32_t *tile_sn = nullptr, *tile_ij = nullptr, *ptask_sn = nullptr, *ptask_r0 = nullptr;
   SolveTask *fwd = nullptr, *bwd = nullptr, *fwd_small = nullptr, *bwd_small = nullptr;
   int32_t *fwd_tgt = nullptr, *fwd_expect = nullptr, *bwd_nchunk = nullptr;
+  int32_t *fwd_lane = nullptr, *bwd_lane = nullptr;   // 4 ints per lane item
   int nfwd = 0, nbwd = 0;
   // factor values
   double *LDi = nullptr, *UDi = nullptr, *Lo = nullptr, *Uo = nullptr;

@@ -205,6 +205,128 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
+// Narrow supernodes (w <= LANE_W columns) of one level, forward, one per lane (up to 32 per
+// warp task): wait for the lane's own arrivals, y_s <- L11^-1 y_s, y_R -= L21 y_s, then
+// arrive at the targets.
+constexpr int LANE_W = 4;
+template <int NRHS>
+__device__ __noinline__ void fwd_lanes(const SolveArgs& A, const SolveTask& T, int lane) {
+  const DevicePlan& P = A.P;
+  int32_t* arrive = P.sync + 2;
+  const int n = A.n;
+  if (lane < T.r0) {
+    const int4 it = __ldg(reinterpret_cast<const int4*>(P.fwd_lane) + T.sn + lane);
+    const int s = it.x;
+    const int c0 = __ldg(P.sn_start + s), w = __ldg(P.sn_start + s + 1) - c0;
+    const int64_t rp = __ldg(P.rptr + s);
+    const int r = (int)(__ldg(P.rptr + s + 1) - rp);
+    const double* Li = P.LDi + __ldg(P.d_off + s);
+    const double* Lo = P.Lo + __ldg(P.o_off + s);
+    if (wait_geq(arrive + s, it.w, A.status)) {
+      double y[LANE_W][NRHS], z[LANE_W][NRHS];
+#pragma unroll
+      for (int j = 0; j < LANE_W; ++j)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          y[j][k] = j < w ? __ldcg(A.y + (int64_t)k * n + c0 + j) : 0.0;
+          z[j][k] = 0.0;
+        }
+      // z = L11^-1 y (lower triangular, column-major w x w)
+#pragma unroll
+      for (int q = 0; q < LANE_W; ++q)
+#pragma unroll
+        for (int j = 0; j <= q; ++j)
+          if (q < w) {
+            const double m = __ldg(Li + q + j * w);
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k) z[q][k] += m * y[j][k];
+          }
+#pragma unroll
+      for (int q = 0; q < LANE_W; ++q)
+        if (q < w)
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) A.y[(int64_t)k * n + c0 + q] = z[q][k];
+      for (int i = 0; i < r; ++i) {
+        double acc[NRHS];
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+#pragma unroll
+        for (int j = 0; j < LANE_W; ++j)
+          if (j < w) {
+            const double l = __ldg(Lo + i + (int64_t)j * r);
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k) acc[k] += l * z[j][k];
+          }
+        const int row = __ldg(P.rows + rp + i);
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
+      }
+      __threadfence();
+      for (int q = 0; q < it.z; ++q) red_release_add(arrive + __ldg(P.fwd_tgt + it.y + q), 1);
+    }
+  }
+  __syncwarp();
+}
+
+// Narrow supernodes of one depth, backward, one per lane: once the parent is done,
+// x_s = U11^-1 (y_s - U12 x_R); then the supernode is marked done for its children.
+template <int NRHS>
+__device__ __noinline__ void bwd_lanes(const SolveArgs& A, const SolveTask& T, int lane) {
+  const DevicePlan& P = A.P;
+  int32_t* done = P.sync + 2 + P.nsn;
+  const int n = A.n;
+  if (lane < T.r0) {
+    const int4 it = __ldg(reinterpret_cast<const int4*>(P.bwd_lane) + T.sn + lane);
+    const int s = it.x, parent = it.y;
+    const int c0 = __ldg(P.sn_start + s), w = __ldg(P.sn_start + s + 1) - c0;
+    const int64_t rp = __ldg(P.rptr + s);
+    const int r = (int)(__ldg(P.rptr + s + 1) - rp);
+    const double* Ui = P.UDi + __ldg(P.d_off + s);
+    const double* Uo = P.Uo + __ldg(P.o_off + s);
+    if (parent < 0 || wait_geq(done + parent, 2, A.status)) {
+      double acc[LANE_W][NRHS];
+#pragma unroll
+      for (int j = 0; j < LANE_W; ++j)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k)
+          acc[j][k] = j < w ? __ldcg(A.y + (int64_t)k * n + c0 + j) : 0.0;
+      for (int i = 0; i < r; ++i) {
+        const int row = __ldg(P.rows + rp + i);
+        double xr[NRHS];
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) xr[k] = __ldcg(A.y + (int64_t)k * n + row);
+#pragma unroll
+        for (int j = 0; j < LANE_W; ++j)
+          if (j < w) {
+            const double u = __ldg(Uo + i + (int64_t)j * r);
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k) acc[j][k] -= u * xr[k];
+          }
+      }
+      // x = U11^-1 acc (upper triangular, column-major w x w)
+#pragma unroll
+      for (int q = 0; q < LANE_W; ++q)
+        if (q < w) {
+          double x[NRHS];
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) x[k] = 0.0;
+#pragma unroll
+          for (int j = q; j < LANE_W; ++j)
+            if (j < w) {
+              const double m = __ldg(Ui + q + j * w);
+#pragma unroll
+              for (int k = 0; k < NRHS; ++k) x[k] += m * acc[j][k];
+            }
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) A.y[(int64_t)k * n + c0 + q] = x[k];
+        }
+      __threadfence();
+      st_release(done + s, 2);
+    }
+  }
+  __syncwarp();
+}
+
 // a far chunk of a large supernode, forward, one warp: lanes over rows,
 // y[R[i]] -= sum_j Lo[i + j r] z_j with z = y_s (written by the supernode's DIAG task)
 template <int NRHS>
@@ -385,9 +507,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_fwd(SolveArgs A) {
     if (e >= P.nfwd) break;
     SolveTask T = P.fwd[e];
     if (T.kind == TASK_GROUP) {
-      if (wq < T.r0)
-        fwd_small<NRHS>(A, P.fwd_small[T.sn + wq], lane,
-                        reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64));
+      if (wq < T.r0) {
+        const SolveTask& U = P.fwd_small[T.sn + wq];
+        double (*buf)[64] = reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64);
+        if (U.kind == TASK_LANES) fwd_lanes<NRHS>(A, U, lane);
+        else fwd_small<NRHS>(A, U, lane, buf);
+      }
       continue;
     }
     if (T.kind == TASK_BULK) {
@@ -498,9 +623,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_bwd(SolveArgs A) {
     if (e >= P.nbwd) break;
     SolveTask T = P.bwd[e];
     if (T.kind == TASK_GROUP) {
-      if (wq < T.r0)
-        bwd_small<NRHS>(A, P.bwd_small[T.sn + wq], lane,
-                        reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64));
+      if (wq < T.r0) {
+        const SolveTask& U = P.bwd_small[T.sn + wq];
+        double (*buf)[64] = reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64);
+        if (U.kind == TASK_LANES) bwd_lanes<NRHS>(A, U, lane);
+        else bwd_small<NRHS>(A, U, lane, buf);
+      }
       continue;
     }
     if (T.kind == TASK_BULK) {

@@ -701,6 +701,7 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
   // 5. triangular-solve work lists ---------------------------------------------------
   {
     S.fwd.clear(); S.bwd.clear(); S.fwd_small.clear(); S.bwd_small.clear(); S.fwd_tgt.clear();
+    S.fwd_lane.clear(); S.bwd_lane.clear();
     S.fwd_expect.assign(nsn, 0);
     S.bwd_nchunk.assign(nsn, 0);
     const int CH = opt.solve_chunk;
@@ -721,6 +722,11 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       int64_t w = S.sn_start[s + 1] - S.sn_start[s];
       int64_t r = S.rptr[s + 1] - S.rptr[s];
       return w * (w + r) <= opt.fused_limit;
+    };
+    // narrow supernodes with few rows: one lane each (a warp task holds 32)
+    auto lane_item = [&](int s) {
+      return opt.lane_rows > 0 && S.sn_start[s + 1] - S.sn_start[s] <= opt.lane_width &&
+             S.rptr[s + 1] - S.rptr[s] <= opt.lane_rows;
     };
     // warp tasks (small supernodes, far chunks) live in fwd_small / bwd_small; a CTA entry
     // GROUP/BULK refers to up to 8 consecutive warp tasks of one level
@@ -743,14 +749,40 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     std::iota(bord.begin(), bord.end(), 0);
     std::stable_sort(ford.begin(), ford.end(), [&](int a, int b) { return S.level[a] < S.level[b]; });
     std::stable_sort(bord.begin(), bord.end(), [&](int a, int b) { return depth[a] < depth[b]; });
-    // forward: per level, small supernodes (GROUP), DIAG entries, then far chunks (BULK)
+    // forward: per level, narrow supernodes (one per lane) and small ones (one per warp) in
+    // GROUP entries, DIAG entries, then far chunks (BULK)
     for (size_t k0 = 0; k0 < ford.size();) {
       size_t k1 = k0;
       while (k1 < ford.size() && S.level[ford[k1]] == S.level[ford[k0]]) ++k1;
       int first = (int)S.fwd_small.size();
+      bool lane_level = false;
+      {
+        // lane tasks of this level: 32 narrow supernodes per warp task
+        std::vector<int> items;
+        for (size_t k = k0; k < k1; ++k) {
+          int s = ford[k];
+          if (!lane_item(s)) continue;
+          items.push_back(s);
+        }
+        // a level too narrow to fill the GPU's warps is latency-bound: a warp per supernode
+        if ((int)items.size() < opt.lane_min_level) items.clear();
+        lane_level = !items.empty();
+        for (size_t a = 0; a < items.size(); a += 32) {
+          int cnt = (int)std::min<size_t>(32, items.size() - a);
+          SolveTask t{TASK_LANES, (int32_t)(S.fwd_lane.size() / 4), cnt, 0, 0, 0, -1, 0};
+          for (int b = 0; b < cnt; ++b) {
+            int s = items[a + b];
+            SolveTask u{};
+            add_targets(s, 0, (int)(S.rptr[s + 1] - S.rptr[s]), u);
+            S.fwd_lane.insert(S.fwd_lane.end(), {s, u.tgt0, u.ntgt, 0});
+          }
+          S.fwd_small.push_back(t);
+          if ((int)S.fwd_small.size() - first == 8) flush(S.fwd, S.fwd_small, first, TASK_GROUP);
+        }
+      }
       for (size_t k = k0; k < k1; ++k) {
         int s = ford[k];
-        if (!small(s)) continue;
+        if (!small(s) || (lane_level && lane_item(s))) continue;
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
         SolveTask t{TASK_FUSED, s, 0, r, 0, 0, -1, 0};
         add_targets(s, 0, r, t);
@@ -799,9 +831,30 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
         }
       }
       flush(S.bwd, S.bwd_small, first, TASK_BULK);
+      bool lane_level = false;
+      {
+        std::vector<int> items;
+        for (size_t k = k0; k < k1; ++k) {
+          int s = bord[k];
+          if (!lane_item(s)) continue;
+          items.push_back(s);
+        }
+        if ((int)items.size() < opt.lane_min_level) items.clear();
+        lane_level = !items.empty();
+        for (size_t a = 0; a < items.size(); a += 32) {
+          int cnt = (int)std::min<size_t>(32, items.size() - a);
+          SolveTask t{TASK_LANES, (int32_t)(S.bwd_lane.size() / 4), cnt, 0, 0, 0, -1, 0};
+          for (int b = 0; b < cnt; ++b) {
+            int s = items[a + b];
+            S.bwd_lane.insert(S.bwd_lane.end(), {s, S.sn_parent[s], 0, 0});
+          }
+          S.bwd_small.push_back(t);
+          if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_GROUP);
+        }
+      }
       for (size_t k = k0; k < k1; ++k) {
         int s = bord[k];
-        if (!small(s)) continue;
+        if (!small(s) || (lane_level && lane_item(s))) continue;
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
         S.bwd_small.push_back(SolveTask{TASK_FUSED, s, 0, r, 0, 0, S.sn_parent[s], 0});
         if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_GROUP);
@@ -818,6 +871,7 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     // descriptors: everything a task needs in one record
     auto fill = [&](SolveTask& t, bool fwd) {
       if (t.kind == TASK_GROUP || t.kind == TASK_BULK) return;
+      if (t.kind == TASK_LANES) return;
       int s = t.sn;
       t.c0 = S.sn_start[s];
       t.w = S.sn_start[s + 1] - t.c0;
@@ -828,6 +882,7 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       if (fwd) t.wait_cnt = (t.kind == TASK_OFF) ? 1 : S.fwd_expect[s];
       else t.wait_cnt = (t.kind == TASK_DIAG) ? S.bwd_nchunk[s] : 0;
     };
+    for (size_t q = 0; q < S.fwd_lane.size(); q += 4) S.fwd_lane[q + 3] = S.fwd_expect[S.fwd_lane[q]];
     for (auto& t : S.fwd) fill(t, true);
     for (auto& t : S.fwd_small) fill(t, true);
     for (auto& t : S.bwd) fill(t, false);

@@ -18,6 +18,10 @@ struct SymbolicOptions {
   int solve_chunk = 64;      // rows of the near chunk done by a large supernode's DIAG task
   int warp_chunk = 32;       // rows of a far chunk (one warp; 8 chunks per BULK entry)
   int fused_limit = 2048;    // w*(w+r) at or below which one warp does a supernode's solve
+  int lane_rows = 32;        // supernodes of at most lane_width columns and lane_rows rows
+  int lane_width = 4;        // are solved one per lane (32 per warp task); 0 rows disables
+  int lane_min_level = 4096; // ... on levels with at least this many of them (narrower levels
+                             // are latency-bound and get a warp per supernode)
 };
 
 // Work entry of the triangular-solve kernels.  A CTA takes one entry at a time:
@@ -26,7 +30,7 @@ struct SymbolicOptions {
 //   OFF   : a further row chunk [r0, r1) of a large supernode (one warp);
 //   BULK  : up to 8 OFF chunks (a..a+b-1 in the chunk list), one per warp.
 enum TaskKind : int32_t { TASK_FUSED = 0, TASK_DIAG = 1, TASK_OFF = 2, TASK_GROUP = 3,
-                          TASK_BULK = 4 };
+                          TASK_BULK = 4, TASK_LANES = 5 };
 
 struct SolveTask {
   int32_t kind;
@@ -87,6 +91,9 @@ struct Symbolic {
   std::vector<int32_t> fwd_tgt;    // target lists of forward tasks
   std::vector<int32_t> fwd_expect; // nsn : units that scatter into each supernode
   std::vector<int32_t> bwd_nchunk; // nsn : far OFF chunks of each supernode (backward)
+  // lane items of TASK_LANES warp tasks, 4 ints each: forward (sn, tgt0, ntgt, expected
+  // arrivals), backward (sn, parent, 0, 0)
+  std::vector<int32_t> fwd_lane, bwd_lane;
   // statistics
   int64_t nnz_L = 0;               // including the diagonal
   double flops = 0.0;              // refactor flops

@@ -70,6 +70,8 @@ def make(E, circ, **kw):
     ("rc2d", S.rc_mesh_2d(12, 9, seed=3)),
     ("rc3d", S.rc_mesh_3d(14, 13, 12, seed=2, n_loads=50)),     # several solve chunks
     ("inv", S.inverter_chain(stages=6, tree_nodes=30, seed=4)),
+    # long chain of 100-node parasitic trees: most supernodes are solved by subtree tasks
+    ("inv_trees", S.inverter_chain(stages=40, tree_nodes=100, seed=7)),
 ])
 def test_solve_matches_sparse_lu(ers, name, circ):
     sim = make(ers, circ)
@@ -85,6 +87,23 @@ def test_solve_matches_sparse_lu(ers, name, circ):
         res = np.max(np.abs(lin.Gk @ x - b)) / np.max(np.abs(b))
         assert res < 1e-11, res
         assert np.max(np.abs(x - ref)) <= 1e-8 * np.max(np.abs(ref))
+    sim.close()
+
+
+def test_batch_solve_matches_per_instance_lu(ers):
+    """Block-diagonal factor of many chains (subtree tasks in every instance)."""
+    circs = [S.inverter_chain(stages=st, tree_nodes=50, seed=20 + st) for st in range(3, 23)]
+    sim = ers.BatchSimulator(circs)
+    x0 = np.concatenate([O.dc_solution(c) for c in circs])
+    sim.set_state(0.0, x0)
+    b = np.random.default_rng(3).normal(size=sim.n)
+    x = sim.solve(b)
+    o = 0
+    for c in circs:
+        lin = O.linearize(c, x0[o:o + c.n])
+        ref = lin.solve(b[o:o + c.n])
+        assert np.max(np.abs(x[o:o + c.n] - ref)) <= 1e-8 * np.max(np.abs(ref))
+        o += c.n
     sim.close()
 
 
