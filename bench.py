@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--tree", type=int, default=20, help="batch: RC tree nodes per stage")
     p.add_argument("--t-end", type=float, default=0.3e-9)
     p.add_argument("--train-n", type=int, default=16)
+    p.add_argument("--ctrl-parts", type=int, default=1,
+                   help="batch: learned proposals used (1 step size, 2 Krylov dimension, 3 both)")
+    p.add_argument("--ctrl-margin", type=float, default=0.3,
+                   help="batch: log2 margin subtracted from proposed step ratios")
     p.add_argument("--seq-sample", type=int, default=4,
                    help="batch: instances timed one context at a time")
     return p.parse_args()
@@ -382,7 +386,8 @@ def run_batch_workload(a):
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     proc, fh = clocks_start(local, clk_path)
     for name, net in (("batched_plain", None), ("batched_learned", mlp)):
-        sim.set_controller(net, 3 if net is not None else 0)
+        sim.set_controller(net, a.ctrl_parts if net is not None else 0,
+                           a.ctrl_margin if net is not None else 0.0)
         sim.set_state(0.0, x0)
         sim.run_batch(a.t_end, a.tol, max_steps=max(a.warmup, 3))     # warm-up rounds
         sim.set_state(0.0, x0)
@@ -463,6 +468,7 @@ def run_batch_workload(a):
                        "nodes": nodes, "train_instances": a.train_n,
                        "train_samples": int(X.shape[0]), "train_loss": loss,
                        "train_s": train_s, "create_s": create_s,
+                       "controller": {"parts": a.ctrl_parts, "margin_log2": a.ctrl_margin},
                        "parallelism": "instances split over ranks" if world > 1 else "single GPU",
                        "l2_flush": "none: every round streams the factor and all Krylov bases"},
             "arms": {**arms,

@@ -216,10 +216,12 @@ void ers_mlp_destroy(ers_mlp* mlp);
 /* Use `mlp` (not owned; must outlive the runs, NULL = plain controller) as the step proposer of
  * a batched context.  parts selects which proposals are used: ERS_CTRL_H (the next step size;
  * otherwise the plain rule's), ERS_CTRL_M (the first dimension of the residual test; otherwise
- * m_min), or both. */
+ * m_min), or both.  margin >= 0 (log2 units) is subtracted from every proposed step ratio:
+ * h_next = h_k 2^(y0 - margin).  In a batch one rejected instance makes the whole round
+ * repeat its error basis, so a batch wants fewer rejections than a single circuit does. */
 #define ERS_CTRL_H 1
 #define ERS_CTRL_M 2
-ers_status ers_batch_set_controller(ers_ctx* ctx, ers_mlp* mlp, int32_t parts);
+ers_status ers_batch_set_controller(ers_ctx* ctx, ers_mlp* mlp, int32_t parts, double margin);
 /* Keep every accepted step's record (enable = 1) instead of the last 8; clears the records. */
 ers_status ers_batch_trace(ers_ctx* ctx, int32_t enable);
 /* Records of instance k: *count receives how many are kept; up to cap are copied to out. */

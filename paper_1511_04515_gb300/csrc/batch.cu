@@ -874,7 +874,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
         int i = ask[q];
         double hn;
         int ms;
-        ctrl_propose(&pred[2 * q], h[i], h_max, o.m_min, o.m_max, &hn, &ms);
+        ctrl_propose(&pred[2 * q], h[i], h_max, o.m_min, o.m_max, c->ctrl_margin, &hn, &ms);
         if (c->ctrl_parts & ERS_CTRL_H) {
           c->hprop_inst[i] = hn;
           c->proposed_inst[i] = 1;
@@ -898,11 +898,14 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   return ERS_OK;
 }
 
-ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts) {
+ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts, double margin) {
   if (!c) return ERS_ERR_INVALID;
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   if (mlp && (parts & ~(ERS_CTRL_H | ERS_CTRL_M)) != 0)
     return ctx_fail(c, ERS_ERR_INVALID, "unknown controller parts");
+  if (!(margin >= 0.0) || !std::isfinite(margin))
+    return ctx_fail(c, ERS_ERR_INVALID, "margin must be finite and >= 0");
+  c->ctrl_margin = margin;
   c->ctrl = (parts & (ERS_CTRL_H | ERS_CTRL_M)) ? mlp : nullptr;
   c->ctrl_parts = parts;
   std::fill(c->proposed_inst.begin(), c->proposed_inst.end(), 0);

@@ -38,9 +38,9 @@ bool ctrl_target(const ers_step_record* recs, int count, const ers_step_record& 
   return std::isfinite(t0);
 }
 
-void ctrl_propose(const float* y, double h_k, double h_max, int m_min, int m_max, double* h_next,
-                  int* m_start) {
-  double l2 = std::isfinite(y[0]) ? clampd(y[0], -3.0, 2.0) : 1.0;
+void ctrl_propose(const float* y, double h_k, double h_max, int m_min, int m_max, double margin,
+                  double* h_next, int* m_start) {
+  double l2 = std::isfinite(y[0]) ? clampd(y[0] - margin, -3.0, 2.0) : 1.0;
   *h_next = std::min(h_k * std::exp2(l2), h_max);
   double mm = std::isfinite(y[1]) ? y[1] * m_max : (double)m_min;
   int ms = (int)std::floor(mm + 0.5) - 1;

@@ -158,6 +158,7 @@ struct ers_ctx {
   int32_t* bscan_fin = nullptr;
   std::vector<int32_t> scan_mask;      // instances masked in the current batch_bases call
   int ctrl_parts = 0;                  // ERS_CTRL_H | ERS_CTRL_M: which proposals are used
+  double ctrl_margin = 0.0;            // log2 margin subtracted from proposed step ratios
   // learned step controller of batched runs
   ers_mlp* ctrl = nullptr;             // not owned; nullptr = plain controller
   bool trace = false;                  // keep every record (else the last ERS_CTRL_HISTORY)

@@ -143,7 +143,7 @@ def lib():
         "ers_mlp_train": ([P, pf, pf, I32, I32, I32, C.c_float, C.c_uint64, pf], C.c_int),
         "ers_mlp_last_error": ([P], C.c_char_p),
         "ers_mlp_destroy": ([P], None),
-        "ers_batch_set_controller": ([P, P, I32], C.c_int),
+        "ers_batch_set_controller": ([P, P, I32, D], C.c_int),
         "ers_batch_trace": ([P, I32], C.c_int),
         "ers_batch_records": ([P, I32, C.POINTER(StepRecord), I32, pi], C.c_int),
         "ers_batch_samples": ([P, pf, pf, I32, pi], C.c_int),
@@ -523,12 +523,13 @@ class BatchSimulator(Simulator):
                                         _iptr(ns), _iptr(nr)))
         return ns, nr
 
-    def set_controller(self, mlp: Optional["Mlp"], parts: int = 3):
+    def set_controller(self, mlp: Optional["Mlp"], parts: int = 3, margin: float = 0.0):
         """Learned (h, m) proposer (None = the plain controller of Alg. 2); parts: 1 = use the
-        proposed step size, 2 = the proposed first residual-test dimension, 3 = both."""
+        proposed step size, 2 = the proposed first residual-test dimension, 3 = both; margin
+        (log2) is subtracted from the proposed step ratios."""
         self._mlp = mlp
         self._check(lib().ers_batch_set_controller(self._ctx, mlp.handle if mlp else None,
-                                                   int(parts)))
+                                                   int(parts), float(margin)))
 
     def trace(self, enable: bool = True):
         self._check(lib().ers_batch_trace(self._ctx, int(bool(enable))))
