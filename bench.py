@@ -31,10 +31,10 @@ METRIC = "ER-Euler steps/s & Krylov vectors/s at rel err 1e-6; plain vs batched+
 UNIT = "steps/s"
 FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32)
 # DRAM bytes / algorithmic bytes of one solve pair, from an ncu capture of the same kernels on
-# the 70^3 mesh (2.646 GB measured vs 2.553 GB algorithmic); the full-size traffic is this ratio
+# the 70^3 mesh (2.663 GB measured vs 2.553 GB algorithmic); the full-size traffic is this ratio
 # times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
 # k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
-SOLVE_TRAFFIC_RATIO = None
+SOLVE_TRAFFIC_RATIO = 2.6626 / 2.5525
 SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same generator
 SAMPLE_STEPS = 10
 
