@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--workload", default="mesh", choices=["mesh", "batch"])
+    p.add_argument("--workload", default="mesh", choices=["mesh", "chain", "batch"])
+    p.add_argument("--stages", type=int, default=2000, help="chain: inverter stages")
     p.add_argument("--batch-n", type=int, default=64, help="batch: instances")
     p.add_argument("--stage-lo", type=int, default=4)
     p.add_argument("--stage-hi", type=int, default=40)
@@ -65,13 +66,23 @@ def parse():
     return p.parse_args()
 
 
-def workload(size):
+def workload(size, kind="mesh", stages=2000):
     from synth import circuits as S
+    if kind == "chain":
+        return S.inverter_chain(stages=stages, tree_nodes=100, seed=2, t_end=5e-9)
     loads = 10000 if size == 100 else max(1, (size ** 3) // 100)
     return S.rc_mesh_3d(size, size, size, seed=1, n_loads=loads)
 
 
-def workload_name(size):
+def workload_t_end(kind):
+    return 5e-9 if kind == "chain" else 2e-9
+
+
+def workload_name(size, kind="mesh", stages=2000):
+    if kind == "chain":
+        return (f"invchain_{stages}x100: nonlinear inverter chain, {stages} stages x 100-node "
+                f"RC trees ({stages * 100 + 1} nodes), square-law MOSFETs, LU refactor of G_k "
+                f"every step, adaptive h (tol 1e-6, eps 1e-7), first steps from DC over 5 ns")
     return (f"rc3d_{size}x{size}x{size}: linear 3D RC power-grid mesh ({size ** 3} nodes), "
             f"pulse loads, G factored once, adaptive h (tol 1e-6, eps 1e-7) over 2 ns")
 
@@ -126,34 +137,45 @@ def clocks_stop(proc, f, path):
 # --------------------------------------------------------------------------------------
 # oracle (CPU) sample: runs in a fresh single-threaded interpreter
 # --------------------------------------------------------------------------------------
-def oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE):
+def oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE, kind="mesh", stages=2000):
     import numpy as np
     from oracle import ers_oracle as O
-    circ = workload(size)
+    circ = workload(size, kind, stages)
+    x0 = O.dc_solution(circ, x0=circ.nodeset) if kind == "chain" else np.zeros(circ.n)
     t0 = time.perf_counter()
-    x, t, st = O.er_run(circ, t_end=2e-9, tol=1e-6, max_steps=steps, x0=np.zeros(circ.n))
+    x, t, st = O.er_run(circ, t_end=workload_t_end(kind), tol=1e-6, max_steps=steps, x0=x0)
     dt = time.perf_counter() - t0
     return {"steps": st.steps, "seconds": dt, "krylov": st.krylov, "t_reached": t, "n": circ.n}
 
 
-def run_oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE):
+def run_oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE, kind="mesh", stages=2000):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--steps", str(steps),
-           "--size", str(size)]
+           "--size", str(size), "--workload", kind, "--stages", str(stages)]
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     r = json.loads(out.stdout.strip().splitlines()[-1])
     value = r["steps"] / r["seconds"]
+    what = (f"the {size}^3 mesh ({r['n']} nodes, same generator and seed) from x = 0"
+            if kind == "mesh" else
+            f"the {stages}-stage chain ({r['n']} nodes, same generator and seed) from DC")
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"first {r['steps']} adaptive ER steps of the {size}^3 mesh "
-                       f"({r['n']} nodes, same generator and seed) from x = 0, SuperLU + numpy, "
+            "sample": (f"first {r['steps']} adaptive ER steps of {what}, SuperLU + numpy, "
                        f"1 thread, {r['seconds']:.1f} s; steps/s on the sample, not scaled "
-                       f"to the 1M-node mesh"),
+                       f"to the full workload"),
             "krylov_vectors_per_s": r["krylov"] / r["seconds"]}
 
 
 # --------------------------------------------------------------------------------------
+def oracle_args(a):
+    """(steps, size, kind, stages) of the bounded oracle sample: 10 steps of a 24^3 mesh, or
+    100 steps of a 100-stage chain (about 10 s of one host core each)."""
+    if a.workload == "chain":
+        return 100, SAMPLE_SIZE, "chain", 100
+    return SAMPLE_STEPS, SAMPLE_SIZE, "mesh", 2000
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -166,16 +188,18 @@ def run_reference(a):
     if rank != 0:
         return
     for _ in range(a.warmup):
-        run_oracle_sample(steps=2)
+        run_oracle_sample(2, *oracle_args(a)[1:])
     t0 = time.perf_counter()
-    vals = [run_oracle_sample(steps=SAMPLE_STEPS) for _ in range(max(1, a.steps // 5))]
+    kind = "chain" if a.workload == "chain" else "mesh"
+    vals = [run_oracle_sample(*oracle_args(a)) for _ in range(max(1, a.steps // 5))]
     wall = time.perf_counter() - t0
     v = statistics.median(x["value"] for x in vals)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(a.size), "sample_of": "oracle on a reduced mesh",
+            "config": {"workload": workload_name(a.size, kind, a.stages),
+                       "sample_of": "oracle on a reduced circuit of the same generator",
                        "parallelism": "host cores, rank 0"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"]},
@@ -199,8 +223,9 @@ def run_ours(a):
         torch.distributed.barrier()
     from paper_1511_04515_gb300 import ers
 
-    circ = workload(a.size)
-    t_end = 2e-9
+    kind = "chain" if a.workload == "chain" else "mesh"
+    circ = workload(a.size, kind, a.stages)
+    t_end = workload_t_end(kind)
     opts = ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100)
     tc = time.perf_counter()
     sim = ers.Simulator.from_circuit(circ, opts=opts)
@@ -208,7 +233,7 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     sim.set_stream(stream)
     tf = time.perf_counter()
-    sim.dc()                               # x(0): factor G once + one solve
+    sim.dc(circ.nodeset)                   # x(0): Newton (linear: factor G once + one solve)
     torch.cuda.synchronize()
     factor_s = time.perf_counter() - tf
     if a.warmup:
@@ -297,7 +322,8 @@ def run_ours(a):
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / max(steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(a.size), "n": n, "nnz_G": int(circ.G.nnz),
+            "config": {"workload": workload_name(a.size, kind, a.stages), "n": n,
+                       "nnz_G": int(circ.G.nnz), "devices": int(len(circ.dev)),
                        "loads": int(circ.p), "nnz_L": int(st1["nnz_L"]),
                        "factor_GB": st1["factor_doubles"] * 8 / 1e9,
                        "l2_flush": "inputs larger than L2 (factor values alone exceed 129 MB)",
@@ -312,7 +338,7 @@ def run_ours(a):
                     "d2h_bytes_per_step": 8 * n}}
     if not a.no_baseline and world == 1:
         try:
-            line["cpu_baseline"] = run_oracle_sample()
+            line["cpu_baseline"] = run_oracle_sample(*oracle_args(a))
         except Exception as ex:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "error": str(ex)[-300:]}
     print(json.dumps(line), flush=True)
@@ -357,14 +383,17 @@ def run_batch_workload(a):
     def progress(msg):
         print(f"[batch {time.perf_counter() - t_start:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
-    # instances are independent: with N ranks each takes every N-th instance (no exchange)
+    # instances are independent: with N ranks each runs its LPT share (no exchange); every rank
+    # trains the same network on the same traces (deterministic kernels: identical weights)
+    from paper_1511_04515_gb300.partition import instance_cost, lpt_partition
     stream = torch.cuda.current_stream()
     # 1. training set: plain-controller traces of other seeds; the network is trained by the
     #    library's own BF16 forward/backward/Adam kernels
     ttr = time.perf_counter()
-    tr = ers.BatchSimulator(family(a.train_n, 2000)[rank::world])
+    trc = family(a.train_n, 2000)
+    tr = ers.BatchSimulator(trc)
     tr.set_stream(stream)
-    tr.dc()
+    tr.dc(np.concatenate([c.nodeset for c in trc]))
     tr.trace(True)
     tr.run_batch(a.t_end, a.tol)
     X, T = tr.samples()
@@ -374,12 +403,14 @@ def run_batch_workload(a):
     train_s = time.perf_counter() - ttr
     progress(f"trained on {X.shape[0]} samples, loss {loss:.3g}")
     # 2. held-out batch
-    circs = family(a.batch_n, 5000)[rank::world]
+    allc = family(a.batch_n, 5000)
+    share = lpt_partition([instance_cost(c) for c in allc], world)[rank]
+    circs = [allc[i] for i in share]
     tc = time.perf_counter()
     sim = ers.BatchSimulator(circs)
     create_s = time.perf_counter() - tc
     sim.set_stream(stream)
-    sim.dc()
+    sim.dc(np.concatenate([c.nodeset for c in circs]))
     _, x0, _ = sim.state()
     arms = {}
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
@@ -423,7 +454,7 @@ def run_batch_workload(a):
     for k in pick:
         one = ers.Simulator.from_circuit(circs[k])
         one.set_stream(stream)
-        one.dc()
+        one.dc(circs[k].nodeset)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         n1, _ = one.run(a.t_end, a.tol)
@@ -438,7 +469,7 @@ def run_batch_workload(a):
     ref_idx = pick[:2]
     ref = ers.BatchSimulator([circs[k] for k in ref_idx])
     ref.set_stream(stream)
-    ref.dc()
+    ref.dc(np.concatenate([circs[k].nodeset for k in ref_idx]))
     ref.run_batch(a.t_end, a.tol / 10)
     xref = [ref.state_inst(q)[1] for q in range(len(ref_idx))]
     ref.close()
@@ -469,7 +500,8 @@ def run_batch_workload(a):
                        "train_samples": int(X.shape[0]), "train_loss": loss,
                        "train_s": train_s, "create_s": create_s,
                        "controller": {"parts": a.ctrl_parts, "margin_log2": a.ctrl_margin},
-                       "parallelism": "instances split over ranks" if world > 1 else "single GPU",
+                       "parallelism": ("instances split over ranks (LPT on node count)"
+                                       if world > 1 else "single GPU"),
                        "l2_flush": "none: every round streams the factor and all Krylov bases"},
             "arms": {**arms,
                      "plain_sequential": {"seconds_est": seq_est, "sampled_instances": len(pick),
@@ -490,7 +522,7 @@ def run_batch_workload(a):
 def main():
     a = parse()
     if a.oracle_sample:
-        print(json.dumps(oracle_sample(a.steps, a.size)))
+        print(json.dumps(oracle_sample(a.steps, a.size, a.workload, a.stages)))
         return
     if a.impl == "reference":
         run_reference(a)

@@ -183,6 +183,17 @@ ers_status ers_ctrl_features(const ers_step_record* recs, int32_t count, float* 
 ers_status ers_ctrl_target(const ers_step_record* recs, int32_t count, const ers_step_record* next,
                            float* t);
 
+/* Next step from a network output y (2 floats) and the last accepted step `last`:
+ *   l = clamp(y[0] - margin, -3, 2)   (non-finite y[0]: l = 1)
+ *   r = clamp(-log2(last.err / last.E) / 2, -3, 6)   (err = 0: r = 6), the log2 of the ratio
+ *       that lands on the budget under the local error model err ~ h^2
+ *   l = clamp(l, min(0, r - 1), max(0, r + 1))   (a safety band around the network)
+ *   h_next = min(last.h 2^l, last.h_max)
+ *   m_start = clamp(round(y[1] last.m_max) - 1, m_min, last.m_max)   (non-finite: m_min)
+ * Host-only. */
+ers_status ers_ctrl_propose(const float* y, const ers_step_record* last, double margin,
+                            int32_t m_min, double* h_next, int32_t* m_start);
+
 /* Network of the learned controller: 32 -> 64 -> 64 -> 64 -> 2, ReLU, BF16 weights and
  * activations with FP32 accumulation on the tensor cores, FP32 master weights, Adam.
  * Parameter vector (FP32, ers_mlp_nparam() entries): W1 (64x32 row-major), b1, W2 (64x64),
@@ -242,7 +253,10 @@ ers_status ers_set_stream(ers_ctx* ctx, void* stream);
 
 /* x(0) = DC solution (Alg. 2): Newton on G_lin x + i_dev(x) = B u(0) through the same LU
  * kernels (voltage step clamp 0.5 V, at most 50 iterations, residual 1e-12 A).
- * x0_guess (n, may be NULL = zeros) is the starting point.  Sets t = 0. */
+ * x0_guess (n, may be NULL = zeros) is the starting point.  A long chain of gates needs a
+ * guess near its logic levels (a nodeset): linearised at 0 V every stage is an amplifier
+ * (gain gm/gds ~ 30 in saturation) and the Newton system of k stages grows like gain^k until
+ * it overflows, which shows as ERS_ERR_SINGULAR or ERS_ERR_NONFINITE.  Sets t = 0. */
 ers_status ers_dc(ers_ctx* ctx, const double* x0_guess);
 
 /* Device evaluation at the current x, stamping of G_k and the numeric LU refactor of G_k

@@ -770,32 +770,20 @@ ers_status ers_refactor(ers_ctx* c) {
   return sync_status(c);
 }
 
-ers_status ers_dc(ers_ctx* c, const double* x0) {
-  if (!c) return ERS_ERR_INVALID;
-  ers_status st = clear_status(c);
-  if (st != ERS_OK) return st;
-  if (x0) {
-    for (int i = 0; i < c->n; ++i)
-      if (!std::isfinite(x0[i])) return fail(c, ERS_ERR_NONFINITE, "non-finite initial guess");
-    std::vector<double> xp(c->n);
-    for (int k = 0; k < c->n; ++k) xp[k] = x0[c->sym.perm[k]];
-    CU(cudaMemcpyAsync(c->x, xp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-  } else {
-    CU(cudaMemsetAsync(c->x, 0, sizeof(double) * c->n, c->stream));
-  }
-  k_pwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, 0.0, 0.0, c->u,
-                                             nullptr);
-  k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, nullptr, c->tmp);
-  c->stats.kernel_launches++;
-  for (int it = 0; it < 50; ++it) {
+// Newton on G_lin x + i_dev(x) = B u(0) from the current x (one refactor of G_k per
+// iteration), each update clamped to 0.5 V per node.  *res receives the final residual
+// max-norm.
+static ers_status dc_newton(ers_ctx* c, double tol, int maxit, double* res) {
+  ers_status st = ERS_OK;
+  *res = INFINITY;
+  for (int it = 0; it < maxit; ++it) {
     st = do_refactor(c);
-    if (st != ERS_OK) return st;
+    if (st != ERS_OK) break;
     k_dc_res<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->G_ptr, c->G_idx, c->G_val, c->x, c->F,
                                                  c->tmp, c->rhs);
-    double res = host_absmax(c, c->rhs, &st);
-    if (st != ERS_OK) return st;
-    if (res <= 1e-12) break;
+    *res = host_absmax(c, c->rhs, &st);
+    if (st != ERS_OK) break;
+    if (*res <= tol || !std::isfinite(*res)) break;
     k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F,
                                              c->solve_buf);
     CU(launch_solve(c, c->solve_buf, 1));
@@ -807,6 +795,32 @@ ers_status ers_dc(ers_ctx* c, const double* x0) {
     }
     c->factored = false;
   }
+  if (st == ERS_OK) st = sync_status(c);
+  return st;
+}
+
+ers_status ers_dc(ers_ctx* c, const double* x0) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (x0) {
+    std::vector<double> xp(c->n);
+    for (int i = 0; i < c->n; ++i)
+      if (!std::isfinite(x0[i])) return fail(c, ERS_ERR_NONFINITE, "non-finite initial guess");
+    for (int k = 0; k < c->n; ++k) xp[k] = x0[c->sym.perm[k]];
+    CU(cudaMemcpyAsync(c->x, xp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  } else {
+    CU(cudaMemsetAsync(c->x, 0, sizeof(double) * c->n, c->stream));
+  }
+  k_pwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, 0.0, 0.0, c->u,
+                                             nullptr);
+  k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, nullptr, c->tmp);
+  c->stats.kernel_launches++;
+  double res = INFINITY;
+  st = dc_newton(c, 1e-12, 50, &res);
+  if (st != ERS_OK) return st;
+  if (!std::isfinite(res)) return fail(c, ERS_ERR_NONFINITE, "DC Newton diverged");
   if (!c->linear) c->factored = false;
   c->t = 0.0;
   return sync_status(c);

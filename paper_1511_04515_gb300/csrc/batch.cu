@@ -874,7 +874,9 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
         int i = ask[q];
         double hn;
         int ms;
-        ctrl_propose(&pred[2 * q], h[i], h_max, o.m_min, o.m_max, c->ctrl_margin, &hn, &ms);
+        const ers_step_record& last = c->recs[i].back();
+        ctrl_propose(&pred[2 * q], h[i], h_max, o.m_min, o.m_max, c->ctrl_margin,
+                     last.E > 0.0 ? last.err / last.E : 0.0, &hn, &ms);
         if (c->ctrl_parts & ERS_CTRL_H) {
           c->hprop_inst[i] = hn;
           c->proposed_inst[i] = 1;

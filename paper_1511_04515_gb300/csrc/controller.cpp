@@ -39,8 +39,13 @@ bool ctrl_target(const ers_step_record* recs, int count, const ers_step_record& 
 }
 
 void ctrl_propose(const float* y, double h_k, double h_max, int m_min, int m_max, double margin,
-                  double* h_next, int* m_start) {
+                  double err_ratio, double* h_next, int* m_start) {
   double l2 = std::isfinite(y[0]) ? clampd(y[0] - margin, -3.0, 2.0) : 1.0;
+  // safety band from the local error model err ~ h^2: r* = (E / err)^(1/2) is the ratio that
+  // would land on the budget; the proposal stays within [min(1, r*/2), max(1, 2 r*)]
+  double lr = (err_ratio > 0.0 && std::isfinite(err_ratio)) ? -0.5 * std::log2(err_ratio) : 6.0;
+  lr = clampd(lr, -3.0, 6.0);
+  l2 = clampd(l2, std::min(0.0, lr - 1.0), std::max(0.0, lr + 1.0));
   *h_next = std::min(h_k * std::exp2(l2), h_max);
   double mm = std::isfinite(y[1]) ? y[1] * m_max : (double)m_min;
   int ms = (int)std::floor(mm + 0.5) - 1;
@@ -61,6 +66,17 @@ ers_status ers_ctrl_target(const ers_step_record* recs, int32_t count, const ers
                            float* t) {
   if (!recs || count < 1 || !next || !t) return ERS_ERR_INVALID;
   return ers::ctrl_target(recs, count, *next, t) ? ERS_OK : ERS_ERR_INVALID;
+}
+
+ers_status ers_ctrl_propose(const float* y, const ers_step_record* last, double margin,
+                            int32_t m_min, double* h_next, int32_t* m_start) {
+  if (!y || !last || !h_next || !m_start || !(margin >= 0.0) || m_min < 1 || last->m_max < m_min)
+    return ERS_ERR_INVALID;
+  int ms = 0;
+  double ratio = last->E > 0.0 ? last->err / last->E : 0.0;
+  ers::ctrl_propose(y, last->h, last->h_max, m_min, last->m_max, margin, ratio, h_next, &ms);
+  *m_start = ms;
+  return ERS_OK;
 }
 
 }  // extern "C"

@@ -89,7 +89,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_set_params", "ers_mlp_get_params", "ers_mlp_forward", "ers_mlp_forward_dev",
            "ers_mlp_grad", "ers_mlp_adam_step", "ers_mlp_train", "ers_mlp_last_error",
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
-           "ers_batch_samples", "ers_batch_ctrl_stats"]
+           "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose"]
 
 _lib = None
 
@@ -132,6 +132,7 @@ def lib():
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
         "ers_ctrl_features": ([C.POINTER(StepRecord), I32, pf], C.c_int),
         "ers_ctrl_target": ([C.POINTER(StepRecord), I32, C.POINTER(StepRecord), pf], C.c_int),
+        "ers_ctrl_propose": ([pf, C.POINTER(StepRecord), D, I32, pd, pi], C.c_int),
         "ers_mlp_nparam": ([], I32),
         "ers_mlp_create": ([C.POINTER(P), C.c_uint64], C.c_int),
         "ers_mlp_set_params": ([P, pf], C.c_int),
@@ -200,6 +201,18 @@ def ctrl_target(recs, nxt):
     out = np.zeros(2, np.float32)
     rc = lib().ers_ctrl_target(arr, len(recs), nx, _fptr(out))
     return out if rc == 0 else None
+
+
+def ctrl_propose(y, last, margin=0.0, m_min=3):
+    """(h_next, m_start) from a network output and the last accepted step (see ers.h)."""
+    yy = np.ascontiguousarray(y, np.float32)
+    lr = _records([last])
+    h = C.c_double(0.0)
+    m = C.c_int32(0)
+    rc = lib().ers_ctrl_propose(_fptr(yy), lr, float(margin), int(m_min), C.byref(h), C.byref(m))
+    if rc != 0:
+        raise ErsError(rc, "ers_ctrl_propose")
+    return h.value, m.value
 
 
 class Mlp:

@@ -17,7 +17,7 @@ these seeded generators stand in for them with the sizes of the paper's workload
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 import scipy.sparse as sp
@@ -46,6 +46,9 @@ class Circuit:
     vdd: float = 1.0
     t_end: float = 1e-9
     meta: dict = field(default_factory=dict)
+    # starting point for the DC operating point when the netlist knows one (a "nodeset": the
+    # logic levels of a gate chain); None = start from 0 V
+    nodeset: Optional[np.ndarray] = None
 
     @property
     def p(self) -> int:
@@ -128,6 +131,25 @@ def rc_mesh_2d(nx=32, ny=32, seed=0, n_src=16, gmin=1e-12, t_end=1e-9):
                    meta=dict(kind="rc2d", nx=nx, ny=ny, seed=seed, h=1e-12, m=20))
 
 
+def coupled_rc_mesh_2d(nx=32, ny=32, seed=0, n_src=16, t_end=1e-9, cc_lo=1e-15, cc_hi=1e-14):
+    """rc_mesh_2d plus a coupling capacitor (log-uniform cc_lo..cc_hi) across every diagonal
+    neighbour pair (i, j)-(i+1, j+1): C is no longer diagonal (nnz_C close to nnz_G, as in
+    circuits with complex coupling capacitance) and stays symmetric positive definite."""
+    base = rc_mesh_2d(nx, ny, seed=seed, n_src=n_src, t_end=t_end)
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    n = nx * ny
+    idx = np.arange(n).reshape(ny, nx)
+    a = idx[:-1, :-1].ravel()
+    b = idx[1:, 1:].ravel()
+    cc = _log_uniform(rng, cc_lo, cc_hi, a.size)
+    r, c, v = _resistor_stamps(a, b, cc)       # same stamp pattern as a conductance
+    C = (base.C + _csr(r, c, v, n, n)).tocsr()
+    C.sort_indices()
+    return Circuit(name=f"rc2dcc_{nx}x{ny}", n=n, G=base.G, C=C, B=base.B, dev=base.dev,
+                   pwl=base.pwl, t_end=t_end,
+                   meta=dict(kind="rc2dcc", nx=nx, ny=ny, seed=seed))
+
+
 def rc_mesh_3d(nx=100, ny=100, nz=100, seed=1, n_loads=10000, pad_pitch=10,
                gmin=1e-12, t_end=2e-9, delay_grid=10e-12, n_delay=189):
     """Linear 3D RC power-grid mesh: 6-neighbour conductances log-uniform 0.1-10 S,
@@ -189,6 +211,11 @@ def inverter_chain(stages=2000, tree_nodes=100, seed=2, vdd=1.0, gmin=1e-12,
         return x * np.exp(rng.normal(0.0, sigma, np.shape(x)))
 
     n = 1 + stages * tree_nodes
+    # nodeset: logic levels with the input low (u(0) = 0): stage outputs alternate vdd, 0, ...
+    # and every node of a stage's tree sits at its output level (no DC current in the trees)
+    nodeset = np.zeros(n)
+    for st in range(stages):
+        nodeset[1 + st * tree_nodes:1 + (st + 1) * tree_nodes] = vdd if st % 2 == 0 else 0.0
     rows, cols, vals = [], [], []
     caps = np.zeros(n)
     dev = np.zeros(2 * stages, DEVICE_DTYPE)
@@ -234,7 +261,7 @@ def inverter_chain(stages=2000, tree_nodes=100, seed=2, vdd=1.0, gmin=1e-12,
         tt.append(t_end); vv.append(vv[-1])
     pwl = [(np.array(tt), np.array(vv))]
     return Circuit(name=f"invchain_{stages}x{tree_nodes}", n=n, G=G, C=C, B=B, dev=dev,
-                   pwl=pwl, vdd=vdd, t_end=t_end,
+                   pwl=pwl, vdd=vdd, t_end=t_end, nodeset=nodeset,
                    meta=dict(kind="invchain", stages=stages, tree_nodes=tree_nodes, seed=seed))
 
 

@@ -208,6 +208,43 @@ def test_er_step_rc2d_per_step(ers):
     sim.close()
 
 
+def test_er_step_coupled_capacitance(ers):
+    """Non-diagonal C (coupling capacitors on every diagonal neighbour pair): per-step parity
+    at fixed m and with the Krylov dimension from Eq. 16."""
+    circ = S.coupled_rc_mesh_2d(16, 16, seed=3, n_src=8, t_end=0.3e-9)
+    x = np.zeros(circ.n)
+    states = {}
+    for k in range(120):
+        if k in (40, 119):
+            states[k] = x.copy()
+        x = O.er_step(circ, x, k * 1e-12, 1e-12, m=20).x
+    sim = make(ers, circ)
+    for k, xk in states.items():
+        t = k * 1e-12
+        for m in (20, 0):
+            ref = O.er_step(circ, xk, t, 1e-12, m=m)
+            sim.set_state(t, xk)
+            mu, _ = sim.step(1e-12, m)
+            _, xg, _ = sim.state()
+            ok, worst = node_close(xg, ref.x)
+            assert ok, (k, m, worst)
+            assert mu == ref.m1
+    sim.close()
+
+
+def test_adaptive_run_coupled_capacitance(ers):
+    circ = S.coupled_rc_mesh_2d(12, 12, seed=5, n_src=6, t_end=0.2e-9)
+    sim = make(ers, circ)
+    sim.set_state(0.0, np.zeros(circ.n))
+    ns, nr = sim.run(circ.t_end, 1e-6)
+    _, xg, _ = sim.state()
+    xr, tr, st = O.er_run(circ, tol=1e-6, x0=np.zeros(circ.n))
+    assert ns == st.steps
+    ok, worst = node_close(xg, xr, 1e-8)
+    assert ok, worst
+    sim.close()
+
+
 def test_er_trajectory_rc2d_full(ers):
     """Full fixed-step trajectory of the 32x32 mesh (1000 steps of 1 ps, m = 20).  Per-step
     differences accumulate along a trajectory; the oracle's own trajectory moves by up to
@@ -241,6 +278,19 @@ def test_dc_matches_oracle(ers):
     _, x, _ = sim.state()
     ref = O.dc_solution(circ)
     assert np.max(np.abs(x - ref)) <= 1e-9
+    sim.close()
+
+
+def test_dc_long_chain_matches_oracle(ers):
+    """DC of a 400-stage chain from its logic-level nodeset, against the oracle's Newton from
+    the same guess (from 0 V the linearised chain is a 400-stage amplifier whose Newton
+    system overflows, on either side)."""
+    circ = S.inverter_chain(stages=400, tree_nodes=20, seed=2, t_end=1e-9)
+    sim = make(ers, circ)
+    sim.dc(circ.nodeset)
+    _, xg, _ = sim.state()
+    xr = O.dc_solution(circ, x0=circ.nodeset)
+    assert np.max(np.abs(xg - xr)) <= 1e-9
     sim.close()
 
 

@@ -195,3 +195,29 @@ def test_library_targets_match_oracle(E):
             assert ours is None
         else:
             np.testing.assert_allclose(ours, ref.astype(np.float32), rtol=0, atol=2e-7)
+
+
+def test_library_proposal_rule_by_hand(E):
+    import math
+    last = rec(h=1e-12, h_max=1e-10, err=0.25e-6, E=1e-6, m=10, m_max=40)
+    # r* = 2 (log2 1): band [0, 2]; y0 = 0.5, no margin -> 2^0.5 h
+    h, m = E.ctrl_propose([0.5, 0.25], last)
+    assert h == pytest.approx(math.sqrt(2) * 1e-12, rel=1e-12) and m == 9
+    # a shrink request after an easy step is held at h (lower band edge 0)
+    h, _ = E.ctrl_propose([-2.0, 0.25], last)
+    assert h == pytest.approx(1e-12, rel=1e-12)
+    # margin shifts the request: 0.5 - 0.3
+    h, _ = E.ctrl_propose([0.5, 0.25], last, margin=0.3)
+    assert h == pytest.approx(2 ** 0.2 * 1e-12, rel=1e-12)
+    # near the budget (err/E = 0.9): upper edge r* + 1
+    hi = 1 - 0.5 * math.log2(0.9)
+    h, _ = E.ctrl_propose([2.0, 0.25], rec(h=1e-12, h_max=1e-10, err=0.9e-6, E=1e-6, m_max=40))
+    assert h == pytest.approx(2 ** hi * 1e-12, rel=1e-12)
+    # err = 0 (linear circuit): r* capped at 2^6, so the network's 4x stands; h_max caps
+    h, _ = E.ctrl_propose([2.0, 0.25], rec(h=4e-11, h_max=1e-10, err=0.0, E=1e-6, m_max=40))
+    assert h == pytest.approx(1e-10, rel=1e-12)
+    # m_start: round(y1 m_max) - 1 clamped to [m_min, m_max]; non-finite -> m_min
+    assert E.ctrl_propose([0.0, 0.99], last)[1] == 39
+    assert E.ctrl_propose([0.0, 0.0], last)[1] == 3
+    h, m = E.ctrl_propose([float("nan"), float("nan")], last)
+    assert m == 3 and h == pytest.approx(2e-12, rel=1e-12)   # non-finite y0: l = 1

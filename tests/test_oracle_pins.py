@@ -59,6 +59,26 @@ def test_random_rc_step_matches_eigen_solution(seed):
     assert np.max(np.abs(r.x - ex)) <= 1e-11 * np.max(np.abs(ex))
 
 
+def test_coupled_capacitance_step_matches_eigen_solution():
+    """Non-diagonal C (coupling capacitors): the ER step with a full Krylov space equals the
+    exact solution from the generalized eigenproblem G q = lambda C q."""
+    circ = S.coupled_rc_mesh_2d(5, 5, seed=4, n_src=4, t_end=50e-12)
+    assert (circ.C - sp_diag(circ.C)).nnz > 0
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=circ.n) * 0.1
+    t = 0.0
+    nb = circ.breakpoints()
+    h = min(3e-12, float(nb[nb > t][0]) - t)
+    r = O.er_step(circ, x, t, h, m=circ.n)
+    ex = exact_linear_step(circ, x, t, h)
+    assert np.max(np.abs(r.x - ex)) <= 1e-10 * np.max(np.abs(ex))
+
+
+def sp_diag(M):
+    import scipy.sparse as sp
+    return sp.diags(M.diagonal())
+
+
 def test_random_rc_trajectory_exact():
     circ = S.random_rc(n=12, seed=5, p=3, t_end=30e-12)
     bps = list(circ.breakpoints())
