@@ -37,20 +37,30 @@ __device__ inline void sm_matmul(double* C, const double* A, const double* B, in
   __syncthreads();
 }
 
-// LU with partial pivoting of M (m x m, in place); piv[k] = row swapped with k.
+// LU with partial pivoting of M (m x m, column-major, in place); piv[k] = row swapped with k.
+// The pivot search is a warp arg-max (ties to the lowest row), the row swap, the scaling of
+// column k and the trailing update are spread over the CTA: two barriers per column.
 __device__ inline void sm_lu(double* M, int* piv, int m) {
   __shared__ int s_p;
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
       int p = k;
-      double best = fabs(M[k + k * m]);
-      for (int i = k + 1; i < m; ++i)
-        if (fabs(M[i + k * m]) > best) { best = fabs(M[i + k * m]); p = i; }
-      s_p = p;
-      piv[k] = p;
+      for (int i = k + lane; i < m; i += 32) {
+        double v = fabs(M[i + k * m]);
+        if (v > best) { best = v; p = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (lane == 0) { s_p = p; piv[k] = p; }
     }
     __syncthreads();
-    int p = s_p;
+    const int p = s_p;
+    // swap rows k and p (all columns), then scale column k below the diagonal
     if (p != k)
       for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
         double t = M[k + jj * m];
@@ -58,36 +68,48 @@ __device__ inline void sm_lu(double* M, int* piv, int m) {
         M[p + jj * m] = t;
       }
     __syncthreads();
-    double inv = 1.0 / M[k + k * m];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] *= inv;
-    __syncthreads();
-    int rem = m - k - 1;
+    const double inv = 1.0 / M[k + k * m];
+    const int rem = m - k - 1;
+    // trailing update with the multipliers l_i = M[i,k] / M[k,k] formed on the fly (column k
+    // and row k are only read here), then column k is scaled
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
       int i = k + 1 + e % rem, jj = k + 1 + e / rem;
-      M[i + jj * m] -= M[i + k * m] * M[k + jj * m];
+      M[i + jj * m] -= (M[i + k * m] * inv) * M[k + jj * m];
     }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] *= inv;
     __syncthreads();
   }
 }
 
-// Solve (LU) X = B column by column in place (B: m x m); column jj by one thread.
+// Solve (LU) X = B in place (B: m x m, column-major) with the CTA: the row permutation, then
+// forward and backward substitution row by row, each row's update of the rows below (above)
+// spread over all m columns.
 __device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, int m) {
   for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
     double* b = B + jj * m;
     for (int k = 0; k < m; ++k)
       if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
-    for (int i = 1; i < m; ++i) {
-      double acc = b[i];
-      for (int k = 0; k < i; ++k) acc -= LU[i + k * m] * b[k];
-      b[i] = acc;
-    }
-    for (int i = m - 1; i >= 0; --i) {
-      double acc = b[i];
-      for (int k = i + 1; k < m; ++k) acc -= LU[i + k * m] * b[k];
-      b[i] = acc / LU[i + i * m];
-    }
   }
   __syncthreads();
+  for (int k = 0; k < m - 1; ++k) {          // L (unit diagonal): B[i,:] -= L[i,k] B[k,:]
+    const int rem = m - k - 1;
+    for (int e = threadIdx.x; e < rem * m; e += blockDim.x) {
+      int i = k + 1 + e % rem, jj = e / rem;
+      B[i + jj * m] -= LU[i + k * m] * B[k + jj * m];
+    }
+    __syncthreads();
+  }
+  for (int k = m - 1; k >= 0; --k) {         // U: B[k,:] /= U[k,k]; B[i,:] -= U[i,k] B[k,:]
+    const double d = LU[k + k * m];
+    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) B[k + jj * m] /= d;
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * m; e += blockDim.x) {
+      int i = e % k, jj = e / k;
+      B[i + jj * m] -= LU[i + k * m] * B[k + jj * m];
+    }
+    __syncthreads();
+  }
 }
 
 // y = exp(h H^-1) e_1 for the leading m x m block of H (ld ldh); last = e_m^T H^-1 y.
