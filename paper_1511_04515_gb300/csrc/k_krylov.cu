@@ -296,8 +296,12 @@ cudaError_t krylov_init_constants() {
                               (6 * MAX_M * MAX_M + 2 * MAX_M) * 8);
 }
 
+// Grid of the cooperative vector kernels: every inner product of MGS is a grid-wide reduction
+// (arrival counter, one CTA sums the partials), whose cost grows with the CTA count, so the grid
+// is sized for at least 8 elements per thread; the memory traffic of an iteration stays far
+// below what the resulting CTAs can stream.
 static int coop_blocks_for(ers_ctx* c, int n) {
-  int want = (n + KB - 1) / KB;
+  int want = (n + 8 * KB - 1) / (8 * KB);
   return std::max(1, std::min(want, c->coop_blocks));
 }
 
