@@ -230,7 +230,7 @@ def run_ours(a):
     tc = time.perf_counter()
     sim = ers.Simulator.from_circuit(circ, opts=opts)
     create_s = time.perf_counter() - tc
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # the library's stream; events are recorded on it
     sim.set_stream(stream)
     tf = time.perf_counter()
     sim.dc(circ.nodeset)                   # x(0): Newton (linear: factor G once + one solve)
@@ -386,7 +386,7 @@ def run_batch_workload(a):
     # instances are independent: with N ranks each runs its LPT share (no exchange); every rank
     # trains the same network on the same traces (deterministic kernels: identical weights)
     from paper_1511_04515_gb300.partition import instance_cost, lpt_partition
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # the library's stream; events are recorded on it
     # 1. training set: plain-controller traces of other seeds; the network is trained by the
     #    library's own BF16 forward/backward/Adam kernels
     ttr = time.perf_counter()

@@ -94,6 +94,7 @@ typedef struct {
   double solve_ms;             /* device time of the solve kernels (profiling on)     */
   double solve_bytes_per_pass; /* factor bytes one solve pair reads (values+indices)  */
   double solve_fma_per_rhs;    /* FP64 FMAs of one solve pair per right-hand side     */
+  int64_t graph_launches;      /* CUDA graph launches (batched Arnoldi iterations)     */
 } ers_stats_t;
 
 /* One circuit of a batch (ers_create_batch): the same data ers_create takes. */
@@ -242,13 +243,23 @@ ers_status ers_batch_records(const ers_ctx* ctx, int32_t k, ers_step_record* out
  * successor did not land on a corner (features of steps <= k, target from step k+1).  X: cap x
  * 32, T: cap x 2 (may be NULL to count); *count receives the number of samples available. */
 ers_status ers_batch_samples(const ers_ctx* ctx, float* X, float* T, int32_t cap, int32_t* count);
+/* Batched Arnoldi iterations as CUDA graphs (enable = 1, the default) or as separate launches.
+ * One graph per combination of Krylov spaces (the solution spaces, the error space) holds an
+ * iteration: C v_j, the forward and backward solves, Gram-Schmidt and the dimension test; the
+ * iteration index lives on the device, so the same graph is replayed for every j.  Graphs are
+ * captured on the context's stream; on the legacy default stream (which cannot be captured)
+ * or if a capture fails, the context falls back to separate launches. */
+ers_status ers_batch_set_graphs(ers_ctx* ctx, int32_t enable);
+
 /* Controller counters of the batched runs so far: proposals made by the network, proposals
  * rejected by the error test (each falls back to the plain rule), Krylov vectors built. */
 ers_status ers_batch_ctrl_stats(const ers_ctx* ctx, int64_t* proposals, int64_t* rejected,
                                 int64_t* krylov_vectors);
 
-/* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL = a private stream
- * created at ers_create).  All device work of later calls is ordered on it. */
+/* Bind the context to a CUDA stream (cudaStream_t passed as void*; NULL = the private stream
+ * created at ers_create).  All device work of later calls is ordered on it.  The caller keeps
+ * ownership of its stream, which must outlive the context's use of it; ers_destroy destroys
+ * only the private stream. */
 ers_status ers_set_stream(ers_ctx* ctx, void* stream);
 
 /* x(0) = DC solution (Alg. 2): Newton on G_lin x + i_dev(x) = B u(0) through the same LU

@@ -547,8 +547,8 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
       return bail(fail(c, e_ == cudaErrorMemoryAllocation ? ERS_ERR_OOM : ERS_ERR_CUDA,  \
                        std::string(#call) + ": " + cudaGetErrorString(e_)));             \
   } while (0)
-  CUB(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-  c->own_stream = true;
+  CUB(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  c->stream = c->own_stream;
   CUB(factor_kernel_attributes());
   CUB(solve_kernel_attributes());
   CUB(krylov_init_constants());
@@ -751,12 +751,11 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const e
 
 ers_status ers_set_stream(ers_ctx* c, void* stream) {
   if (!c) return ERS_ERR_INVALID;
-  if (stream) c->stream = (cudaStream_t)stream;
-  else {
-    if (!c->own_stream) {
-      CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-      c->own_stream = true;
-    }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;   // the caller's; never destroyed by the library
+  } else {
+    if (!c->own_stream) CU(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
   }
   return ERS_OK;
 }
@@ -1149,13 +1148,15 @@ void ers_destroy(ers_ctx* c) {
                   (void*)c->d_mstart, (void*)c->d_mused, (void*)c->bdf, (void*)c->d_feat,
                   (void*)c->d_pred, (void*)c->d_kv, (void*)c->d_where,
                   (void*)c->bscan_res, (void*)c->bscan_last, (void*)c->bscan_fin,
-                  (void*)c->bscan_y})
+                  (void*)c->bscan_y, (void*)c->bj})
     f(p);
+  for (auto& g : c->iter_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& ev : c->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
 

@@ -65,6 +65,7 @@ struct BArgs {
   double eps;
   int m_min, m_max;
   unsigned* status;
+  const int32_t* jdev;         // device iteration index (graph replays); NULL: use j
   unsigned long long* kv;      // count of directions built
   unsigned* where;             // first non-finite result: [flag, status bit, instance, slot * 256 + j]
   PadeCoef pade;
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(BT) k_bmgs(BArgs A) {
   const int i = blockIdx.x, b = blockIdx.y, slot = A.slot[b];
   KrylovState& K = A.ks[slot * A.ninst + i];
   if (!A.mask[i] || K.done) return;
-  const int s0 = A.seg[2 * i], s1 = A.seg[2 * i + 1], n = A.n, j = A.j;
+  const int s0 = A.seg[2 * i], s1 = A.seg[2 * i + 1], n = A.n;
+  const int j = A.jdev ? *A.jdev : A.j;
   double* w = A.src[b];
   const double* V = A.V[b];
   double* H = bH_of(A, slot, i);
@@ -297,6 +299,8 @@ __global__ void k_bpick(BArgs A, ScanBuf S) {
   }
 }
 
+__global__ void k_binc(int32_t* jdev) { *jdev += 1; }
+
 // largest dimension chosen by the spaces of each instance
 // (spaces 0 .. nb-1)
 __global__ void k_bmused(int ninst, int nb, const KrylovState* ks, int32_t* out) {
@@ -379,12 +383,14 @@ __global__ void k_bcopy(int n, const int32_t* inst_of, const int32_t* mask, cons
   if (e < n && mask[inst_of[e]]) dst[e] = src[e];
 }
 
+// y_v = C (V_v)_j for the nv spaces; j from jdev when given (graph replays), else j
 __global__ void k_brhs_C(int n, int nv, const int32_t* ptr, const int32_t* idx,
-                         const double* val, const double* x0, const double* x1, const double* x2,
-                         double* y) {
+                         const double* val, const double* V0, const double* V1, const double* V2,
+                         const int32_t* jdev, int j, double* y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double* xs[3] = {x0, x1, x2};
+  const int64_t off = (int64_t)(jdev ? *jdev : j) * n;
+  const double* xs[3] = {V0 + off, V1 ? V1 + off : nullptr, V2 ? V2 + off : nullptr};
   for (int v = 0; v < nv; ++v) {
     double acc = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * xs[v][idx[e]];
@@ -466,6 +472,86 @@ ScanBuf scan_buf(ers_ctx* c) {
   return ScanBuf{c->bscan_res, c->bscan_last, c->bscan_fin, c->bscan_y};
 }
 
+// One Arnoldi iteration of the spaces of A: C v_j, the solves, Gram-Schmidt, the dimension
+// test.  With use_jdev the iteration index is read from (and advanced in) device memory, which
+// makes the sequence replayable as a graph.
+cudaError_t enqueue_iteration(ers_ctx* c, const BArgs& A, int nb, int j, bool use_jdev) {
+  const int32_t* jd = use_jdev ? c->bj : nullptr;
+  k_brhs_C<<<nblk(c->n), 256, 0, c->stream>>>(c->n, nb, c->C_ptr, c->C_idx, c->C_val, A.V[0],
+                                               nb > 1 ? A.V[1] : nullptr,
+                                               nb > 2 ? A.V[2] : nullptr, jd, j, c->solve_buf);
+  c->stats.kernel_launches++;
+  cudaError_t e = launch_solve(c, c->solve_buf, nb);
+  if (e != cudaSuccess) return e;
+  BArgs M = A;
+  M.j = j;
+  M.jdev = jd;
+  for (int b = 0; b < nb; ++b) M.src[b] = c->solve_buf + (size_t)b * c->n;
+  k_bmgs<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(M);
+  c->stats.kernel_launches++;
+  BArgs S = A;
+  S.mode = SMALL_RESID;
+  size_t mm = (size_t)c->opts.m_max;
+  k_bsmall<<<c->ninst * nb, 256, (6 * mm * mm + 2 * mm) * 8, c->stream>>>(S);
+  c->stats.kernel_launches++;
+  if (use_jdev) {
+    k_binc<<<1, 1, 0, c->stream>>>(c->bj);
+    c->stats.kernel_launches++;
+  }
+  return cudaGetLastError();
+}
+
+// The graph of one iteration for this combination of spaces (captured on first use).  Returns
+// nullptr when graphs are off or the capture fails (then graphs stay off for the context).
+ers_ctx::IterGraph* iteration_graph(ers_ctx* c, const BArgs& A, int nb, const int* slots) {
+  if (!c->batch_graphs) return nullptr;
+  const int ctrl = c->ctrl != nullptr;
+  for (auto& g : c->iter_graphs) {
+    bool same = g.nb == nb && g.ctrl == ctrl;
+    for (int b = 0; b < nb && same; ++b) same = g.slot[b] == slots[b];
+    if (same) return &g;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (c->stream == nullptr || cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    c->batch_graphs = false;     // legacy default stream, or a capture of the caller's
+    cudaGetLastError();
+    return nullptr;
+  }
+  const ers_stats_t s0 = c->stats;
+  const bool prof = c->profile;
+  c->profile = false;   // no event records inside the graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t ee = enqueue_iteration(c, A, nb, 0, true);
+    e = cudaStreamEndCapture(c->stream, &graph);
+    if (e == cudaSuccess) e = ee;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  c->profile = prof;
+  ers_ctx::IterGraph g;
+  g.launches = c->stats.kernel_launches - s0.kernel_launches;
+  g.solves = c->stats.solves - s0.solves;
+  g.passes = c->stats.solve_passes - s0.solve_passes;
+  g.rhs = c->stats.solve_rhs - s0.solve_rhs;
+  c->stats = s0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    c->batch_graphs = false;
+    return nullptr;
+  }
+  g.nb = nb;
+  g.ctrl = ctrl;
+  for (int b = 0; b < nb; ++b) g.slot[b] = slots[b];
+  g.exec = exec;
+  c->iter_graphs.push_back(g);
+  return &c->iter_graphs.back();
+}
+
 // Algorithm 1 up to the MEVP for the spaces `slots` of every instance set in `mask` (the host
 // copy of the device mask; adaptive m).  No space can finish before its first decision (at
 // m_min, or at the proposed dimension) unless it breaks down, and a broken-down space only
@@ -482,6 +568,8 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
   BArgs A = make_bargs(c, nb, slots, src, 1);
   k_binit<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(A);
   c->stats.kernel_launches++;
+  ers_ctx::IterGraph* G = iteration_graph(c, A, nb, slots);
+  if (G) BCU(cudaMemsetAsync(c->bj, 0, sizeof(int32_t), c->stream));
   for (int j = 0; j < mc; ++j) {
     if (j > 0 && j >= first_test) {
       k_bcount<<<1, 256, 0, c->stream>>>(A, c->bcount);
@@ -491,21 +579,16 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
       c->stats.kernel_launches++;
       if (cnt == 0) break;
     }
-    double* V[3] = {A.V[0], nb > 1 ? A.V[1] : nullptr, nb > 2 ? A.V[2] : nullptr};
-    k_brhs_C<<<nblk(c->n), 256, 0, c->stream>>>(c->n, nb, c->C_ptr, c->C_idx, c->C_val,
-                                                 V[0] + (size_t)j * c->n,
-                                                 V[1] ? V[1] + (size_t)j * c->n : nullptr,
-                                                 V[2] ? V[2] + (size_t)j * c->n : nullptr,
-                                                 c->solve_buf);
-    c->stats.kernel_launches++;
-    BCU(launch_solve(c, c->solve_buf, nb));
-    BArgs M = A;
-    M.j = j;
-    for (int b = 0; b < nb; ++b) M.src[b] = c->solve_buf + (size_t)b * c->n;
-    k_bmgs<<<dim3(c->ninst, nb), BT, 0, c->stream>>>(M);
-    c->stats.kernel_launches++;
-    ers_status st = launch_bsmall(c, A, SMALL_RESID);
-    if (st != ERS_OK) return st;
+    if (G) {
+      BCU(cudaGraphLaunch(G->exec, c->stream));
+      c->stats.graph_launches++;
+      c->stats.kernel_launches += G->launches;
+      c->stats.solves += G->solves;
+      c->stats.solve_passes += G->passes;
+      c->stats.solve_rhs += G->rhs;
+    } else {
+      BCU(enqueue_iteration(c, A, nb, j, false));
+    }
     // instances whose proposed first decision is at dimension j + 1: test [m_min, j + 1]
     if (c->ctrl && j + 1 > c->opts.m_min) {
       bool any = false;
@@ -661,6 +744,7 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
   BCU(cudaMalloc((void**)&c->bcount, sizeof(int32_t)));
   BCU(cudaMalloc((void**)&c->d_mstart, sizeof(int32_t) * ninst));
   BCU(cudaMalloc((void**)&c->d_kv, sizeof(unsigned long long)));
+  BCU(cudaMalloc((void**)&c->bj, sizeof(int32_t)));
   BCU(cudaMalloc((void**)&c->d_where, 4 * sizeof(unsigned)));
   BCU(cudaMemset(c->d_where, 0, 4 * sizeof(unsigned)));
   BCU(cudaMemset(c->d_kv, 0, sizeof(unsigned long long)));
@@ -912,6 +996,13 @@ ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts, dou
   c->ctrl_parts = parts;
   std::fill(c->proposed_inst.begin(), c->proposed_inst.end(), 0);
   std::fill(c->mstart_inst.begin(), c->mstart_inst.end(), c->opts.m_min);
+  return ERS_OK;
+}
+
+ers_status ers_batch_set_graphs(ers_ctx* c, int32_t enable) {
+  if (!c) return ERS_ERR_INVALID;
+  if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
+  c->batch_graphs = enable != 0;
   return ERS_OK;
 }
 

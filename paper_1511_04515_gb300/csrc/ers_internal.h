@@ -95,7 +95,7 @@ struct ers_ctx {
   ers::Symbolic sym;
   ers::DevicePlan plan;
   cudaStream_t stream = nullptr;
-  bool own_stream = false;
+  cudaStream_t own_stream = nullptr;   // the stream the library created (destroyed with it)
   int device = 0;
   int sm_count = 0;
   // host copies (permuted) needed by the driver
@@ -155,6 +155,16 @@ struct ers_ctx {
   unsigned long long* d_kv = nullptr;  // Krylov vectors built by the batched Arnoldi kernels
   unsigned* d_where = nullptr;         // first non-finite value of a batched run (4 words)
   double *bscan_res = nullptr, *bscan_last = nullptr, *bscan_y = nullptr;  // per (space, dim)
+  // CUDA graphs of one batched Arnoldi iteration, per combination of spaces
+  struct IterGraph {
+    int nb = 0, ctrl = 0;
+    int slot[ers::MAX_RHS] = {0, 0, 0};
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0, solves = 0, passes = 0, rhs = 0;   // per replay
+  };
+  std::vector<IterGraph> iter_graphs;
+  bool batch_graphs = true;
+  int32_t* bj = nullptr;               // device index of the current Arnoldi iteration
   int32_t* bscan_fin = nullptr;
   std::vector<int32_t> scan_mask;      // instances masked in the current batch_bases call
   int ctrl_parts = 0;                  // ERS_CTRL_H | ERS_CTRL_M: which proposals are used

@@ -425,32 +425,6 @@ __device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// One warp issues L2 prefetches for the factor data of a (non-group) task.
-__device__ __forceinline__ void prefetch_task(const SolveTask& T, const double* D,
-                                              const double* Pn, const int32_t* rows, int lane) {
-  if (T.kind == TASK_GROUP) return;
-  if (T.kind == TASK_DIAG) {
-    const char* d = reinterpret_cast<const char*>(D + T.d_off);
-    for (int64_t o = (int64_t)lane * 128; o < (int64_t)T.w * T.w * 8; o += 32 * 128)
-      prefetch_l2(d + o);
-  }
-  int len = T.r1 - T.r0;
-  if (len > 0) {
-    int lines = (len * 8 + 127) / 128 + 1;
-    const double* base = Pn + T.o_off;
-    for (int q = lane; q < T.w * lines; q += 32) {
-      int j = q / lines, l = q % lines;
-      int off = T.r0 + l * 16;
-      if (off < T.r) prefetch_l2(base + (int64_t)j * T.r + off);
-    }
-    if (lane == 0) prefetch_l2(rows + T.row_off + T.r0);
-  }
-}
-
 // Stage a w x w diagonal block and panel rows [r0, r1) (ld r) into shared memory.  Every
 // thread first issues all its loads (at most 16 + 16 independent requests), then stores.
 __device__ __forceinline__ void stage(const double* D, int w, const double* Pn, int r, int r0,

@@ -74,7 +74,8 @@ class Stats(C.Structure):
                 ("arena_doubles", C.c_int64), ("refactor_flops", C.c_double),
                 ("kernel_launches", C.c_int64), ("solve_passes", C.c_int64),
                 ("solve_rhs", C.c_int64), ("solve_ms", C.c_double),
-                ("solve_bytes_per_pass", C.c_double), ("solve_fma_per_rhs", C.c_double)]
+                ("solve_bytes_per_pass", C.c_double), ("solve_fma_per_rhs", C.c_double),
+                ("graph_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,7 +90,8 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_set_params", "ers_mlp_get_params", "ers_mlp_forward", "ers_mlp_forward_dev",
            "ers_mlp_grad", "ers_mlp_adam_step", "ers_mlp_train", "ers_mlp_last_error",
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
-           "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose"]
+           "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
+           "ers_batch_set_graphs"]
 
 _lib = None
 
@@ -146,6 +148,7 @@ def lib():
         "ers_mlp_destroy": ([P], None),
         "ers_batch_set_controller": ([P, P, I32, D], C.c_int),
         "ers_batch_trace": ([P, I32], C.c_int),
+        "ers_batch_set_graphs": ([P, I32], C.c_int),
         "ers_batch_records": ([P, I32, C.POINTER(StepRecord), I32, pi], C.c_int),
         "ers_batch_samples": ([P, pf, pf, I32, pi], C.c_int),
         "ers_batch_ctrl_stats": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -543,6 +546,10 @@ class BatchSimulator(Simulator):
         self._mlp = mlp
         self._check(lib().ers_batch_set_controller(self._ctx, mlp.handle if mlp else None,
                                                    int(parts), float(margin)))
+
+    def set_graphs(self, enable: bool = True):
+        """Batched Arnoldi iterations as CUDA graph replays (default) or separate launches."""
+        self._check(lib().ers_batch_set_graphs(self._ctx, int(bool(enable))))
 
     def trace(self, enable: bool = True):
         self._check(lib().ers_batch_trace(self._ctx, int(bool(enable))))
