@@ -12,6 +12,9 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <climits>
+#include <map>
+#include <set>
 #include <cstring>
 #include <numeric>
 
@@ -564,44 +567,52 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     std::vector<int32_t> pos(S.lvl_sn_ptr.begin(), S.lvl_sn_ptr.end() - 1);
     for (int s = 0; s < nsn; ++s) S.lvl_sn[pos[S.level[s]]++] = s;
   }
-  // arena: first-fit allocator simulated level by level
+  // arena: an allocator simulated level by level (best fit, ties to the lowest offset; free
+  // blocks indexed by offset for coalescing and by (length, offset) for the fit: O(log n) per
+  // operation, since a batch of many circuits has millions of fronts)
   {
-    struct Block { int64_t off, len; };
-    std::vector<Block> freel;  // sorted by offset
+    std::map<int64_t, int64_t> by_off;               // offset -> length
+    std::set<std::pair<int64_t, int64_t>> by_len;    // (length, offset)
     int64_t top = 0;
+    auto take = [&](std::map<int64_t, int64_t>::iterator it) {
+      by_len.erase({it->second, it->first});
+      by_off.erase(it);
+    };
+    auto put = [&](int64_t off, int64_t len) {
+      by_off[off] = len;
+      by_len.insert({len, off});
+    };
     auto alloc = [&](int64_t len) -> int64_t {
       len = (len + 31) & ~(int64_t)31;
-      for (size_t b = 0; b < freel.size(); ++b)
-        if (freel[b].len >= len) {
-          int64_t o = freel[b].off;
-          freel[b].off += len;
-          freel[b].len -= len;
-          if (freel[b].len == 0) freel.erase(freel.begin() + b);
-          return o;
-        }
+      auto f = by_len.lower_bound({len, INT64_MIN});
+      if (f != by_len.end()) {
+        int64_t o = f->second, l = f->first;
+        take(by_off.find(o));
+        if (l > len) put(o + len, l - len);
+        return o;
+      }
       int64_t o = top;
       top += len;
       return o;
     };
     auto release = [&](int64_t off, int64_t len) {
       len = (len + 31) & ~(int64_t)31;
-      Block nb{off, len};
-      auto it = std::lower_bound(freel.begin(), freel.end(), nb,
-                                 [](const Block& a, const Block& b) { return a.off < b.off; });
-      it = freel.insert(it, nb);
-      size_t k = it - freel.begin();
-      if (k + 1 < freel.size() && freel[k].off + freel[k].len == freel[k + 1].off) {
-        freel[k].len += freel[k + 1].len;
-        freel.erase(freel.begin() + k + 1);
+      auto nx = by_off.lower_bound(off);
+      if (nx != by_off.end() && off + len == nx->first) {   // merge with the next block
+        len += nx->second;
+        take(nx);
       }
-      if (k > 0 && freel[k - 1].off + freel[k - 1].len == freel[k].off) {
-        freel[k - 1].len += freel[k].len;
-        freel.erase(freel.begin() + k);
+      auto it = by_off.lower_bound(off);
+      if (it != by_off.begin()) {                              // merge with the previous block
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == off) {
+          off = pv->first;
+          len += pv->second;
+          take(pv);
+        }
       }
-      if (!freel.empty() && freel.back().off + freel.back().len == top) {
-        top = freel.back().off;
-        freel.pop_back();
-      }
+      if (off + len == top) top = off;                         // the block ends the arena
+      else put(off, len);
     };
     S.front_off.assign(nsn, 0);
     int64_t peak = 0;
