@@ -236,6 +236,7 @@ def run_ours(a):
     sim.dc(circ.nodeset)                   # x(0): Newton (linear: factor G once + one solve)
     torch.cuda.synchronize()
     factor_s = time.perf_counter() - tf
+    tuned, tune_ms = sim.autotune(nrhs=2, passes=3)     # resident CTAs per SM of the solves
     if a.warmup:
         sim.run(t_end, a.tol, max_steps=a.warmup)
     sim.profile(True)
@@ -328,7 +329,9 @@ def run_ours(a):
                        "factor_GB": st1["factor_doubles"] * 8 / 1e9,
                        "l2_flush": "inputs larger than L2 (factor values alone exceed 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "create_s": create_s, "factor_and_dc_s": factor_s},
+                       "create_s": create_s, "factor_and_dc_s": factor_s,
+                       "solve_ctas_per_sm": tuned,
+                       "autotune_ms_per_pass_at_1_2_3": tune_ms},
             "krylov_vectors_per_s": kvec_all / (ms_max * 1e-3),
             "rejects": int(nr),
             "gpu_launches": int(launches),
@@ -411,6 +414,7 @@ def run_batch_workload(a):
     create_s = time.perf_counter() - tc
     sim.set_stream(stream)
     sim.dc(np.concatenate([c.nodeset for c in circs]))
+    tuned, tune_ms = sim.autotune(nrhs=2, passes=3)
     _, x0, _ = sim.state()
     arms = {}
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
@@ -500,6 +504,7 @@ def run_batch_workload(a):
                        "train_samples": int(X.shape[0]), "train_loss": loss,
                        "train_s": train_s, "create_s": create_s,
                        "controller": {"parts": a.ctrl_parts, "margin_log2": a.ctrl_margin},
+                       "solve_ctas_per_sm": tuned, "autotune_ms_per_pass_at_1_2_3": tune_ms,
                        "parallelism": ("instances split over ranks (LPT on node count)"
                                        if world > 1 else "single GPU"),
                        "l2_flush": "none: every round streams the factor and all Krylov bases"},

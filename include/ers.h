@@ -330,6 +330,14 @@ ers_status ers_phi_small(ers_ctx* ctx, const double* H, int32_t ldh, int32_t m, 
  * and waits for the stream before returning. */
 ers_status ers_solve_dev_noalloc(ers_ctx* ctx, const double* b_dev, double* x_dev);
 
+/* Autotuner of the persistent triangular-solve kernels: with the current factor of G_k (the
+ * context refactors first if needed) time `passes` solve passes of `nrhs` (1-3) right-hand
+ * sides for 1, 2 and 3 resident CTAs per SM (any count is deadlock-free: a task only waits on
+ * earlier tasks of the ordered work list) and keep the fastest for the context's later solves.
+ * ms (3 doubles, may be NULL) receives the average pass time of each; *chosen (may be NULL) the
+ * count kept.  Changes no result: the same tasks run with the same dependencies. */
+ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen);
+
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
 /* Turn CUDA-event timing of the triangular-solve kernels on (1) or off (0); resets the

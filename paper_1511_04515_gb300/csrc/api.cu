@@ -1076,6 +1076,50 @@ ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, do
   return ERS_OK;
 }
 
+ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen) {
+  if (!c) return ERS_ERR_INVALID;
+  if (nrhs < 1 || nrhs > MAX_RHS || passes < 1)
+    return fail(c, ERS_ERR_INVALID, "autotune: nrhs in 1..3 and passes >= 1");
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  if (!c->factored) {
+    st = do_refactor(c);
+    if (st != ERS_OK) return st;
+  }
+  // right-hand sides from the state (any finite vector times the same work)
+  for (int k = 0; k < nrhs; ++k)
+    CU(cudaMemcpyAsync(c->solve_buf + (size_t)k * c->n, c->x, sizeof(double) * c->n,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const bool prof = c->profile;
+  c->profile = false;
+  double best = INFINITY;
+  int keep = c->solve_ctas_per_sm;
+  cudaError_t err = cudaSuccess;
+  for (int k = 1; k <= 3 && err == cudaSuccess; ++k) {
+    c->solve_ctas_per_sm = k;
+    err = launch_solve(c, c->solve_buf, nrhs);   // warm-up pass
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int q = 0; q < passes && err == cudaSuccess; ++q) err = launch_solve(c, c->solve_buf, nrhs);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    double avg = (double)t / passes;
+    if (ms) ms[k - 1] = avg;
+    if (err == cudaSuccess && avg < best) { best = avg; keep = k; }
+  }
+  c->profile = prof;
+  c->solve_ctas_per_sm = keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(c, ERS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
+  if (chosen) *chosen = keep;
+  return sync_status(c);
+}
+
 ers_status ers_stats(const ers_ctx* cc, ers_stats_t* out) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c || !out) return ERS_ERR_INVALID;

@@ -98,6 +98,7 @@ struct ers_ctx {
   cudaStream_t own_stream = nullptr;   // the stream the library created (destroyed with it)
   int device = 0;
   int sm_count = 0;
+  int solve_ctas_per_sm = 3;           // resident CTAs per SM of the persistent solves (tunable)
   // host copies (permuted) needed by the driver
   std::vector<double> bp;              // sorted unique PWL corner times
   // device arrays (permuted node order)

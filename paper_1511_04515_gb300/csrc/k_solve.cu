@@ -727,7 +727,7 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
   cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * (2 + 3 * (size_t)P.nsn), c->stream);
   if (e != cudaSuccess) return e;
   SolveArgs A{P, y, c->n, c->d_status};
-  int blocks = c->sm_count * 3;
+  int blocks = c->sm_count * c->solve_ctas_per_sm;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profile) {
     if (c->ev_free.empty()) {
@@ -842,7 +842,7 @@ extern "C" ers_status ers_solve_dev_noalloc(ers_ctx* c, const double* b_dev, dou
   if (e != cudaSuccess) return cuda_fail(e);
   k_gather_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, b_dev, c->solve_buf);
   SolveArgs A{P, c->solve_buf, n, c->d_status};
-  launch_pair<1>(c, A, c->sm_count * 3);
+  launch_pair<1>(c, A, c->sm_count * c->solve_ctas_per_sm);
   k_scatter_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, c->solve_buf, x_dev);
   c->stats.kernel_launches += 4;
   e = cudaGetLastError();

@@ -107,6 +107,22 @@ def test_batch_solve_matches_per_instance_lu(ers):
     sim.close()
 
 
+def test_autotuned_solves_match_sparse_lu(ers):
+    """The autotuner times 1, 2 and 3 resident CTAs per SM and keeps one; solves stay exact."""
+    circ = S.inverter_chain(stages=30, tree_nodes=40, seed=8)
+    sim = make(ers, circ)
+    x0 = O.dc_solution(circ, x0=circ.nodeset)
+    sim.set_state(0.0, x0)
+    chosen, ms = sim.autotune(nrhs=2, passes=3)
+    assert chosen in (1, 2, 3) and all(t > 0 for t in ms)
+    lin = O.linearize(circ, x0)
+    b = np.random.default_rng(5).normal(size=circ.n)
+    x = sim.solve(b)
+    ref = lin.solve(b)
+    assert np.max(np.abs(x - ref)) <= 1e-8 * np.max(np.abs(ref))
+    sim.close()
+
+
 def test_spmv_C(ers):
     circ = S.rc_mesh_2d(10, 10, seed=1)
     sim = make(ers, circ)
