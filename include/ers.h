@@ -338,6 +338,14 @@ ers_status ers_solve_dev_noalloc(ers_ctx* ctx, const double* b_dev, double* x_de
  * count kept.  Changes no result: the same tasks run with the same dependencies. */
 ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen);
 
+/* Host-only check of the triangular-solve work lists built for a pattern (no GPU): every
+ * supernode is computed by exactly one task per direction and every wait of a task refers to
+ * an earlier entry of its list (the property that makes the persistent solves deadlock-free).
+ * counts (8 values, may be NULL): forward and backward CTA entries, lane items (fwd, bwd),
+ * warp-task supernodes (fwd, bwd), DIAG entries (fwd, bwd).  ERS_ERR_INVALID with a
+ * violated property (or a malformed pattern). */
+ers_status ers_solve_plan_check(const ers_csr* pattern, int64_t* counts);
+
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
 /* Turn CUDA-event timing of the triangular-solve kernels on (1) or off (0); resets the

@@ -1165,6 +1165,17 @@ ers_status ers_analyze(const ers_csr* pat, ers_stats_t* out, int32_t* perm) {
   return ERS_OK;
 }
 
+ers_status ers_solve_plan_check(const ers_csr* pat, int64_t* counts) {
+  if (!pat || pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
+  Symbolic S;
+  SymbolicOptions so;
+  if (!analyze(pat->n_rows, pat->rowptr, pat->colidx, so, S).empty()) return ERS_ERR_INVALID;
+  int64_t c[8];
+  std::string err = check_solve_plan(S, c);
+  if (counts) std::memcpy(counts, c, sizeof(c));
+  return err.empty() ? ERS_OK : ERS_ERR_INVALID;
+}
+
 void ers_destroy(ers_ctx* c) {
   if (!c) return;
   auto f = [](void* p) { if (p) cudaFree(p); };

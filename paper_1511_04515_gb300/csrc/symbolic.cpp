@@ -902,4 +902,112 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
   return "";
 }
 
+
+std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
+  const int nsn = S.nsn;
+  for (int q = 0; q < 8; ++q) counts[q] = 0;
+  counts[0] = (int64_t)S.fwd.size();
+  counts[1] = (int64_t)S.bwd.size();
+  // ---- forward: the entry computing each supernode, and the entries of every arrival
+  std::vector<int64_t> fpos(nsn, -1);
+  std::vector<int64_t> arrive_last(nsn, -1), arrive_cnt(nsn, 0);
+  std::vector<int64_t> chunk_entry;   // entries holding far chunks, with their supernode
+  std::vector<int32_t> chunk_sn;
+  auto arrive = [&](int32_t tgt0, int32_t ntgt, int64_t e) {
+    for (int q = 0; q < ntgt; ++q) {
+      int t = S.fwd_tgt[tgt0 + q];
+      arrive_last[t] = std::max(arrive_last[t], e);
+      arrive_cnt[t]++;
+    }
+  };
+  for (int64_t e = 0; e < (int64_t)S.fwd.size(); ++e) {
+    const SolveTask& T = S.fwd[e];
+    if (T.kind == TASK_DIAG) {
+      if (fpos[T.sn] >= 0) return "forward: supernode computed twice";
+      fpos[T.sn] = e;
+      counts[6]++;
+      arrive(T.tgt0, T.ntgt, e);
+    } else if (T.kind == TASK_GROUP || T.kind == TASK_BULK) {
+      for (int w = 0; w < T.r0; ++w) {
+        const SolveTask& U = S.fwd_small[T.sn + w];
+        if (U.kind == TASK_FUSED) {
+          if (fpos[U.sn] >= 0) return "forward: supernode computed twice";
+          fpos[U.sn] = e;
+          counts[4]++;
+          arrive(U.tgt0, U.ntgt, e);
+        } else if (U.kind == TASK_LANES) {
+          for (int l = 0; l < U.r0; ++l) {
+            const int32_t* it = S.fwd_lane.data() + 4 * ((int64_t)U.sn + l);
+            if (fpos[it[0]] >= 0) return "forward: supernode computed twice";
+            fpos[it[0]] = e;
+            counts[2]++;
+            arrive(it[1], it[2], e);
+          }
+        } else if (U.kind == TASK_OFF) {
+          chunk_entry.push_back(e);
+          chunk_sn.push_back(U.sn);
+          arrive(U.tgt0, U.ntgt, e);
+        } else {
+          return "forward: unknown warp task";
+        }
+      }
+    } else {
+      return "forward: unknown entry";
+    }
+  }
+  for (int s = 0; s < nsn; ++s) {
+    if (fpos[s] < 0) return "forward: supernode " + std::to_string(s) + " never computed";
+    if (arrive_cnt[s] != S.fwd_expect[s]) return "forward: arrival count mismatch";
+    if (arrive_last[s] >= fpos[s]) return "forward: an arrival comes after the wait";
+  }
+  for (size_t q = 0; q < chunk_entry.size(); ++q)
+    if (fpos[chunk_sn[q]] >= chunk_entry[q]) return "forward: far chunk before its DIAG";
+  // ---- backward
+  std::vector<int64_t> bpos(nsn, -1), chunks_last(nsn, -1), chunks_cnt(nsn, 0);
+  struct Wait { int64_t e; int32_t on; };
+  std::vector<Wait> waits;
+  for (int64_t e = 0; e < (int64_t)S.bwd.size(); ++e) {
+    const SolveTask& T = S.bwd[e];
+    if (T.kind == TASK_DIAG) {
+      if (bpos[T.sn] >= 0) return "backward: supernode computed twice";
+      bpos[T.sn] = e;
+      counts[7]++;
+      if (T.wait_sn >= 0) waits.push_back({e, T.wait_sn});
+    } else if (T.kind == TASK_GROUP || T.kind == TASK_BULK) {
+      for (int w = 0; w < T.r0; ++w) {
+        const SolveTask& U = S.bwd_small[T.sn + w];
+        if (U.kind == TASK_FUSED) {
+          if (bpos[U.sn] >= 0) return "backward: supernode computed twice";
+          bpos[U.sn] = e;
+          counts[5]++;
+          if (U.wait_sn >= 0) waits.push_back({e, U.wait_sn});
+        } else if (U.kind == TASK_LANES) {
+          for (int l = 0; l < U.r0; ++l) {
+            const int32_t* it = S.bwd_lane.data() + 4 * ((int64_t)U.sn + l);
+            if (bpos[it[0]] >= 0) return "backward: supernode computed twice";
+            bpos[it[0]] = e;
+            counts[3]++;
+            if (it[1] >= 0) waits.push_back({e, it[1]});
+          }
+        } else if (U.kind == TASK_OFF) {
+          chunks_last[U.sn] = std::max(chunks_last[U.sn], e);
+          chunks_cnt[U.sn]++;
+          if (U.wait_sn >= 0) waits.push_back({e, U.wait_sn});
+        } else {
+          return "backward: unknown warp task";
+        }
+      }
+    } else {
+      return "backward: unknown entry";
+    }
+  }
+  for (int s = 0; s < nsn; ++s) {
+    if (bpos[s] < 0) return "backward: supernode " + std::to_string(s) + " never computed";
+    if (chunks_cnt[s] != S.bwd_nchunk[s]) return "backward: chunk count mismatch";
+    if (chunks_last[s] >= bpos[s]) return "backward: a far chunk comes after its DIAG";
+  }
+  for (const Wait& w : waits)
+    if (bpos[w.on] >= w.e) return "backward: a wait refers to a later entry";
+  return "";
+}
 }  // namespace ers

@@ -102,6 +102,14 @@ struct Symbolic {
 };
 
 // pattern: n x n CSR (old order, rows sorted, unique). Returns "" on success.
+// Check the triangular-solve work lists: every supernode is computed by exactly one task per
+// direction, and every wait of a task (forward: the arrivals of all units that scatter into
+// it, the DIAG task that publishes a far chunk's supernode; backward: the parent's or the
+// touched ancestor's completion, the far chunks a DIAG counts) refers to an entry earlier in
+// its list, which makes the persistent solves deadlock-free.  counts[8] receives: forward and
+// backward CTA entries, lane items, warp-task supernodes, DIAG entries (fwd, bwd each).
+std::string check_solve_plan(const Symbolic& S, int64_t counts[8]);
+
 std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const SymbolicOptions& opt,
                     Symbolic& out);
 

@@ -91,7 +91,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_grad", "ers_mlp_adam_step", "ers_mlp_train", "ers_mlp_last_error",
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
-           "ers_batch_set_graphs", "ers_autotune"]
+           "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check"]
 
 _lib = None
 
@@ -133,6 +133,7 @@ def lib():
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
+        "ers_solve_plan_check": ([C.POINTER(Csr), C.POINTER(C.c_int64)], C.c_int),
         "ers_ctrl_features": ([C.POINTER(StepRecord), I32, pf], C.c_int),
         "ers_ctrl_target": ([C.POINTER(StepRecord), I32, C.POINTER(StepRecord), pf], C.c_int),
         "ers_ctrl_propose": ([pf, C.POINTER(StepRecord), D, I32, pd, pi], C.c_int),
@@ -340,6 +341,19 @@ def analyze(pattern) -> dict:
     d = st.as_dict()
     d["perm"] = perm
     return d
+
+
+def solve_plan_check(pattern) -> dict:
+    """Host-only check of the solve work lists of a square CSR pattern (see ers.h); raises
+    ErsError when a property is violated."""
+    h = _CsrHold(pattern)
+    counts = np.zeros(8, np.int64)
+    rc = lib().ers_solve_plan_check(C.byref(h.c), counts.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc != 0:
+        raise ErsError(rc, "solve plan check failed")
+    keys = ["fwd_entries", "bwd_entries", "fwd_lane_items", "bwd_lane_items",
+            "fwd_warp_supernodes", "bwd_warp_supernodes", "fwd_diag", "bwd_diag"]
+    return dict(zip(keys, counts.tolist()))
 
 
 class Simulator:

@@ -101,3 +101,29 @@ def test_analyze_rejects_missing_diagonal(E):
     M.eliminate_zeros()
     with pytest.raises(E.ErsError):
         E.analyze(M)
+
+
+@pytest.mark.parametrize("name", ["rc2d", "rc3d", "chain", "batch", "randrc"])
+def test_solve_plan_covers_and_orders(E, name):
+    """Every supernode is computed once per direction, every wait points to an earlier entry
+    (deadlock-free persistent solves); the batch of chains exercises the lane tasks."""
+    if name == "rc2d":
+        G = S.rc_mesh_2d(32, 32, seed=0).G
+    elif name == "rc3d":
+        G = S.rc_mesh_3d(20, 20, 20, seed=1, n_loads=80).G
+    elif name == "chain":
+        G = S.inverter_chain(stages=50, tree_nodes=100, seed=2).G
+    elif name == "batch":
+        circs = S.batch_family(n_inst=48, seed0=7000, stage_lo=30, stage_hi=60, tree_nodes=100)
+        G = sp.block_diag([c.G for c in circs], format="csr")
+    else:
+        G = S.random_rc(n=60, seed=3, density=0.4).G
+    G = sp.csr_matrix(G)
+    G.sort_indices()
+    c = E.solve_plan_check(G)
+    st = E.analyze(G)
+    nsn = st["nsn"]
+    assert c["fwd_lane_items"] + c["fwd_warp_supernodes"] + c["fwd_diag"] == nsn
+    assert c["bwd_lane_items"] + c["bwd_warp_supernodes"] + c["bwd_diag"] == nsn
+    if name == "batch":
+        assert c["fwd_lane_items"] > 0 and c["bwd_lane_items"] > 0
