@@ -361,6 +361,35 @@ def batch_workload_name(a):
             f"sigma 5%, 0 -> {a.t_end * 1e9:g} ns (first input edge), tol 1e-6")
 
 
+def _oracle_instance(args):
+    """One batch instance to t_end with the oracle (runs in a spawned worker, 1 BLAS thread)."""
+    import numpy as np
+    from oracle import ers_oracle as O
+    circ, t_end, tol = args
+    x0 = O.dc_solution(circ, x0=circ.nodeset)
+    t0 = time.perf_counter()
+    x, t, st = O.er_run(circ, t_end=t_end, tol=tol, x0=x0)
+    return st.steps, time.perf_counter() - t0
+
+
+def batch_oracle_baseline(circs, idx, t_end, tol):
+    """The oracle on the sampled instances, in parallel over the host cores (spawn pool)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    cores = max(1, min(len(idx), os.cpu_count() or 1))
+    w0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_instance, [(circs[k], t_end, tol) for k in idx])
+    wall = time.perf_counter() - w0
+    steps = sum(r[0] for r in res)
+    return {"value": steps / wall, "unit": "instance-steps/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{len(idx)} instances of the batch to t_end, one per worker process "
+                       f"(spawn, 1 BLAS thread each), SuperLU + numpy; {steps} steps in "
+                       f"{wall:.1f} s wall; per-instance seconds "
+                       f"{[round(r[1], 1) for r in res]}")}
+
+
 def run_batch_workload(a):
     import numpy as np
     import torch
@@ -478,6 +507,15 @@ def run_batch_workload(a):
     xref = [ref.state_inst(q)[1] for q in range(len(ref_idx))]
     ref.close()
     progress("tight reference done")
+    cpu = None
+    if not a.no_baseline and world == 1:
+        try:
+            ncpu = max(1, min(len(circs), os.cpu_count() or 1))
+            cpu_pick = list(range(0, len(circs), max(1, len(circs) // ncpu)))[:ncpu]
+            cpu = batch_oracle_baseline(circs, cpu_pick, a.t_end, a.tol)
+            progress(f"oracle baseline: {cpu['value']:.1f} instance-steps/s on {cpu['cores']} cores")
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "error": str(ex)[-300:]}
     err = {}
     for name, arm in arms.items():
         err[name] = max(float(np.max(np.abs(arm["x"][k] - xr))) for k, xr in zip(ref_idx, xref))
@@ -518,6 +556,7 @@ def run_batch_workload(a):
                         "batched_plain_vs_plain_sequential": seq_est / plain["seconds"]},
             "max_abs_err_vs_tight_run": {**err, "instances": ref_idx, "tight_tol": a.tol / 10},
             "instance_steps_per_s": learned["steps"] / learned["seconds"],
+            "cpu_baseline": cpu,
             "krylov_vectors_per_s": learned["krylov_vectors"] / learned["seconds"],
             "gpu_launches": learned["gpu_launches"],
             "clocks": clocks}
