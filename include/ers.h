@@ -330,6 +330,12 @@ ers_status ers_phi_small(ers_ctx* ctx, const double* H, int32_t ldh, int32_t m, 
  * and waits for the stream before returning. */
 ers_status ers_solve_dev_noalloc(ers_ctx* ctx, const double* b_dev, double* x_dev);
 
+/* Failure-path self-test: a kernel waits, with the bounded wait every device-side dependency
+ * uses, on a flag that nothing sets.  Returns ERS_ERR_TIMEOUT (the wait gave up after its
+ * poll limit, under a second, and recorded the timeout instead of hanging); the context's
+ * status is cleared again and the context stays usable. */
+ers_status ers_wait_selftest(ers_ctx* ctx);
+
 /* Autotuner of the persistent triangular-solve kernels: with the current factor of G_k (the
  * context refactors first if needed) time `passes` solve passes of `nrhs` (1-3) right-hand
  * sides for 1, 2 and 3 resident CTAs per SM (any count is deadlock-free: a task only waits on

@@ -20,6 +20,7 @@ cudaError_t factor_kernel_attributes();
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag);
 cudaError_t solve_kernel_attributes();
 // k_krylov.cu
 cudaError_t krylov_init_constants();
@@ -1074,6 +1075,20 @@ ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, do
   for (int k = 0; k < m; ++k) y[k] = hy[k];
   *last = hy[m];
   return ERS_OK;
+}
+
+ers_status ers_wait_selftest(ers_ctx* c) {
+  if (!c) return ERS_ERR_INVALID;
+  ers_status st = clear_status(c);
+  if (st != ERS_OK) return st;
+  // the flag: a zeroed word of the device reduction scratch that no kernel is using now
+  int32_t* flag = reinterpret_cast<int32_t*>(c->red);
+  CU(cudaMemsetAsync(flag, 0, sizeof(int32_t), c->stream));
+  CU(launch_wait_probe(c, flag));
+  CU(cudaStreamSynchronize(c->stream));
+  st = sync_status(c);          // ERS_ERR_TIMEOUT when the bounded wait gave up
+  ers_status cl = clear_status(c);
+  return cl != ERS_OK ? cl : st;
 }
 
 ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen) {

@@ -703,6 +703,18 @@ void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const doubl
   c->stats.kernel_launches++;
 }
 
+// Failure-path self-test: one thread waits, with the solves' bounded wait, on a flag that
+// nothing sets; the wait gives up after SPIN_LIMIT polls and records ST_TIMEOUT.
+__global__ void k_wait_probe(const int32_t* flag, unsigned* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) wait_geq(flag, 1, status);
+}
+
+cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag) {
+  k_wait_probe<<<1, 32, 0, c->stream>>>(flag, c->d_status);
+  c->stats.kernel_launches++;
+  return cudaGetLastError();
+}
+
 template <int NRHS>
 static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
   k_trsv_fwd<NRHS><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);

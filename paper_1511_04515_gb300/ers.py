@@ -91,7 +91,8 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_grad", "ers_mlp_adam_step", "ers_mlp_train", "ers_mlp_last_error",
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
-           "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check"]
+           "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check",
+           "ers_wait_selftest"]
 
 _lib = None
 
@@ -127,6 +128,7 @@ def lib():
         "ers_phi_small": ([P, pd, I32, I32, D, pd, pd], C.c_int),
         "ers_stats": ([P, C.POINTER(Stats)], C.c_int),
         "ers_autotune": ([P, I32, I32, pd, pi], C.c_int),
+        "ers_wait_selftest": ([P], C.c_int),
         "ers_profile": ([P, I32], C.c_int),
         "ers_solve_dev_noalloc": ([P, P, P], C.c_int),
         "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, C.POINTER(Opts)], C.c_int),
@@ -490,6 +492,10 @@ class Simulator:
         self._check(lib().ers_phi_small(self._ctx, _dptr(H.ravel(order="F")), int(H.shape[0]), m,
                                         float(h), _dptr(y), C.byref(last)))
         return y, last.value
+
+    def wait_selftest(self) -> int:
+        """Status of the bounded-wait self-test (ERS_ERR_TIMEOUT = 6 expected; see ers.h)."""
+        return int(lib().ers_wait_selftest(self._ctx))
 
     def autotune(self, nrhs: int = 2, passes: int = 5):
         """Pick the resident CTAs per SM of the solve kernels by timing (see ers.h); returns

@@ -389,6 +389,21 @@ def test_adaptive_run_matches_oracle(ers):
 
 
 # --- boundary behaviour ------------------------------------------------------------------
+def test_bounded_wait_reports_timeout(ers):
+    """Failure detection without a GPU fault: a device wait on a flag that nothing sets gives
+    up after its poll limit and reports ERS_ERR_TIMEOUT; the context keeps working."""
+    circ = S.rc_mesh_2d(8, 8, seed=1)
+    sim = make(ers, circ)
+    sim.set_state(0.0, np.zeros(circ.n))
+    assert sim.wait_selftest() == 6          # ERS_ERR_TIMEOUT
+    lin = O.linearize(circ, np.zeros(circ.n))
+    b = np.random.default_rng(9).normal(size=circ.n)
+    x = sim.solve(b)
+    ref = lin.solve(b)
+    assert np.max(np.abs(x - ref)) <= 1e-8 * np.max(np.abs(ref))
+    sim.close()
+
+
 def test_step_across_breakpoint_rejected(ers):
     circ = S.rc_mesh_2d(8, 8, seed=1)
     sim = make(ers, circ)
