@@ -129,6 +129,9 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, con
  * instance k-1's); ers_get_state_inst reads one instance. */
 ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
                             const ers_opts* opts);
+/* (opts->correction and opts->combined_vector are single-context options: ERS_ERR_INVALID
+ * here.  ers_step / ers_run on a batched context return ERS_ERR_INVALID: it steps with
+ * ers_run_batch.) */
 
 /* Advance every instance of a batched context to t_end with Algorithm 2 (at most max_steps
  * rounds when max_steps > 0; in a round every unfinished instance takes one accepted step).

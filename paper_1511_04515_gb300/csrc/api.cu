@@ -858,6 +858,7 @@ static ers_status step_core(ers_ctx* c, double h, int32_t m, int32_t* m_used, do
 
 ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* err_inf) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->bks) return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
   ers_status st = step_core(c, h, m, m_used, err_inf);
   if (st != ERS_OK) return st;
   CU(cudaMemcpyAsync(c->x, c->xnew, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
@@ -871,6 +872,7 @@ ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* er
 ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int32_t* nsteps,
                    int32_t* nreject) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->bks) return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
   if (!(t_end > c->t)) return fail(c, ERS_ERR_INVALID, "t_end must exceed the current time");
   if (!(tol > 0.0)) return fail(c, ERS_ERR_INVALID, "tol must be positive");
   const ers_opts& o = c->opts;

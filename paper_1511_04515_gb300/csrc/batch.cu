@@ -635,6 +635,10 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
   ers_ctx* c = new ers_ctx();
   *out = c;
   if (!inst || ninst < 1) return ctx_fail(c, ERS_ERR_INVALID, "need at least one instance");
+  if (opts && (opts->correction || opts->combined_vector))
+    return ctx_fail(c, ERS_ERR_INVALID,
+                    "batched runs use the ER step with separate phi_1 / phi_2 spaces "
+                    "(correction and combined_vector are single-context options)");
   // concatenate the instances into one block-diagonal circuit
   std::vector<int32_t> gp{0}, gi, cp{0}, ci, bp{0}, bi;
   std::vector<double> gv, cv, bv;

@@ -127,3 +127,13 @@ def test_solve_plan_covers_and_orders(E, name):
     assert c["bwd_lane_items"] + c["bwd_warp_supernodes"] + c["bwd_diag"] == nsn
     if name == "batch":
         assert c["fwd_lane_items"] > 0 and c["bwd_lane_items"] > 0
+
+
+def test_batch_rejects_single_context_options(E):
+    """ER-C and the combined space are single-context options: a batched context refuses them
+    (checked before any device work, so this runs without a GPU)."""
+    circs = [S.rc_mesh_2d(4, 4, seed=s, n_src=4) for s in range(2)]
+    for kw in ({"correction": 1}, {"combined_vector": 1}):
+        with pytest.raises(E.ErsError) as ei:
+            E.BatchSimulator(circs, opts=E.make_opts(**kw))
+        assert "single-context" in str(ei.value)
