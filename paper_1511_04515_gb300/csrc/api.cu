@@ -688,6 +688,8 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   CUB(upload(&P.lvl_sn, S.lvl_sn));
   CUB(upload(&P.lvl_slot, S.lvl_slot));
   CUB(upload(&P.ea_child, S.ea_child));
+  CUB(upload(&P.ch_ptr, S.ch_ptr));
+  CUB(upload(&P.ch_list, S.ch_list));
   CUB(upload(&P.asm_dst, S.asm_dst));
   CUB(upload(&P.tile_sn, S.tile_sn));
   CUB(upload(&P.tile_ij, S.tile_ij));
@@ -1199,7 +1201,7 @@ void ers_destroy(ers_ctx* c) {
   DevicePlan& P = c->plan;
   for (void* p : {(void*)P.sn_start, (void*)P.sn_parent, (void*)P.rows, (void*)P.rel, (void*)P.rptr,
                   (void*)P.d_off, (void*)P.o_off, (void*)P.front_off, (void*)P.lvl_sn,
-                  (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.asm_dst, (void*)P.tile_sn,
+                  (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.ch_ptr, (void*)P.ch_list, (void*)P.asm_dst, (void*)P.tile_sn,
                   (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd, (void*)P.fwd_small, (void*)P.bwd_small,
                   (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.fwd_lane,
                   (void*)P.bwd_lane, (void*)P.LDi,

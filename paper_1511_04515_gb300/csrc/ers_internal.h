@@ -60,6 +60,7 @@ struct DevicePlan {
   int32_t *sn_start = nullptr, *sn_parent = nullptr, *rows = nullptr, *rel = nullptr;
   int64_t *rptr = nullptr, *d_off = nullptr, *o_off = nullptr, *front_off = nullptr;
   int32_t *lvl_sn = nullptr, *lvl_slot = nullptr, *ea_child = nullptr;
+  int32_t *ch_ptr = nullptr, *ch_list = nullptr;   // children in rank order (CSR)
   int64_t* asm_dst = nullptr;
   int32_t *tile_sn = nullptr, *tile_ij = nullptr, *ptask_sn = nullptr, *ptask_r0 = nullptr;
   SolveTask *fwd = nullptr, *bwd = nullptr, *fwd_small = nullptr, *bwd_small = nullptr;

@@ -139,21 +139,35 @@ __global__ void k_mf_assemble(DevicePlan P, int lo, int hi, const double* Gval) 
   P.arena[P.asm_dst[e]] = Gval[e];
 }
 
-// extend-add of the children listed in ea_child[lo..hi) (each parent at most once)
-__global__ void k_mf_extend_add(DevicePlan P, int lo, int hi) {
-  int c = P.ea_child[lo + blockIdx.x];
-  int p = P.sn_parent[c];
-  int cc0, cw, cr, pc0, pw, pr;
-  sn_dims(P, c, cc0, cw, cr);
+// extend-add of every child into the supernodes lvl_sn[lo..hi) in one launch: CTA (x, y)
+// owns the columns pcol of parent lvl_sn[lo + x] with pcol % gridDim.y == y and adds the
+// parent's children one after another in rank order (a barrier between children, whose rows
+// reach the same parent entries through different threads).  Every parent entry thus receives
+// its additions in the same order as with one launch per child rank: the same sums, bit for
+// bit, and no two CTAs write one entry.
+__global__ void k_mf_extend_add_level(DevicePlan P, int lo) {
+  const int p = P.lvl_sn[lo + blockIdx.x];
+  const int cb = P.ch_ptr[p], ce = P.ch_ptr[p + 1];
+  if (cb == ce) return;
+  int pc0, pw, pr;
   sn_dims(P, p, pc0, pw, pr);
-  int64_t fc = cw + cr, fp = pw + pr;
-  const double* Fc = P.arena + P.front_off[c];
+  const int64_t fp = pw + pr;
   double* Fp = P.arena + P.front_off[p];
-  const int32_t* rel = P.rel + P.rptr[c];
-  for (int b = blockIdx.y; b < cr; b += gridDim.y) {
-    int64_t pcol = (int64_t)rel[b] * fp;
-    const double* src = Fc + (int64_t)(cw + b) * fc + cw;
-    for (int a = threadIdx.x; a < cr; a += blockDim.x) Fp[rel[a] + pcol] += src[a];
+  for (int q = cb; q < ce; ++q) {
+    const int c = P.ch_list[q];
+    int cc0, cw, cr;
+    sn_dims(P, c, cc0, cw, cr);
+    const int64_t fc = cw + cr;
+    const double* Fc = P.arena + P.front_off[c];
+    const int32_t* rel = P.rel + P.rptr[c];
+    for (int b = 0; b < cr; ++b) {
+      const int pcol = rel[b];
+      if (pcol % (int)gridDim.y != (int)blockIdx.y) continue;
+      const double* src = Fc + (int64_t)(cw + b) * fc + cw;
+      double* dst = Fp + (int64_t)pcol * fp;
+      for (int a = threadIdx.x; a < cr; a += blockDim.x) dst[rel[a]] += src[a];
+    }
+    __syncthreads();
   }
 }
 
@@ -358,18 +372,21 @@ cudaError_t launch_refactor(ers_ctx* c) {
     c->stats.kernel_launches += 2;
     int slo = S.lvl_slot_ptr[l], shi = S.lvl_slot_ptr[l + 1];
     if (shi > slo) k_mf_assemble<<<(shi - slo + 255) / 256, 256, 0, c->stream>>>(P, slo, shi, c->G_val);
-    for (int rk = 0; rk < S.ea_maxrank; ++rk) {
-      int g = l * S.ea_maxrank + rk;
-      int elo = S.ea_ptr[g], ehi = S.ea_ptr[g + 1];
-      if (ehi == elo) continue;
-      int maxr = 1;
-      for (int q = elo; q < ehi; ++q) {
-        int ch = S.ea_child[q];
-        maxr = std::max<int>(maxr, (int)(S.rptr[ch + 1] - S.rptr[ch]));
+    {
+      // children of this level's supernodes, all ranks in one launch
+      const int g0 = l * S.ea_maxrank, g1 = g0 + S.ea_maxrank;
+      if (S.ea_ptr[g1] > S.ea_ptr[g0]) {
+        int64_t maxf = 1;
+        for (int k = lo; k < hi; ++k) {
+          int s = S.lvl_sn[k];
+          if (S.ch_ptr[s + 1] > S.ch_ptr[s])
+            maxf = std::max<int64_t>(maxf, (S.sn_start[s + 1] - S.sn_start[s]) +
+                                               (S.rptr[s + 1] - S.rptr[s]));
+        }
+        int ey = (int)std::min<int64_t>(maxf, 64);
+        k_mf_extend_add_level<<<dim3(hi - lo, ey), 128, 0, c->stream>>>(P, lo);
+        c->stats.kernel_launches++;
       }
-      int ey = std::min(maxr, 1024);
-      k_mf_extend_add<<<dim3(ehi - elo, ey), 128, 0, c->stream>>>(P, elo, ehi);
-      c->stats.kernel_launches++;
     }
     size_t smd = 2 * (size_t)maxw * maxw * sizeof(double);
     k_mf_diag<<<hi - lo, 128, smd, c->stream>>>(P, lo, c->d_status);

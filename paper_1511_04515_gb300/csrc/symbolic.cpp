@@ -669,6 +669,12 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
   }
   // extend-add pairs grouped by (parent level, child rank)
   {
+    S.ch_ptr.assign(nsn + 1, 0);
+    S.ch_list.clear();
+    for (int s = 0; s < nsn; ++s) {
+      S.ch_list.insert(S.ch_list.end(), children[s].begin(), children[s].end());
+      S.ch_ptr[s + 1] = (int32_t)S.ch_list.size();
+    }
     int maxrank = 1;
     for (int s = 0; s < nsn; ++s) maxrank = std::max<int>(maxrank, (int)children[s].size());
     S.ea_maxrank = maxrank;

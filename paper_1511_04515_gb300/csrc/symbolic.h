@@ -78,6 +78,8 @@ struct Symbolic {
   std::vector<int32_t> ea_ptr;     // nlevels * maxrank + 1
   std::vector<int32_t> ea_child;
   int ea_maxrank = 0;
+  // children of each supernode in rank order (CSR): the per-level extend-add
+  std::vector<int32_t> ch_ptr, ch_list;
   // GEMM tile lists per level (Schur update F22 -= F21 F12)
   std::vector<int32_t> tile_ptr;   // nlevels+1
   std::vector<int32_t> tile_sn;    // per tile: supernode
