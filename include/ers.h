@@ -37,7 +37,7 @@ typedef enum {
   ERS_ERR_SINGULAR = 2,         /* zero / tiny pivot in the static-pivot LU of G_k      */
   ERS_ERR_NONFINITE = 3,        /* NaN or Inf in inputs or results                       */
   ERS_ERR_STEP_UNDERFLOW = 4,   /* adaptive h fell below h_min                           */
-  ERS_ERR_KRYLOV = 5,           /* exp(h H_m^{-1}) not finite in fixed-m mode            */
+  ERS_ERR_KRYLOV = 5,           /* exp(h H_m^{-1}) e_1 not finite at any usable dimension */
   ERS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up                    */
   ERS_ERR_CUDA = 7,             /* CUDA runtime error                                    */
   ERS_ERR_OOM = 8               /* device allocation failed                              */
@@ -84,14 +84,19 @@ typedef struct {
 } ers_opts;
 
 typedef struct {
-  int64_t steps, rejects, refactors, krylov_vectors, solves;
-  int32_t n, nsn, nlevels, etree_height, max_front;
+  int64_t steps;               /* accepted steps (a batched context: rounds)            */
+  int64_t rejects;             /* rejected tries                                         */
+  int64_t refactors;           /* LU refactors of G_k                                    */
+  int64_t krylov_vectors;      /* Arnoldi directions built (every space, every instance) */
+  int64_t solves;              /* right-hand sides through the L and U solves            */
+  int32_t n, nsn, nlevels, etree_height, max_front;   /* symbolic analysis              */
   int64_t nnz_L, factor_doubles, arena_doubles;
   double refactor_flops;
   int64_t kernel_launches;     /* kernels launched by the library so far              */
   int64_t solve_passes;        /* forward+backward solve pairs (any number of RHS)    */
   int64_t solve_rhs;           /* right-hand sides solved                              */
-  double solve_ms;             /* device time of the solve kernels (profiling on)     */
+  double solve_ms;             /* device time of the solve kernels (profiling on; solves
+                                  replayed inside CUDA graphs are not timed)           */
   double solve_bytes_per_pass; /* factor bytes one solve pair reads (values+indices)  */
   double solve_fma_per_rhs;    /* FP64 FMAs of one solve pair per right-hand side     */
   int64_t graph_launches;      /* CUDA graph launches (batched Arnoldi iterations)     */

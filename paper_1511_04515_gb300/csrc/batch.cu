@@ -984,6 +984,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   for (int i = 0; i < ninst; ++i) {
     if (nsteps) nsteps[i] = (int32_t)(c->steps_inst[i] - steps0[i]);
     if (nreject) nreject[i] = (int32_t)(c->rejects_inst[i] - rejects0[i]);
+    c->stats.rejects += c->rejects_inst[i] - rejects0[i];
   }
   return ERS_OK;
 }
