@@ -350,3 +350,46 @@ def test_ercorrection_runs_and_changes_solution():
     b = _fixed_er(circ, x0, t0, t1, 2e-12, correction=True)
     assert np.max(np.abs(a - b)) > 0
     assert np.all(np.isfinite(b))
+
+
+def _phi2_dense(A):
+    """phi_2(A) from the exponential of the block matrix [[A, I, 0], [0, 0, I], [0, 0, 0]],
+    whose top-right block is phi_2(A) (Saad 1992; Al-Mohy and Higham 2011)."""
+    n = A.shape[0]
+    Z = np.zeros((3 * n, 3 * n))
+    Z[:n, :n] = A
+    Z[:n, n:2 * n] = np.eye(n)
+    Z[n:2 * n, 2 * n:] = np.eye(n)
+    return sla.expm(Z)[:n, 2 * n:]
+
+
+@pytest.mark.parametrize("h", [0.5e-12, 2e-12])
+def test_ercorrection_equals_dense_phi2(h):
+    """ER-C (Eq. 17): x_c = x_ER - D with D = gamma h phi_2(hJ) C^{-1} dF, J = -C^{-1} G_k and
+    dF = F(x_ER) - F(x_k).  The oracle evaluates D in the form of Eq. 20, through one more
+    invert-Krylov MEVP; here phi_2 comes from a dense block exponential instead.
+
+    Tolerance: Eq. 20 adds (e^{hJ} - I) G^{-1} C G^{-1} dF and h G^{-1} dF, which cancel to
+    order (h lambda)^2 on a slow mode lambda, so the MEVP's ~1e-13 relative error grows by
+    2 / (h lambda_min)^2 (about 1e6 here at h = 0.5 ps).  1e-5 relative still fails a wrong
+    sign, a dropped term, gamma or 1/h misplaced, or phi_1 in place of phi_2 by orders of
+    magnitude."""
+    circ, x0, t0, _ = _switching_window()
+    n = circ.n
+    t = t0 + 4e-12
+    x = _fixed_er(circ, x0, t0, t, 0.25e-12)          # a state on the switching edge
+    gamma = 0.3
+    er = O.er_step(circ, x, t, h, m=n, opts=O.Options(eps=1e-14, m_max=n))
+    erc = O.er_step(circ, x, t, h, m=n,
+                    opts=O.Options(eps=1e-14, m_max=n, correction=True, gamma=gamma))
+    D = er.x - erc.x
+    lin = O.linearize(circ, x)
+    dF = lin.remainder(circ, er.x) - lin.F
+    Cd = circ.C.toarray()
+    J = -np.linalg.solve(Cd, lin.Gk.toarray())
+    ref = gamma * h * _phi2_dense(h * J) @ np.linalg.solve(Cd, dF)
+    assert np.max(np.abs(ref)) > 0
+    assert np.max(np.abs(D - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # the correction is a second-order term: far below the error estimate's h phi_1 part
+    e_rr = (sla.expm(h * J) - np.eye(n)) @ np.linalg.solve(lin.Gk.toarray(), dF)
+    assert np.max(np.abs(D)) < np.max(np.abs(e_rr))
