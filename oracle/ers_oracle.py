@@ -27,6 +27,10 @@ Readings of points the paper leaves open (all listed in the design doc's readings tab
     and the MEVP uses j - 1.  A residual that is not finite (a spurious Ritz value of J^{-1} in the
     right half-plane makes exp(h H^{-1}) overflow) counts as "not converged".
   * E_rr = tol * max(1 V, ||x_k||_inf); steps never straddle a PWL corner.
+  * Singular C (nodes without capacitance, Sec. IV-A and Sec. V): e^{h/mu} and e^{h/mu}/mu
+    are taken at their limit 0 for the eigenvalue mu = 0 of H_m and for any |mu| <= h/700
+    (exp_hinv_e1).  For a linear index-1 circuit this makes the ER step the exact solution
+    of the differential-algebraic system.
 """
 from __future__ import annotations
 
@@ -145,13 +149,43 @@ def linearize(circ, x) -> Linearization:
 # ----------------------------------------------------------------------------------------
 # Small dense matrix functions (Sec. IV, Eq. 14 and the residual of Eq. 16).
 # ----------------------------------------------------------------------------------------
+ALGEBRAIC_EXPONENT = 700.0   # e^{-700} ~ 1e-304: below it e^{h/mu} is zero in FP64
+
+
 def exp_hinv_e1(Hm, h):
-    """exp(h H_m^{-1}) e_1 and e_m^T H_m^{-1} exp(h H_m^{-1}) e_1 (Eq. 14 and Eq. 16)."""
+    """exp(h H_m^{-1}) e_1 and e_m^T H_m^{-1} exp(h H_m^{-1}) e_1 (Eq. 14 and Eq. 16).
+
+    Both are functions of H_m: f(mu) = e^{h/mu} and g(mu) = e^{h/mu} / mu.  The paper keeps
+    C out of every factorisation so that a singular C needs no regularisation (Sec. IV-A);
+    then J^{-1} = -G^{-1} C has the eigenvalue 0 on ker C (nodes without capacitance), and
+    f, g are taken at their limit 0 from the stable side (such modes relax instantly).  The
+    same limit is used for every eigenvalue with |mu| <= h / 700: a real stiff mode there has
+    e^{h/mu} below 1e-304 anyway, and a tiny eigenvalue of either sign is the rounding image of
+    a zero one.  Those eigenvalues are split off by an ordered Schur form H = Z T Z^*, where
+    f(T) = [[f(T11), F12], [0, 0]] and F12 solves T11 F12 - F12 T22 = f(T11) T12 (from
+    T f(T) = f(T) T); same for g.  Without such eigenvalues this is the plain dense
+    exponential of h H_m^{-1}."""
     m = Hm.shape[0]
-    Hinv = np.linalg.solve(Hm, np.eye(m))
-    E = sla.expm(h * Hinv)
-    y = E[:, 0].copy()
-    return y, float((Hinv @ y)[m - 1])
+    tau = h / ALGEBRAIC_EXPONENT
+    if np.all(np.abs(np.linalg.eigvals(Hm)) > tau):
+        Hinv = np.linalg.solve(Hm, np.eye(m))
+        E = sla.expm(h * Hinv)
+        y = E[:, 0].copy()
+        return y, float((Hinv @ y)[m - 1])
+    T, Z, s = sla.schur(Hm.astype(complex), output="complex", sort=lambda mu: abs(mu) > tau)
+    if s == 0:
+        return np.zeros(m), 0.0
+    T11, T12, T22 = T[:s, :s], T[:s, s:], T[s:, s:]
+    T11inv = np.linalg.solve(T11, np.eye(s))
+    fT = np.zeros((m, m), complex)
+    gT = np.zeros((m, m), complex)
+    fT[:s, :s] = sla.expm(h * T11inv)
+    gT[:s, :s] = T11inv @ fT[:s, :s]
+    fT[:s, s:] = sla.solve_sylvester(T11, -T22, fT[:s, :s] @ T12)
+    gT[:s, s:] = sla.solve_sylvester(T11, -T22, gT[:s, :s] @ T12)
+    z1 = Z.conj().T[:, 0]                       # Z^* e_1
+    y = (Z @ (fT @ z1)).real
+    return y, float((Z @ (gT @ z1))[m - 1].real)
 
 
 # ----------------------------------------------------------------------------------------

@@ -265,9 +265,11 @@ def inverter_chain(stages=2000, tree_nodes=100, seed=2, vdd=1.0, gmin=1e-12,
                    meta=dict(kind="invchain", stages=stages, tree_nodes=tree_nodes, seed=seed))
 
 
-def random_rc(n=16, seed=0, density=0.3, p=2, t_end=50e-12):
-    """Small dense-ish random RC network (every node has a ground cap and a path to ground),
-    used to pin the oracle against a dense matrix exponential."""
+def random_rc(n=16, seed=0, density=0.3, p=2, t_end=50e-12, n_alg=0, alg_source=False):
+    """Small dense-ish random RC network (every node has a path to ground), used to pin the
+    oracle against a dense matrix exponential.  Every node has a ground cap unless n_alg > 0:
+    then n_alg nodes (one of them a source node when alg_source) have no capacitance at all,
+    which makes C singular (algebraic nodes of a differential-algebraic system)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     rows, cols, vals = [], [], []
     # spanning chain keeps the network connected, extra random edges add coupling
@@ -288,8 +290,18 @@ def random_rc(n=16, seed=0, density=0.3, p=2, t_end=50e-12):
     B = _csr(nodes, np.arange(p), np.ones(p), n, p)
     pwl = [pulse_pwl(float(rng.integers(0, 5)) * 1e-12, 5e-12, 10e-12, 5e-12, 1e-3, t_end)
            for _ in range(p)]
+    alg = np.zeros(0, np.int64)
+    if n_alg:
+        arng = np.random.Generator(np.random.PCG64(seed + 104729))
+        pool = np.setdiff1d(np.arange(n), nodes)
+        alg = arng.choice(pool, size=n_alg - int(alg_source), replace=False)
+        if alg_source:
+            alg = np.concatenate([alg, nodes[:1]])
+        alg = np.sort(alg)
+        keep = np.setdiff1d(np.arange(n), alg)
+        C = _csr(keep, keep, C.diagonal()[keep], n, n)
     return Circuit(name=f"randrc_{n}", n=n, G=G, C=C, B=B, dev=np.zeros(0, DEVICE_DTYPE),
-                   pwl=pwl, t_end=t_end, meta=dict(kind="randrc", seed=seed))
+                   pwl=pwl, t_end=t_end, meta=dict(kind="randrc", seed=seed, algebraic=alg))
 
 
 def single_rc(g=1e-3, c=1e-15, i_amp=1e-3, ramp=None, t_end=10e-12):

@@ -426,3 +426,115 @@ def test_rc_mesh_32x32_converges_to_exact_solution():
         errs.append(err)
     assert errs[0] <= 1e-5 and errs[1] <= 1e-6, errs
     assert errs[1] <= errs[0] / 10, errs
+
+
+# --- Singular C (nodes without capacitance; Sec. IV-A, Sec. V) ---------------------------
+def kron_exact_step(circ, x, t, h):
+    """Exact solution over [t, t+h] of C x' = -G x + B u(t) with singular diagonal C and u
+    linear on the step.  The algebraic nodes a (no capacitance) obey G_a x = (B u)_a at every
+    instant; eliminating them (Kron reduction) leaves the ODE
+        C_dd x_d' = -(G_dd - G_da G_aa^{-1} G_ad) x_d + (B_d - G_da G_aa^{-1} B_a) u(t),
+    solved by the generalized eigenproblem; x_a follows from the constraint at t + h.  Only
+    x_d of the initial state matters (an inconsistent x_a is forgotten)."""
+    alg = circ.meta["algebraic"]
+    dyn = np.setdiff1d(np.arange(circ.n), alg)
+    G = circ.G.toarray(); C = circ.C.toarray(); B = circ.B.toarray()
+    Gdd, Gda = G[np.ix_(dyn, dyn)], G[np.ix_(dyn, alg)]
+    Gad, Gaa = G[np.ix_(alg, dyn)], G[np.ix_(alg, alg)]
+    Gr = Gdd - Gda @ np.linalg.solve(Gaa, Gad)
+    Br = B[dyn] - Gda @ np.linalg.solve(Gaa, B[alg])
+    Cr = C[np.ix_(dyn, dyn)]
+    lam, Q = sla.eigh(Gr, Cr)
+    uk = circ.u(t); s = (circ.u(t + h) - uk) / h
+    y0 = Q.T @ Cr @ x[dyn]
+    f = Q.T @ Br @ uk; g = Q.T @ Br @ s
+    e = np.exp(-lam * h)
+    xd = Q @ (e * y0 + f * (1 - e) / lam + g * (h / lam - (1 - e) / lam ** 2))
+    out = np.empty(circ.n)
+    out[dyn] = xd
+    out[alg] = np.linalg.solve(Gaa, B[alg] @ circ.u(t + h) - Gad @ xd)
+    return out
+
+
+def _linear_pieces(circ, h_max):
+    bps = sorted(set([0.0] + [b for b in circ.breakpoints() if b < circ.t_end] + [circ.t_end]))
+    for a, b in zip(bps[:-1], bps[1:]):
+        k = max(1, int(np.ceil((b - a) / h_max - 1e-9)))
+        for i in range(k):
+            yield a + (b - a) * i / k, (b - a) / k
+
+
+@pytest.mark.parametrize("seed,alg_source", [(0, False), (1, True), (2, False)])
+def test_singular_c_step_equals_kron_reduced_solution(seed, alg_source):
+    """ER step (Eq. 13) with a full invert-Krylov space on a circuit with four capacitor-free
+    nodes, from an inconsistent random state, against the exact solution of the
+    differential-algebraic system."""
+    circ = S.random_rc(n=14, seed=seed, p=3, n_alg=4, alg_source=alg_source, t_end=30e-12)
+    assert circ.C.diagonal()[circ.meta["algebraic"]].tolist() == [0.0] * 4
+    x = np.random.default_rng(seed).normal(size=circ.n) * 0.1
+    for t, h in [(0.0, 1e-12), (6e-12, 1e-12), (9e-12, 3e-12)]:
+        nb = circ.breakpoints()
+        nb = nb[nb > t + 1e-18]
+        h = min(h, nb[0] - t) if nb.size else h
+        r = O.er_step(circ, x, t, h, m=circ.n)
+        ex = kron_exact_step(circ, x, t, h)
+        assert np.max(np.abs(r.x - ex)) <= 1e-10 * np.max(np.abs(ex)), (t, h)
+
+
+def test_singular_c_trajectory_and_constraints():
+    """A trajectory through every source corner with the adaptive Krylov dimension (Eq.-16
+    test), from an inconsistent state: it follows the exact solution, and the capacitor-free
+    rows of KCL, (G x)_a = (B u)_a, hold from the first step on.  (A consistent state has
+    G v_1 in the range of C, so only the first step meets the eigenvalue 0.)"""
+    circ = S.random_rc(n=16, seed=5, p=3, n_alg=5, alg_source=True, t_end=30e-12)
+    alg = circ.meta["algebraic"]
+    G = circ.G.toarray(); B = circ.B.toarray()
+    x = np.random.default_rng(5).normal(size=circ.n) * 0.1
+    xe = x.copy()
+    opts = O.Options(eps=1e-12, m_max=circ.n)
+    for t, h in _linear_pieces(circ, 2e-12):
+        x = O.er_step(circ, x, t, h, m=0, opts=opts).x
+        xe = kron_exact_step(circ, xe, t, h)
+        scale = np.max(np.abs(xe))
+        assert np.max(np.abs(x - xe)) <= 1e-8 * scale, t
+        kcl = (G @ x)[alg] - (B @ circ.u(t + h))[alg]
+        assert np.max(np.abs(kcl)) <= 1e-10 * np.max(np.abs(G)) * scale, t
+
+
+def _planted_hessenberg(mus, seed):
+    """Upper Hessenberg H = P^T Q D Q^{-1} P (P orthogonal, from a Hessenberg reduction) with
+    the eigenvalues mus, and f(H) e_1 = (P^T Q) f(D) (P^T Q)^{-1} e_1 for f(mu) = e^{h/mu}
+    and g(mu) = e^{h/mu} / mu evaluated in 50-digit arithmetic from that eigendecomposition,
+    with f(0) = g(0) = 0 (the limit from the stable side)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    m = len(mus)
+    rng = np.random.default_rng(seed)
+    Q = rng.normal(size=(m, m)) + 3 * np.eye(m)
+    H, P = sla.hessenberg(Q @ np.diag(mus) @ np.linalg.inv(Q), calc_q=True)
+    Qm = mp.matrix((P.T @ Q).tolist())
+    Qi_e1 = Qm ** -1 * mp.matrix([1] + [0] * (m - 1))
+
+    def apply(fun):
+        d = [fun(mp.mpf(v)) if v != 0 else mp.mpf(0) for v in mus]
+        return Qm * mp.matrix([d[i] * Qi_e1[i] for i in range(m)])
+    return H, apply, mp
+
+
+@pytest.mark.parametrize("case", ["stiff", "zero", "zero_pair"])
+def test_exp_hinv_e1_with_tiny_and_zero_eigenvalues(case):
+    """exp(h H^{-1}) e_1 and e_m^T H^{-1} exp(h H^{-1}) e_1 against a 50-digit evaluation
+    from the eigendecomposition when H has eigenvalues at or near zero (stiff modes, and the
+    exact zeros of a singular C)."""
+    h = 1e-12
+    base = [-3e-12, -1e-12, -5e-13, -2e-13, -8e-14, -3e-14]
+    extra = {"stiff": [-h / 2000, -h / 1e6], "zero": [0.0], "zero_pair": [0.0, 0.0]}[case]
+    H, apply, mp = _planted_hessenberg(base + extra, seed=len(extra))
+    m = H.shape[0]
+    ref_y = np.array([float(v) for v in apply(lambda mu: mp.exp(h / mu))])
+    ref_g = np.array([float(v) for v in apply(lambda mu: mp.exp(h / mu) / mu)])
+    y, last = O.exp_hinv_e1(H, h)
+    # H itself is rounded (~1e-16 ||H|| cond(Q)); both bars leave room for that, and a
+    # wrong limit at mu = 0 or a lost coupling block misses them by orders of magnitude
+    assert np.max(np.abs(y - ref_y)) <= 1e-12 * np.max(np.abs(ref_y)), case
+    assert abs(last - ref_g[m - 1]) <= 1e-12 * np.max(np.abs(ref_g)), case
