@@ -29,7 +29,7 @@ Readings of points the paper leaves open (all listed in the design doc's readings tab
   * E_rr = tol * max(1 V, ||x_k||_inf); steps never straddle a PWL corner.
   * Singular C (nodes without capacitance, Sec. IV-A and Sec. V): e^{h/mu} and e^{h/mu}/mu
     are taken at their limit 0 for the eigenvalue mu = 0 of H_m and for any |mu| <= h/700
-    (exp_hinv_e1).  For a linear index-1 circuit this makes the ER step the exact solution
+    (exp_hinv_e1); circuits whose C has no zero row keep the plain exponential.  For a linear index-1 circuit this makes the ER step the exact solution
     of the differential-algebraic system.
 """
 from __future__ import annotations
@@ -152,22 +152,22 @@ def linearize(circ, x) -> Linearization:
 ALGEBRAIC_EXPONENT = 700.0   # e^{-700} ~ 1e-304: below it e^{h/mu} is zero in FP64
 
 
-def exp_hinv_e1(Hm, h):
+def exp_hinv_e1(Hm, h, singular_c=False):
     """exp(h H_m^{-1}) e_1 and e_m^T H_m^{-1} exp(h H_m^{-1}) e_1 (Eq. 14 and Eq. 16).
 
-    Both are functions of H_m: f(mu) = e^{h/mu} and g(mu) = e^{h/mu} / mu.  The paper keeps
-    C out of every factorisation so that a singular C needs no regularisation (Sec. IV-A);
-    then J^{-1} = -G^{-1} C has the eigenvalue 0 on ker C (nodes without capacitance), and
-    f, g are taken at their limit 0 from the stable side (such modes relax instantly).  The
-    same limit is used for every eigenvalue with |mu| <= h / 700: a real stiff mode there has
-    e^{h/mu} below 1e-304 anyway, and a tiny eigenvalue of either sign is the rounding image of
-    a zero one.  Those eigenvalues are split off by an ordered Schur form H = Z T Z^*, where
-    f(T) = [[f(T11), F12], [0, 0]] and F12 solves T11 F12 - F12 T22 = f(T11) T12 (from
-    T f(T) = f(T) T); same for g.  Without such eigenvalues this is the plain dense
-    exponential of h H_m^{-1}."""
+    Both are functions of H_m: f(mu) = e^{h/mu} and g(mu) = e^{h/mu} / mu; for a C without
+    zero rows they are the plain dense exponential of h H_m^{-1}.  The paper keeps C out of
+    every factorisation so that a singular C needs no regularisation (Sec. IV-A); with
+    singular_c (C has nodes without capacitance) J^{-1} = -G^{-1} C has the eigenvalue 0 on
+    ker C, and f, g are taken at their limit 0 from the stable side (such modes relax
+    instantly).  The same limit is used for every eigenvalue with |mu| <= h / 700: a real
+    stiff mode there has e^{h/mu} below 1e-304 anyway, and a tiny eigenvalue of either sign is
+    the rounding image of a zero one.  Those eigenvalues are split off by an ordered Schur
+    form H = Z T Z^*, where f(T) = [[f(T11), F12], [0, 0]] and F12 solves
+    T11 F12 - F12 T22 = f(T11) T12 (from T f(T) = f(T) T); same for g."""
     m = Hm.shape[0]
     tau = h / ALGEBRAIC_EXPONENT
-    if np.all(np.abs(np.linalg.eigvals(Hm)) > tau):
+    if not singular_c or np.all(np.abs(np.linalg.eigvals(Hm)) > tau):
         Hinv = np.linalg.solve(Hm, np.eye(m))
         E = sla.expm(h * Hinv)
         y = E[:, 0].copy()
@@ -188,6 +188,12 @@ def exp_hinv_e1(Hm, h):
     return y, float((Z @ (gT @ z1))[m - 1].real)
 
 
+def has_capacitor_free_node(C):
+    """True when some node has no capacitance at all (a zero row of C), i.e. the circuit is
+    differential-algebraic and J^{-1} = -G^{-1} C has the eigenvalue 0."""
+    return bool(np.any(abs(sp.csr_matrix(C)).sum(axis=1) == 0))
+
+
 # ----------------------------------------------------------------------------------------
 # MEVP_IKS (Algorithm 1).
 # ----------------------------------------------------------------------------------------
@@ -203,13 +209,14 @@ class KrylovBasis:
     breakdown: bool = False
     gv_norm: float = 0.0           # ||G v_1||_2 (scale of the relative residual test)
     gvnext_norm: List[float] = field(default_factory=list)  # ||G v_{j+1}||_2 per j
+    singular_c: bool = False       # C has nodes without capacitance (see exp_hinv_e1)
 
     def residual(self, j, h):
         """||r_j(h)||_2 / (beta ||G v_1||) from Eq. 16 with e^T = e_j^T."""
         if self.breakdown and j == self.built:
             return 0.0
         with np.errstate(all="ignore"):
-            _, last = exp_hinv_e1(self.H[:j, :j], h)
+            _, last = exp_hinv_e1(self.H[:j, :j], h, self.singular_c)
         return self.H[j, j - 1] * self.gvnext_norm[j - 1] * abs(last) / self.gv_norm
 
     def mevp(self, h, m=None):
@@ -217,7 +224,7 @@ class KrylovBasis:
         m = self.m if m is None else m
         if self.beta == 0.0:
             return np.zeros(self.V.shape[0])
-        y, _ = exp_hinv_e1(self.H[:m, :m], h)
+        y, _ = exp_hinv_e1(self.H[:m, :m], h, self.singular_c)
         return self.beta * (self.V[:, :m] @ y)
 
 
@@ -231,6 +238,7 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
     If no tested dimension had a finite residual, it uses the largest dimension whose
     exp(h H^{-1}) e_1 is finite."""
     n = v.shape[0]
+    sing = has_capacitor_free_node(C)
     beta = float(np.linalg.norm(v))
     mc = fixed_m if fixed_m > 0 else m_max
     V = np.zeros((n, mc + 1))
@@ -239,7 +247,7 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
         return KrylovBasis(beta=0.0, V=V[:, :1], H=H[:1, :0], m=0, built=0)
     V[:, 0] = v / beta
     basis = KrylovBasis(beta=beta, V=V, H=H, m=mc, built=0,
-                        gv_norm=float(np.linalg.norm(G @ V[:, 0])))
+                        gv_norm=float(np.linalg.norm(G @ V[:, 0])), singular_c=sing)
     best_j, best_res = mc, np.inf
     for j in range(mc):
         w = -lin.solve(C @ V[:, j])                 # solve -G w = C v_j
@@ -254,7 +262,7 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
             basis.m = j + 1
             basis.gvnext_norm.append(0.0)
             with np.errstate(all="ignore"):
-                y, _ = exp_hinv_e1(H[:j + 1, :j + 1], h)
+                y, _ = exp_hinv_e1(H[:j + 1, :j + 1], h, sing)
             if j > 0 and not np.all(np.isfinite(y)):
                 # v_{j+1} was rounding noise (its Ritz value sits at ~+0): drop it
                 basis.m = j
@@ -276,7 +284,7 @@ def arnoldi_iks(C, lin, G, v, h, eps, m_max, m_min=1, fixed_m=0):
                 # exp(h H^{-1}) e_1 is finite
                 with np.errstate(all="ignore"):
                     while basis.m > 1 and not np.all(np.isfinite(
-                            exp_hinv_e1(H[:basis.m, :basis.m], h)[0])):
+                            exp_hinv_e1(H[:basis.m, :basis.m], h, sing)[0])):
                         basis.m -= 1
     basis.V = V[:, :basis.built + 1]
     basis.H = H[:basis.built + 1, :basis.built]

@@ -533,7 +533,7 @@ def test_exp_hinv_e1_with_tiny_and_zero_eigenvalues(case):
     m = H.shape[0]
     ref_y = np.array([float(v) for v in apply(lambda mu: mp.exp(h / mu))])
     ref_g = np.array([float(v) for v in apply(lambda mu: mp.exp(h / mu) / mu)])
-    y, last = O.exp_hinv_e1(H, h)
+    y, last = O.exp_hinv_e1(H, h, singular_c=True)
     # H itself is rounded (~1e-16 ||H|| cond(Q)); both bars leave room for that, and a
     # wrong limit at mu = 0 or a lost coupling block misses them by orders of magnitude
     assert np.max(np.abs(y - ref_y)) <= 1e-12 * np.max(np.abs(ref_y)), case
