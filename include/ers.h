@@ -120,7 +120,10 @@ ers_status ers_default_opts(ers_opts* opts);
  * matrices).  G_lin, C: n x n; B: n x p; dev: ndev MOSFETs (may be NULL if ndev = 0);
  * u: p PWL inputs.  Performs the one-time symbolic analysis of G_k's pattern (the union of
  * G_lin and the device stamps) and allocates device memory.  The state starts at t = 0,
- * x = 0; call ers_dc for the DC operating point.  opts may be NULL (defaults). */
+ * x = 0; call ers_dc for the DC operating point.  opts may be NULL (defaults).
+ * Every node needs a capacitance (a nonzero entry in its row of C): a node without one
+ * makes C singular and H_m of Eq. 14 singular with it, which the small dense stage does not
+ * handle; such a C is refused with ERS_ERR_INVALID before any device work. */
 ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, const ers_csr* B,
                       const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
                       const ers_opts* opts);

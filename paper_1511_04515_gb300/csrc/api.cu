@@ -501,6 +501,14 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   std::string m;
   if (!(m = check_csr(G, n, n, "G_lin")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
   if (!(m = check_csr(C, n, n, "C")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
+  for (int i = 0; i < n; ++i) {
+    bool cap = false;
+    for (int e = C->rowptr[i]; e < C->rowptr[i + 1]; ++e) cap = cap || C->val[e] != 0.0;
+    if (!cap)
+      return bail(fail(c, ERS_ERR_INVALID,
+                       "C row " + std::to_string(i) + " is zero: a node without capacitance "
+                       "makes C singular, which the small dense MEVP stage does not support"));
+  }
   if (p < 0) return bail(fail(c, ERS_ERR_INVALID, "p must be >= 0"));
   if (!(m = check_csr(B, n, p, "B")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
   if (ndev < 0 || (ndev > 0 && !dev)) return bail(fail(c, ERS_ERR_INVALID, "bad device list"));
