@@ -35,6 +35,8 @@ FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32
 # times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
 # k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
 SOLVE_TRAFFIC_RATIO = 2.6626 / 2.5525
+L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
+FLUSH_BYTES = 256 * 2 ** 20
 SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same generator
 SAMPLE_STEPS = 10
 
@@ -247,18 +249,43 @@ def run_ours(a):
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     proc, fh = clocks_start(local, clk_path)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    factor_bytes = st0["factor_doubles"] * 8
     torch.cuda.nvtx.range_push("ers_timed")
-    e0.record(stream)
-    ns, nr = sim.run(t_end, a.tol, max_steps=a.steps)
-    e1.record(stream)
+    if factor_bytes > L2_BYTES:
+        # the factor streams from HBM on every solve: steps run back to back
+        l2_note = "inputs larger than L2 (factor values alone exceed 129 MB)"
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns, nr = sim.run(t_end, a.tol, max_steps=a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    else:
+        # the factor fits in L2: write 256 MB on the library's stream before every step and
+        # time each step with its own events, so no step starts from the previous one's cache
+        l2_note = (f"L2 flushed before every step ({FLUSH_BYTES >> 20} MB write on the "
+                   f"library's stream, outside the per-step events): the factor is "
+                   f"{factor_bytes / 1e6:.1f} MB")
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
+        ns = nr = 0
+        for k in range(a.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+            evs[k][0].record(stream)
+            s_k, r_k = sim.run(t_end, a.tol, max_steps=1)
+            evs[k][1].record(stream)
+            ns += s_k
+            nr += r_k
+        torch.cuda.synchronize()
+        ms = sum(b.elapsed_time(c) for b, c in evs)
+        del flush
     torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = clocks_stop(proc, fh, clk_path)
-    ms = e0.elapsed_time(e1)
     st1 = sim.stats()
     steps = st1["steps"] - st0["steps"]
     kvec = st1["krylov_vectors"] - st0["krylov_vectors"]
@@ -327,7 +354,7 @@ def run_ours(a):
                        "nnz_G": int(circ.G.nnz), "devices": int(len(circ.dev)),
                        "loads": int(circ.p), "nnz_L": int(st1["nnz_L"]),
                        "factor_GB": st1["factor_doubles"] * 8 / 1e9,
-                       "l2_flush": "inputs larger than L2 (factor values alone exceed 129 MB)",
+                       "l2_flush": l2_note,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "create_s": create_s, "factor_and_dc_s": factor_s,
                        "solve_ctas_per_sm": tuned,
