@@ -81,6 +81,10 @@ typedef struct {
   int32_t m_max;       /* Algorithm 1's m_c (default 40, at most 64)                              */
   int32_t combined_vector; /* 1: one Krylov space on v1 + v2 instead of two (default 0)           */
   int32_t correction;  /* 1: ER-C (Eq. 20), 0: ER (default 0)                                      */
+  int32_t ordering;    /* fill-reducing ordering of G_k's pattern (default 0):
+                          0: nested dissection, separator = the BFS level at the median;
+                          1: the smallest BFS level leaving >= 35% of the part on each side,
+                             from either end of the pseudo-diameter (less fill on meshes) */
 } ers_opts;
 
 typedef struct {
@@ -360,8 +364,9 @@ ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, 
  * an earlier entry of its list (the property that makes the persistent solves deadlock-free).
  * counts (8 values, may be NULL): forward and backward CTA entries, lane items (fwd, bwd),
  * warp-task supernodes (fwd, bwd), DIAG entries (fwd, bwd).  ERS_ERR_INVALID with a
- * violated property (or a malformed pattern). */
-ers_status ers_solve_plan_check(const ers_csr* pattern, int64_t* counts);
+ * violated property (or a malformed pattern).  opts (may be NULL: defaults) selects the
+ * ordering, as in ers_create. */
+ers_status ers_solve_plan_check(const ers_csr* pattern, const ers_opts* opts, int64_t* counts);
 
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
@@ -372,8 +377,10 @@ ers_status ers_profile(ers_ctx* ctx, int32_t enable);
 /* Host-only symbolic analysis of an n x n pattern (no GPU needed): fills the fields of
  * out that describe the ordering and factor (n, nsn, nlevels, etree_height, max_front,
  * nnz_L, factor_doubles, arena_doubles, refactor_flops).  perm (may be NULL) receives the
- * fill-reducing permutation new -> old. */
-ers_status ers_analyze(const ers_csr* pattern, ers_stats_t* out, int32_t* perm);
+ * fill-reducing permutation new -> old.  opts (may be NULL: defaults) selects the ordering,
+ * as in ers_create. */
+ers_status ers_analyze(const ers_csr* pattern, const ers_opts* opts, ers_stats_t* out,
+                       int32_t* perm);
 
 const char* ers_last_error(const ers_ctx* ctx);
 void ers_destroy(ers_ctx* ctx);

@@ -445,7 +445,18 @@ ers_status ers_default_opts(ers_opts* o) {
   o->m_max = 40;
   o->combined_vector = 0;
   o->correction = 0;
+  o->ordering = 0;
   return ERS_OK;
+}
+
+// The symbolic-analysis settings an ers_opts selects (NULL: defaults).
+static SymbolicOptions symbolic_options(const ers_opts* o) {
+  SymbolicOptions so;
+  if (o && o->ordering == 1) {
+    so.sep_window_pct = 15;
+    so.sep_roots = 2;
+  }
+  return so;
 }
 
 const char* ers_last_error(const ers_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -529,6 +540,8 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   if (c->opts.m_max < 1 || c->opts.m_max > MAX_M)
     return bail(fail(c, ERS_ERR_INVALID, "m_max must be in 1..64"));
   if (c->opts.m_min < 1) c->opts.m_min = 1;
+  if (c->opts.ordering != 0 && c->opts.ordering != 1)
+    return bail(fail(c, ERS_ERR_INVALID, "ordering must be 0 or 1"));
   c->n = n;
   c->p = p;
   c->ndev = ndev;
@@ -539,7 +552,7 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   std::vector<double> uval;
   ers_status st = build_union(c, G, dev, ndev, uptr, uidx, uval);
   if (st != ERS_OK) return bail(st);
-  SymbolicOptions so;
+  SymbolicOptions so = symbolic_options(&c->opts);
   std::string err = analyze(n, uptr.data(), uidx.data(), so, c->sym);
   if (!err.empty()) return bail(fail(c, ERS_ERR_INVALID, "symbolic analysis: " + err));
   const Symbolic& S = c->sym;
@@ -1171,11 +1184,13 @@ ers_status ers_profile(ers_ctx* c, int32_t enable) {
   return ERS_OK;
 }
 
-ers_status ers_analyze(const ers_csr* pat, ers_stats_t* out, int32_t* perm) {
+ers_status ers_analyze(const ers_csr* pat, const ers_opts* opts, ers_stats_t* out,
+                       int32_t* perm) {
   if (!pat || !out) return ERS_ERR_INVALID;
   if (pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
+  if (opts && opts->ordering != 0 && opts->ordering != 1) return ERS_ERR_INVALID;
   Symbolic S;
-  SymbolicOptions so;
+  SymbolicOptions so = symbolic_options(opts);
   std::string err = analyze(pat->n_rows, pat->rowptr, pat->colidx, so, S);
   if (!err.empty()) return ERS_ERR_INVALID;
   std::memset(out, 0, sizeof(*out));
@@ -1192,10 +1207,11 @@ ers_status ers_analyze(const ers_csr* pat, ers_stats_t* out, int32_t* perm) {
   return ERS_OK;
 }
 
-ers_status ers_solve_plan_check(const ers_csr* pat, int64_t* counts) {
+ers_status ers_solve_plan_check(const ers_csr* pat, const ers_opts* opts, int64_t* counts) {
   if (!pat || pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
+  if (opts && opts->ordering != 0 && opts->ordering != 1) return ERS_ERR_INVALID;
   Symbolic S;
-  SymbolicOptions so;
+  SymbolicOptions so = symbolic_options(opts);
   if (!analyze(pat->n_rows, pat->rowptr, pat->colidx, so, S).empty()) return ERS_ERR_INVALID;
   int64_t c[8];
   std::string err = check_solve_plan(S, c);

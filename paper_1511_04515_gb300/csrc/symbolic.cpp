@@ -63,8 +63,9 @@ Graph symmetrize(int n, const int32_t* ptr, const int32_t* idx) {
 // ---- nested dissection --------------------------------------------------------------
 class Dissector {
  public:
-  Dissector(const Graph& g, int leaf) : g_(g), leaf_(leaf), mark_(g.n, -1), lev_(g.n, -1),
-                                         loc_(g.n, -1) {}
+  Dissector(const Graph& g, int leaf, int window_pct, int roots)
+      : g_(g), leaf_(leaf), window_pct_(window_pct), roots_(roots), mark_(g.n, -1),
+        lev_(g.n, -1), loc_(g.n, -1) {}
 
   // returns new -> old
   std::vector<int32_t> run() {
@@ -83,7 +84,7 @@ class Dissector {
 
  private:
   const Graph& g_;
-  int leaf_;
+  int leaf_, window_pct_, roots_;
   std::vector<int32_t> buf_, mark_, lev_, loc_;
   int stamp_ = 0;
   std::vector<int32_t> queue_, tmp_;
@@ -173,6 +174,26 @@ class Dissector {
     for (int k = lo; k < hi; ++k) buf_[k] = dv[k - lo].second;
   }
 
+  // Separator level of a BFS level structure with cnt[l] vertices on level l: the level where
+  // the cumulative count crosses half, or (window_pct_ > 0) the smallest level that leaves at
+  // least (50 - window_pct_)% of the part on each side (ties: the first).
+  int separator_level(const std::vector<int>& cnt, int size) const {
+    int nlev = (int)cnt.size();
+    int k = 1, acc = cnt[0];
+    while (k < nlev - 1 && acc + cnt[k] <= size / 2) { acc += cnt[k]; ++k; }
+    if (k >= nlev - 1) k = nlev - 2;
+    if (window_pct_ <= 0) return k;
+    int best = -1;
+    int64_t below = cnt[0];
+    const int64_t need = (int64_t)(50 - window_pct_) * size;
+    for (int j = 1; j < nlev - 1; ++j) {
+      int64_t above = size - below - cnt[j];
+      if (100 * below >= need && 100 * above >= need && (best < 0 || cnt[j] < cnt[best])) best = j;
+      below += cnt[j];
+    }
+    return best >= 0 ? best : k;
+  }
+
   void split(int lo, int hi, std::vector<std::pair<int, int>>& stack) {
     int size = hi - lo;
     stamp_range(lo, hi);
@@ -232,12 +253,25 @@ class Dissector {
       if (size <= 64) min_degree(lo, hi); else by_degree(lo, hi);
       return;
     }
-    // separator level: where the cumulative count crosses half
     std::vector<int> cnt(nlev, 0);
     for (int v : queue_) cnt[lev_[v]]++;
-    int k = 1, acc = cnt[0];
-    while (k < nlev - 1 && acc + cnt[k] <= size / 2) { acc += cnt[k]; ++k; }
-    if (k >= nlev - 1) k = nlev - 2;
+    int k = separator_level(cnt, size);
+    if (roots_ > 1) {
+      // the same choice on the level structure from the other end; keep the smaller level
+      int f2;
+      unvisit();
+      int nl2 = bfs(far, f2);
+      std::vector<int> cnt2(nl2, 0);
+      for (int v : queue_) cnt2[lev_[v]]++;
+      int k2 = nl2 >= 3 ? separator_level(cnt2, size) : -1;
+      if (k2 >= 0 && cnt2[k2] < cnt[k]) {
+        k = k2;
+        nlev = nl2;
+      } else {
+        unvisit();
+        nlev = bfs(root, far);
+      }
+    }
     // classify: 0 = A (lev < k), 1 = B (lev > k), 2 = S
     tmp_.clear();
     std::vector<int32_t> A, B, S;
@@ -287,7 +321,7 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
   Graph g = symmetrize(n, ptr, idx);
 
   // 1. ordering
-  Dissector nd(g, std::min(opt.leaf_size, 64));
+  Dissector nd(g, std::min(opt.leaf_size, 64), opt.sep_window_pct, opt.sep_roots);
   std::vector<int32_t> perm = nd.run();
   std::vector<int32_t> iperm(n);
   for (int k = 0; k < n; ++k) iperm[perm[k]] = k;

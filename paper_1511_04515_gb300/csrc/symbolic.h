@@ -12,6 +12,10 @@ namespace ers {
 
 struct SymbolicOptions {
   int leaf_size = 32;        // nested-dissection parts at or below this size get minimum degree
+  int sep_window_pct = 0;    // 0: separator = the BFS level at the median; w > 0: the smallest
+                             // level leaving at least (50 - w)% of the part on each side
+  int sep_roots = 1;         // 2: also try the BFS from the other end of the pseudo-diameter
+                             // and keep the smaller separator
   int max_width = 64;        // supernode width cap (columns)
   int relax_zeros = 20;      // relaxed amalgamation: max % explicit zeros (0 = fundamental only)
   int relax_width = 16;      // merged supernodes up to this width are accepted regardless

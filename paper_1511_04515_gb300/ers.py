@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("beta", C.c_double), ("gamma", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("h_init", C.c_double), ("vdd", C.c_double),
                 ("i_grow", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32),
-                ("combined_vector", C.c_int32), ("correction", C.c_int32)]
+                ("combined_vector", C.c_int32), ("correction", C.c_int32),
+                ("ordering", C.c_int32)]
 
 
 class Instance(C.Structure):
@@ -134,8 +135,9 @@ def lib():
         "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, C.POINTER(Opts)], C.c_int),
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
-        "ers_analyze": ([C.POINTER(Csr), C.POINTER(Stats), pi], C.c_int),
-        "ers_solve_plan_check": ([C.POINTER(Csr), C.POINTER(C.c_int64)], C.c_int),
+        "ers_analyze": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(Stats), pi], C.c_int),
+        "ers_solve_plan_check": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(C.c_int64)],
+                                 C.c_int),
         "ers_ctrl_features": ([C.POINTER(StepRecord), I32, pf], C.c_int),
         "ers_ctrl_target": ([C.POINTER(StepRecord), I32, C.POINTER(StepRecord), pf], C.c_int),
         "ers_ctrl_propose": ([pf, C.POINTER(StepRecord), D, I32, pd, pi], C.c_int),
@@ -331,13 +333,15 @@ def make_opts(**kw) -> Opts:
     return o
 
 
-def analyze(pattern) -> dict:
-    """Host-only symbolic analysis of a square CSR pattern (no GPU needed)."""
+def analyze(pattern, ordering: int = 0) -> dict:
+    """Host-only symbolic analysis of a square CSR pattern (no GPU needed); ordering as the
+    field of ers_opts."""
     h = _CsrHold(pattern)
     st = Stats()
     n = pattern.shape[0]
     perm = np.zeros(n, np.int32)
-    rc = lib().ers_analyze(C.byref(h.c), C.byref(st), _iptr(perm))
+    o = make_opts(ordering=ordering)
+    rc = lib().ers_analyze(C.byref(h.c), C.byref(o), C.byref(st), _iptr(perm))
     if rc != 0:
         raise ErsError(rc, "symbolic analysis failed")
     d = st.as_dict()
@@ -345,12 +349,14 @@ def analyze(pattern) -> dict:
     return d
 
 
-def solve_plan_check(pattern) -> dict:
+def solve_plan_check(pattern, ordering: int = 0) -> dict:
     """Host-only check of the solve work lists of a square CSR pattern (see ers.h); raises
     ErsError when a property is violated."""
     h = _CsrHold(pattern)
     counts = np.zeros(8, np.int64)
-    rc = lib().ers_solve_plan_check(C.byref(h.c), counts.ctypes.data_as(C.POINTER(C.c_int64)))
+    o = make_opts(ordering=ordering)
+    rc = lib().ers_solve_plan_check(C.byref(h.c), C.byref(o),
+                                    counts.ctypes.data_as(C.POINTER(C.c_int64)))
     if rc != 0:
         raise ErsError(rc, "solve plan check failed")
     keys = ["fwd_entries", "bwd_entries", "fwd_lane_items", "bwd_lane_items",

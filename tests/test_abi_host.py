@@ -74,26 +74,40 @@ def _chol_nnz(M, perm):
     return nnz
 
 
+@pytest.mark.parametrize("ordering", [0, 1])
 @pytest.mark.parametrize("circ", [S.rc_mesh_2d(9, 7, seed=1), S.random_rc(n=30, seed=2),
                                   S.inverter_chain(stages=5, tree_nodes=12, seed=3),
                                   S.rc_mesh_3d(6, 5, 4, seed=1, n_loads=5)])
-def test_symbolic_fill_matches_brute_force(E, circ):
+def test_symbolic_fill_matches_brute_force(E, circ, ordering):
     M = _pattern(circ)
-    d = E.analyze(M)
+    d = E.analyze(M, ordering=ordering)
     perm = d["perm"]
     assert sorted(perm.tolist()) == list(range(circ.n))
     assert d["nnz_L"] == _chol_nnz(M, perm)
     assert d["nsn"] >= 1 and d["nlevels"] >= 1
 
 
-def test_tree_ordering_has_no_fill(E):
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_tree_ordering_has_no_fill(E, ordering):
     """A tree small enough for one nested-dissection leaf is ordered by exact minimum
     degree, which eliminates leaves first: zero fill."""
     circ = S.inverter_chain(stages=1, tree_nodes=30, seed=7)
     M = _pattern(circ)
-    d = E.analyze(M)
+    d = E.analyze(M, ordering=ordering)
     sym = ((M + M.T) != 0).astype(int)
     assert d["nnz_L"] == circ.n + (sym.nnz - circ.n) // 2
+
+
+def test_ordering_1_reduces_mesh_fill(E):
+    """ordering = 1 (the smallest BFS level within a 35-65 % split, from either end of the
+    pseudo-diameter) against the median-level separators of ordering = 0 on 2D and 3D meshes;
+    an unknown ordering is refused."""
+    for G in (S.rc_mesh_2d(32, 32, seed=0).G, S.rc_mesh_3d(20, 20, 20, seed=1, n_loads=80).G):
+        a, b = E.analyze(G, ordering=0), E.analyze(G, ordering=1)
+        assert b["nnz_L"] < 0.95 * a["nnz_L"], (a["nnz_L"], b["nnz_L"])
+        assert b["factor_doubles"] < a["factor_doubles"]
+    with pytest.raises(E.ErsError):
+        E.analyze(S.rc_mesh_2d(4, 4, seed=0).G, ordering=2)
 
 
 def test_analyze_rejects_missing_diagonal(E):
@@ -103,8 +117,9 @@ def test_analyze_rejects_missing_diagonal(E):
         E.analyze(M)
 
 
+@pytest.mark.parametrize("ordering", [0, 1])
 @pytest.mark.parametrize("name", ["rc2d", "rc3d", "chain", "batch", "randrc"])
-def test_solve_plan_covers_and_orders(E, name):
+def test_solve_plan_covers_and_orders(E, name, ordering):
     """Every supernode is computed once per direction, every wait points to an earlier entry
     (deadlock-free persistent solves); the batch of chains exercises the lane tasks."""
     if name == "rc2d":
@@ -120,8 +135,8 @@ def test_solve_plan_covers_and_orders(E, name):
         G = S.random_rc(n=60, seed=3, density=0.4).G
     G = sp.csr_matrix(G)
     G.sort_indices()
-    c = E.solve_plan_check(G)
-    st = E.analyze(G)
+    c = E.solve_plan_check(G, ordering=ordering)
+    st = E.analyze(G, ordering=ordering)
     nsn = st["nsn"]
     assert c["fwd_lane_items"] + c["fwd_warp_supernodes"] + c["fwd_diag"] == nsn
     assert c["bwd_lane_items"] + c["bwd_warp_supernodes"] + c["bwd_diag"] == nsn
