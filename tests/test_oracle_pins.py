@@ -538,3 +538,56 @@ def test_exp_hinv_e1_with_tiny_and_zero_eigenvalues(case):
     # wrong limit at mu = 0 or a lost coupling block misses them by orders of magnitude
     assert np.max(np.abs(y - ref_y)) <= 1e-12 * np.max(np.abs(ref_y)), case
     assert abs(last - ref_g[m - 1]) <= 1e-12 * np.max(np.abs(ref_g)), case
+
+
+def test_adaptive_step_sequence_by_hand():
+    """Algorithm 2 on a linear circuit (e_rr = 0, Eq. 15, so no try is rejected): the first
+    step is h_max, a step is clipped to land on the next PWL corner or t_end, and after an
+    accepted step the next one is beta = 2 times it, capped at h_max.  With h_max = 0.3 ps, a
+    corner at 0.35 ps and t_end = 1 ps the steps are, worked out by hand,
+    0.3 | 0.05 (lands on 0.35) | 0.1 | 0.2 | 0.3 | 0.05 (lands on 1.0) ps,
+    and every accepted state is the exact solution (one node: a 1-D Krylov space)."""
+    circ = S.single_rc(t_end=1e-12)
+    circ.pwl = [(np.array([0.0, 0.35e-12, 1e-12]), np.array([0.0, 1e-3, 1e-3]))]
+    x, t, st = O.er_run(circ, t_end=1e-12, tol=1e-6, opts=O.Options(h_max=0.3e-12),
+                        x0=np.zeros(1), trace=True)
+    assert np.allclose(np.array(st.hs) * 1e12, [0.3, 0.05, 0.1, 0.2, 0.3, 0.05], rtol=1e-12,
+                       atol=0)
+    assert np.allclose(np.array(st.ts) * 1e12, [0.3, 0.35, 0.45, 0.65, 0.95, 1.0], rtol=1e-12,
+                       atol=0)
+    assert st.rejects == 0 and st.lu == 6 and t == 1e-12
+    xe = np.zeros(1); ta = 0.0
+    for tb in st.ts:
+        xe = exact_linear_step(circ, xe, ta, tb - ta)
+        ta = tb
+    assert abs(x[0] - xe[0]) <= 1e-12 * abs(xe[0])
+
+
+@pytest.mark.parametrize("i_grow", [5, 1])
+def test_rejection_and_growth_rule_by_hand(monkeypatch, i_grow):
+    """Algorithm 2's reaction to the error test, with the estimate of Eq. 15 replaced by a
+    scripted sequence of ratios err / E_rr (one per try), on a corner-free window (the first
+    input edge is at 0.1 ns, h_max = 1 ps).  Worked out by hand with alpha = 1/2, beta = 2:
+      step 1: ratios 2, 0.5     -> reject, accept at h_max/2 (i = 1);
+      step 2: ratios 3, 3, 0.1  -> reject twice, accept at the proposal / 4 (i = 2);
+      step 3: ratio 0.1         -> accept the proposal (i = 0).
+    A step grows the next proposal by beta only when its retry count i < i_grow:
+      i_grow = 5: proposals H, H, H/2 -> accepted H/2, H/4, H/2;
+      i_grow = 1: proposals H, H/2, H/8 -> accepted H/2, H/8, H/8."""
+    circ = S.inverter_chain(stages=1, tree_nodes=3, seed=9, t_end=1e-9)
+    ratios = iter([2.0, 0.5, 3.0, 3.0, 0.1, 0.1])
+    tol = 1e-6
+
+    def scripted(circ_, st, x_new, h, C, opts, fixed_m=0):
+        E = tol * max(1.0, float(np.max(np.abs(st.lin.x))))
+        e = np.zeros(circ_.n)
+        e[0] = next(ratios) * E
+        return e, np.zeros(circ_.n), None
+
+    monkeypatch.setattr(O, "error_vector", scripted)
+    H = 1e-12
+    _, t, st = O.er_run(circ, t_end=1e-9, tol=tol, opts=O.Options(h_max=H, i_grow=i_grow),
+                        max_steps=3, trace=True)
+    want = [H / 2, H / 4, H / 2] if i_grow == 5 else [H / 2, H / 8, H / 8]
+    assert np.allclose(st.hs, want, rtol=1e-12, atol=0), (st.hs, want)
+    assert st.rejects == 3 and st.lu == 3 and abs(t - sum(want)) <= 1e-24
