@@ -97,3 +97,64 @@ def test_two_rank_sharded_run_matches_single_process():
         assert len(res) == len(circs)
         for (x, s), (xr, sr) in zip(res, ref):
             assert s == sr and np.array_equal(x, xr)
+
+
+def test_missing_share_is_reported():
+    """The host gather notices an instance that no rank returned (a rank whose results were
+    lost) and a run() that returns the wrong number of results."""
+    circs = _circuits()
+    parts = lpt_partition([instance_cost(c) for c in circs], 2)
+
+    def run(insts):
+        return [("ok", c.n) for c in insts]
+
+    def gather_dropping_rank1(obj):
+        return [obj]                     # rank 1's (indices, results) never arrive
+
+    with pytest.raises(RuntimeError, match="not run by any rank"):
+        run_sharded(circs, run, 0, 2, gather_dropping_rank1)
+    with pytest.raises(RuntimeError, match="one result per instance"):
+        run_sharded(circs, lambda insts: [], 0, 2, lambda o: [o, o])
+    assert parts[0] and parts[1]
+
+
+def _dying_worker(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(0)                      # dies between steps, before the gather
+
+    def gather(obj):
+        lst = [None] * world
+        dist.all_gather_object(lst, obj)
+        return lst
+
+    try:
+        run_sharded(_circuits(), lambda insts: [c.n for c in insts], rank, world, gather)
+        q.put((rank, "returned"))
+    except Exception as ex:             # the peer's absence must surface as an error
+        q.put((rank, "error: " + type(ex).__name__))
+
+
+def test_rank_that_dies_is_detected_by_the_survivor():
+    """A rank that exits before the result gather: the surviving rank's collective ends with
+    an error (peer closed, or the 10 s process-group timeout) instead of waiting forever."""
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_dying_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    try:
+        rank, outcome = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert rank == 0 and outcome.startswith("error"), outcome
