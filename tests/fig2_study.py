@@ -39,7 +39,52 @@ def study(hs=(2e-12, 1e-12, 0.5e-12)):
     return rows
 
 
+def trajectory(step, circ, x0, t0, t1, h, every):
+    """States every `every` seconds through the window, by steps of h."""
+    x = x0.copy()
+    out = []
+    k_per = int(round(every / h))
+    for k in range(int(round((t1 - t0) / h))):
+        x = step(circ, x, t0 + k * h, h)
+        if (k + 1) % k_per == 0:
+            out.append(x.copy())
+    return np.array(out)
+
+
+def er_step(circ, x, t, h, correction=False):
+    opts = O.Options(correction=correction, eps=1e-12, m_max=circ.n)
+    return O.er_step(circ, x, t, h, m=0, opts=opts).x
+
+
+def be_step(circ, x, t, h):
+    return O.be_run(_shifted(circ, t), h, t_end=h, x0=x)
+
+
+def paper_setting():
+    """The paper's Fig. 2 setting: BENR and ER at 1e-13 s, ER-C at 2e-13 s, against REF =
+    BENR at 1e-14 s (and, beside it, ER at 1e-14 s), on the inverter output (MOSFET drain)
+    that swings most in the window; errors are the largest difference over the common 0.2 ps grid."""
+    circ, x0, t0, t1 = _switching_window()
+    grid = 0.2e-12
+    ref_be = trajectory(be_step, circ, x0, t0, t1, 0.01e-12, grid)
+    ref_er = trajectory(er_step, circ, x0, t0, t1, 0.01e-12, grid)
+    drains = np.unique(circ.dev["d"][circ.dev["d"] >= 0])
+    node = int(drains[np.argmax(np.ptp(ref_er[:, drains], axis=0))])
+    runs = {"BENR 0.1 ps": trajectory(be_step, circ, x0, t0, t1, 0.1e-12, grid),
+            "ER 0.1 ps": trajectory(er_step, circ, x0, t0, t1, 0.1e-12, grid),
+            "ER 0.2 ps": trajectory(er_step, circ, x0, t0, t1, 0.2e-12, grid),
+            "ER-C 0.2 ps": trajectory(lambda c, x, t, h: er_step(c, x, t, h, True),
+                                      circ, x0, t0, t1, 0.2e-12, grid)}
+    return node, {k: (float(np.max(np.abs(v[:, node] - ref_be[:, node]))),
+                      float(np.max(np.abs(v[:, node] - ref_er[:, node]))))
+                  for k, v in runs.items()}
+
+
 if __name__ == "__main__":
-    print("h (ps)   ER        ER-C      BENR")
+    print("h (ps)   ER        ER-C      BENR      (end of window, all nodes, vs ER at 0.03125 ps)")
     for h, er, erc, be in study():
         print(f"{h * 1e12:6.3f}  {er:.2e}  {erc:.2e}  {be:.2e}")
+    node, errs = paper_setting()
+    print(f"paper's setting, node {node}: max error vs REF = BENR 0.01 ps | vs ER 0.01 ps")
+    for k, (a, b) in errs.items():
+        print(f"  {k:12s} {a:.2e} | {b:.2e}")
