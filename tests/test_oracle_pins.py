@@ -591,3 +591,28 @@ def test_rejection_and_growth_rule_by_hand(monkeypatch, i_grow):
     want = [H / 2, H / 4, H / 2] if i_grow == 5 else [H / 2, H / 8, H / 8]
     assert np.allclose(st.hs, want, rtol=1e-12, atol=0), (st.hs, want)
     assert st.rejects == 3 and st.lu == 3 and abs(t - sum(want)) <= 1e-24
+
+
+def test_residual_test_can_pass_falsely_at_j1_so_m_min_is_3():
+    """Why the Eq. 16 test starts at m_min = 3 rather than at j = 1 as Algorithm 1 writes it.
+    Two decoupled nodes with time constants 1e-16 s and 1e-10 s, v = (1, 1e-3), h = 1 ps: the
+    one-dimensional Ritz value is dominated by the fast mode, e^{h/h_11} underflows, Eq. 16
+    reports a zero residual and the literal loop accepts m = 1 with the result 0, while the
+    slow component should be 1e-3 e^{-0.01}.  From m_min = 2 on the answer is exact."""
+    import scipy.sparse as sp
+    G = sp.csr_matrix(np.eye(2))
+    C = sp.csr_matrix(np.diag([1e-16, 1e-10]))
+
+    class Identity:               # G = I: the solve is the identity
+        Gk = G
+
+        def solve(self, b):
+            return np.asarray(b, float).copy()
+
+    v = np.array([1.0, 1e-3])
+    h = 1e-12
+    exact = np.exp(-h / np.array([1e-16, 1e-10])) * v
+    K1 = O.arnoldi_iks(C, Identity(), G, v, h, 1e-7, 2, 1, 0)
+    assert K1.m == 1 and np.max(np.abs(K1.mevp(h))) == 0.0           # false convergence
+    K3 = O.arnoldi_iks(C, Identity(), G, v, h, 1e-7, 2, O.Options().m_min, 0)
+    assert np.max(np.abs(K3.mevp(h) - exact)) <= 1e-12 * np.max(np.abs(exact))
