@@ -76,6 +76,8 @@ typedef struct {
   double h_max;        /* largest step (0: t_end / 100)                                           */
   double h_init;       /* first step (0: h_max)                                                   */
   double vdd;          /* supply rail voltage for terminals tagged -2 (default 1 V)               */
+  double gmin;         /* conductance added from every node to ground (default 0: the netlist
+                          carries its own; a MOSFET stage needs some, see the inverter chains) */
   int32_t i_grow;      /* grow h when the retry count i < i_grow (Alg. 2, default 5)              */
   int32_t m_min;       /* first dimension at which Eq. 16 is tested (default 3)                   */
   int32_t m_max;       /* Algorithm 1's m_c (default 40, at most 64)                              */

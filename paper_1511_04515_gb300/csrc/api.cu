@@ -440,6 +440,7 @@ ers_status ers_default_opts(ers_opts* o) {
   o->h_max = 0.0;
   o->h_init = 0.0;
   o->vdd = 1.0;
+  o->gmin = 0.0;
   o->i_grow = 5;
   o->m_min = 3;
   o->m_max = 40;
@@ -462,8 +463,8 @@ static SymbolicOptions symbolic_options(const ers_opts* o) {
 const char* ers_last_error(const ers_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 static ers_status build_union(ers_ctx* c, const ers_csr* G, const ers_mosfet* dev, int ndev,
-                              std::vector<int32_t>& uptr, std::vector<int32_t>& uidx,
-                              std::vector<double>& uval) {
+                              double gmin, std::vector<int32_t>& uptr,
+                              std::vector<int32_t>& uidx, std::vector<double>& uval) {
   int n = G->n_rows;
   std::vector<std::vector<int32_t>> extra(n);
   for (int d = 0; d < ndev; ++d) {
@@ -483,7 +484,7 @@ static ers_status build_union(ers_ctx* c, const ers_csr* G, const ers_mosfet* de
   for (int i = 0; i < n; ++i) {
     std::vector<std::pair<int32_t, double>> row;
     for (int e = G->rowptr[i]; e < G->rowptr[i + 1]; ++e) row.push_back({G->colidx[e], G->val[e]});
-    row.push_back({i, 0.0});  // the diagonal is always part of the pattern
+    row.push_back({i, gmin});  // the diagonal is always part of the pattern
     for (int j : extra[i]) row.push_back({j, 0.0});
     std::sort(row.begin(), row.end(), [](auto& a, auto& b) { return a.first < b.first; });
     int last = -1;
@@ -542,6 +543,8 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   if (c->opts.m_min < 1) c->opts.m_min = 1;
   if (c->opts.ordering != 0 && c->opts.ordering != 1)
     return bail(fail(c, ERS_ERR_INVALID, "ordering must be 0 or 1"));
+  if (!(c->opts.gmin >= 0.0) || !std::isfinite(c->opts.gmin))
+    return bail(fail(c, ERS_ERR_INVALID, "gmin must be finite and >= 0"));
   c->n = n;
   c->p = p;
   c->ndev = ndev;
@@ -550,7 +553,7 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   // union pattern of G_k and its symbolic analysis
   std::vector<int32_t> uptr, uidx;
   std::vector<double> uval;
-  ers_status st = build_union(c, G, dev, ndev, uptr, uidx, uval);
+  ers_status st = build_union(c, G, dev, ndev, c->opts.gmin, uptr, uidx, uval);
   if (st != ERS_OK) return bail(st);
   SymbolicOptions so = symbolic_options(&c->opts);
   std::string err = analyze(n, uptr.data(), uidx.data(), so, c->sym);

@@ -45,6 +45,7 @@ class Opts(C.Structure):
     _fields_ = [("eps_krylov", C.c_double), ("E_rr", C.c_double), ("alpha", C.c_double),
                 ("beta", C.c_double), ("gamma", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("h_init", C.c_double), ("vdd", C.c_double),
+                ("gmin", C.c_double),
                 ("i_grow", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32),
                 ("combined_vector", C.c_int32), ("correction", C.c_int32),
                 ("ordering", C.c_int32)]

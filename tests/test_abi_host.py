@@ -179,3 +179,14 @@ def test_coupling_capacitance_fills_c_over_h_plus_g(E):
     a, b = E.analyze(G), E.analyze(CG)
     assert CG.nnz > 1.3 * G.nnz
     assert b["nnz_L"] > 1.3 * a["nnz_L"] and b["refactor_flops"] > 1.4 * a["refactor_flops"]
+
+
+def test_gmin_option_default_and_validation(E):
+    """gmin (conductance from every node to ground added by the library) defaults to 0 and a
+    negative or non-finite value is refused before any device work."""
+    assert E.default_opts().gmin == 0.0
+    circ = S.random_rc(n=8, seed=1)
+    for bad in (-1e-12, float("nan"), float("inf")):
+        with pytest.raises(E.ErsError) as ei:
+            E.Simulator.from_circuit(circ, opts=E.make_opts(gmin=bad))
+        assert ei.value.status == 1 and "gmin" in str(ei.value)
