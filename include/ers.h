@@ -361,9 +361,13 @@ ers_status ers_wait_selftest(ers_ctx* ctx);
  * count kept.  Changes no result: the same tasks run with the same dependencies. */
 ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen);
 
-/* Host-only check of the triangular-solve work lists built for a pattern (no GPU): every
- * supernode is computed by exactly one task per direction and every wait of a task refers to
- * an earlier entry of its list (the property that makes the persistent solves deadlock-free).
+/* Host-only check of the refactor plan and the triangular-solve work lists built for a
+ * pattern (no GPU).  Refactor: fronts whose lives overlap occupy disjoint arena ranges, every
+ * front and assembly target lies inside the arena, no two entries of A assemble into one
+ * position, and every relative index of a child's rows points inside its parent's front.
+ * Solves: every supernode is computed by exactly one task per direction and every wait of a
+ * task refers to an earlier entry of its list (the property that makes the persistent solves
+ * deadlock-free).
  * counts (8 values, may be NULL): forward and backward CTA entries, lane items (fwd, bwd),
  * warp-task supernodes (fwd, bwd), DIAG entries (fwd, bwd).  ERS_ERR_INVALID with a
  * violated property (or a malformed pattern).  opts (may be NULL: defaults) selects the

@@ -943,8 +943,72 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
 }
 
 
+// The multifrontal refactor plan: front s lives from the allocation phase of its level to
+// the release phase of its parent's level (its own, for a root), so every two fronts whose
+// lives overlap must occupy disjoint arena ranges; every front lies inside the arena; no two
+// entries of A assembled at one level go to one arena position; every relative index of a
+// child's rows points inside its parent's front.
+static std::string check_refactor_plan(const Symbolic& S) {
+  const int nsn = S.nsn;
+  auto fsize = [&](int s) -> int64_t {
+    return (S.sn_start[s + 1] - S.sn_start[s]) + (S.rptr[s + 1] - S.rptr[s]);
+  };
+  auto padded = [](int64_t len) { return (len + 31) & ~(int64_t)31; };
+  std::vector<std::vector<int32_t>> born(S.nlevels), dies(S.nlevels);
+  for (int s = 0; s < nsn; ++s) {
+    if (S.level[s] < 0 || S.level[s] >= S.nlevels) return "front level out of range";
+    int p = S.sn_parent[s];
+    int last = p < 0 ? S.level[s] : S.level[p];
+    if (p >= 0 && S.level[p] <= S.level[s]) return "a parent front is not above its child";
+    if (S.front_off[s] < 0 || S.front_off[s] + fsize(s) * fsize(s) > S.arena_size)
+      return "front " + std::to_string(s) + " outside the arena";
+    born[S.level[s]].push_back(s);
+    dies[last].push_back(s);
+  }
+  std::map<int64_t, std::pair<int64_t, int32_t>> live;   // offset -> (end, front)
+  for (int l = 0; l < S.nlevels; ++l) {
+    for (int s : born[l]) {
+      int64_t a = S.front_off[s], b = a + padded(fsize(s) * fsize(s));
+      auto it = live.lower_bound(a);
+      if (it != live.end() && it->first < b)
+        return "fronts " + std::to_string(s) + " and " + std::to_string(it->second.second) +
+               " overlap in the arena";
+      if (it != live.begin() && std::prev(it)->second.first > a)
+        return "fronts " + std::to_string(s) + " and " +
+               std::to_string(std::prev(it)->second.second) + " overlap in the arena";
+      live[a] = {b, s};
+    }
+    for (int s : dies[l]) live.erase(S.front_off[s]);
+  }
+  // entries are assembled level by level (fronts of different levels may reuse memory)
+  for (int l = 0; l < S.nlevels; ++l) {
+    std::vector<int64_t> dst;
+    for (int32_t k = S.lvl_slot_ptr[l]; k < S.lvl_slot_ptr[l + 1]; ++k)
+      dst.push_back(S.asm_dst[S.lvl_slot[k]]);
+    std::sort(dst.begin(), dst.end());
+    for (size_t e = 0; e < dst.size(); ++e) {
+      if (dst[e] < 0 || dst[e] >= S.arena_size) return "assembly target outside the arena";
+      if (e > 0 && dst[e] == dst[e - 1])
+        return "two entries of A assemble into one position at level " + std::to_string(l);
+    }
+  }
+  if (S.lvl_slot_ptr[S.nlevels] != (int32_t)S.asm_dst.size()) return "assembly slots not covered";
+  for (int s = 0; s < nsn; ++s) {
+    int p = S.sn_parent[s];
+    if (p < 0) continue;
+    for (int64_t e = S.rptr[s]; e < S.rptr[s + 1]; ++e)
+      if (S.rel[e] < 0 || S.rel[e] >= fsize(p))
+        return "relative index of front " + std::to_string(s) + " outside its parent";
+  }
+  return "";
+}
+
 std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   const int nsn = S.nsn;
+  {
+    std::string err = check_refactor_plan(S);
+    if (!err.empty()) return "refactor plan: " + err;
+  }
   for (int q = 0; q < 8; ++q) counts[q] = 0;
   counts[0] = (int64_t)S.fwd.size();
   counts[1] = (int64_t)S.bwd.size();
