@@ -35,6 +35,7 @@ FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32
 # times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
 # k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
 SOLVE_TRAFFIC_RATIO = 2.6626 / 2.5525
+CLOCKS_DIR = os.environ.get("ERS_CLOCKS_DIR") or os.path.join(ROOT, ".bench")   # nvidia-smi samples
 L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
 FLUSH_BYTES = 256 * 2 ** 20
 SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same generator
@@ -246,7 +247,7 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    clk_path = os.path.join(CLOCKS_DIR, f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     proc, fh = clocks_start(local, clk_path)
     factor_bytes = st0["factor_doubles"] * 8
@@ -473,7 +474,7 @@ def run_batch_workload(a):
     tuned, tune_ms = sim.autotune(nrhs=2, passes=3)
     _, x0, _ = sim.state()
     arms = {}
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
+    clk_path = os.path.join(CLOCKS_DIR, f"clocks_batch_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     proc, fh = clocks_start(local, clk_path)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")

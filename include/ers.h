@@ -161,7 +161,7 @@ ers_status ers_get_state_inst(const ers_ctx* ctx, int32_t k, double* t, double* 
 
 /* ---- Learned step controller (the paper's controller is the plain rule of Alg. 2: reject ->
  * h = alpha h with the same Krylov spaces, accept -> h = beta h while the step saw fewer than
- * i_grow rejections).  The learned form keeps the error test of Eq. 15 as the judge: a network
+ * i_grow rejections).  The learned form keeps the error test of Eq. 15 as the arbiter: a network
  * proposes the next (h, m) of each instance from its last 8 accepted steps; a rejected
  * proposal falls back to the plain rule (h = alpha h, same spaces).  The proposed m is the
  * Krylov dimension from which the residual test of Eq. 16 is evaluated; the basis still grows

@@ -1,7 +1,7 @@
 // Learned step-size controller network: MLP 32 -> 64 -> 64 -> 64 -> 2 with ReLU, BF16 weights,
 // BF16 tensor-core operands with FP32 accumulation (mma.sync m16n8k16 bf16), FP32 master
 // weights and Adam.  (The paper's controller is the plain rule of Alg. 2; the network proposes
-// the next step from the history of accepted steps and the error test of Eq. 15 stays the judge.)
+// the next step from the history of accepted steps and the error test of Eq. 15 decides.)
 //
 // One CTA of 4 warps handles 64 samples: forward (each warp its 16 samples), loss gradient,
 // backward through the layers, and weight gradients dW_l = dH_l^T H_{l-1} where warp w owns the
