@@ -36,7 +36,7 @@ cudaError_t launch_absmax(ers_ctx* c, const double* x, unsigned long long* out);
 int coop_max_blocks(int sm_count);
 
 // ---------------------------------------------------------------------------------------
-// small kernels local to the driver
+// small kernels local to the host-side step orchestration
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np, double x) {
   if (x <= t[0]) return v[0];

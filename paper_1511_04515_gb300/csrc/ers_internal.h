@@ -100,7 +100,7 @@ struct ers_ctx {
   int device = 0;
   int sm_count = 0;
   int solve_ctas_per_sm = 3;           // resident CTAs per SM of the persistent solves (tunable)
-  // host copies (permuted) needed by the driver
+  // host copies (permuted) needed by the host-side step orchestration
   std::vector<double> bp;              // sorted unique PWL corner times
   // device arrays (permuted node order)
   int32_t* d_perm = nullptr;                    // new -> old node index
