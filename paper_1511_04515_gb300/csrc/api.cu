@@ -562,9 +562,10 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
 
   cudaError_t ce = cudaGetDevice(&c->device);
   if (ce != cudaSuccess) return bail(fail(c, ERS_ERR_CUDA, cudaGetErrorString(ce)));
-  cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, c->device);
-  c->sm_count = prop.multiProcessorCount;
+  ce = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (ce != cudaSuccess || c->sm_count < 1)
+    return bail(fail(c, ERS_ERR_CUDA, ce != cudaSuccess ? cudaGetErrorString(ce)
+                                                        : "device reports no multiprocessors"));
 #define CUB(call)                                                                        \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
