@@ -1091,16 +1091,18 @@ ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, do
                          double* last) {
   if (!c || !H || !y || !last) return ERS_ERR_INVALID;
   if (m < 1 || m > MAX_M || ldh < m) return fail(c, ERS_ERR_INVALID, "bad m / ldh");
-  double *dH = nullptr, *dy = nullptr;
-  CU(cudaMalloc((void**)&dH, sizeof(double) * (size_t)ldh * m));
-  CU(cudaMalloc((void**)&dy, sizeof(double) * (m + 1)));
+  struct DevBuf {   // freed on every return path
+    double* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+  } bH, by;
+  CU(cudaMalloc((void**)&bH.p, sizeof(double) * (size_t)ldh * m));
+  CU(cudaMalloc((void**)&by.p, sizeof(double) * (m + 1)));
+  double *dH = bH.p, *dy = by.p;
   CU(cudaMemcpyAsync(dH, H, sizeof(double) * (size_t)ldh * m, cudaMemcpyHostToDevice, c->stream));
   CU(launch_small_test(c, dH, ldh, m, h, dy, dy + m));
   std::vector<double> hy(m + 1);
   CU(cudaMemcpyAsync(hy.data(), dy, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  cudaFree(dH);
-  cudaFree(dy);
   for (int k = 0; k < m; ++k) y[k] = hy[k];
   *last = hy[m];
   return ERS_OK;
