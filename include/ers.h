@@ -374,6 +374,23 @@ ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, 
  * ordering, as in ers_create. */
 ers_status ers_solve_plan_check(const ers_csr* pattern, const ers_opts* opts, int64_t* counts);
 
+/* Host-only export of one array of the symbolic plan built for a pattern (no GPU), for
+ * checking the plan outside the library.  which selects the array; int32 arrays: PERM
+ * (new -> old), SN_START (nsn+1), SN_PARENT, LEVEL, ROWS (off-diagonal rows of each
+ * supernode, new order), REL (their positions in the parent's front), A_PTR, A_IDX (the
+ * pattern in the new order), A_SRC (each new slot's index in the given CSR), CH_PTR, CH_LIST
+ * (children of each supernode in extend-add order), LVL_SLOT_PTR, LVL_SLOT (slots by level);
+ * int64 arrays: RPTR (nsn+1), FRONT_OFF (arena offset of each f x f column-major front,
+ * f = width + rows), ASM_DST (arena position of each slot), ARENA (one value: the arena size).
+ * With out == NULL only *len (the element count) is set; otherwise out receives *len
+ * elements of the array's type.  ERS_ERR_INVALID for an unknown which or a malformed pattern. */
+enum { ERS_PLAN_PERM = 0, ERS_PLAN_SN_START, ERS_PLAN_SN_PARENT, ERS_PLAN_LEVEL, ERS_PLAN_ROWS,
+       ERS_PLAN_REL, ERS_PLAN_A_PTR, ERS_PLAN_A_IDX, ERS_PLAN_A_SRC, ERS_PLAN_CH_PTR,
+       ERS_PLAN_CH_LIST, ERS_PLAN_LVL_SLOT_PTR, ERS_PLAN_LVL_SLOT, ERS_PLAN_RPTR,
+       ERS_PLAN_FRONT_OFF, ERS_PLAN_ASM_DST, ERS_PLAN_ARENA };
+ers_status ers_plan_array(const ers_csr* pattern, const ers_opts* opts, int32_t which, void* out,
+                          int64_t* len);
+
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
 /* Turn CUDA-event timing of the triangular-solve kernels on (1) or off (0); resets the

@@ -1213,6 +1213,44 @@ ers_status ers_analyze(const ers_csr* pat, const ers_opts* opts, ers_stats_t* ou
   return ERS_OK;
 }
 
+ers_status ers_plan_array(const ers_csr* pat, const ers_opts* opts, int32_t which, void* out,
+                          int64_t* len) {
+  if (!pat || !len || pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
+  if (opts && opts->ordering != 0 && opts->ordering != 1) return ERS_ERR_INVALID;
+  Symbolic S;
+  if (!analyze(pat->n_rows, pat->rowptr, pat->colidx, symbolic_options(opts), S).empty())
+    return ERS_ERR_INVALID;
+  const std::vector<int32_t>* v32 = nullptr;
+  const std::vector<int64_t>* v64 = nullptr;
+  std::vector<int64_t> arena{S.arena_size};
+  switch (which) {
+    case ERS_PLAN_PERM: v32 = &S.perm; break;
+    case ERS_PLAN_SN_START: v32 = &S.sn_start; break;
+    case ERS_PLAN_SN_PARENT: v32 = &S.sn_parent; break;
+    case ERS_PLAN_LEVEL: v32 = &S.level; break;
+    case ERS_PLAN_ROWS: v32 = &S.rows; break;
+    case ERS_PLAN_REL: v32 = &S.rel; break;
+    case ERS_PLAN_A_PTR: v32 = &S.a_ptr; break;
+    case ERS_PLAN_A_IDX: v32 = &S.a_idx; break;
+    case ERS_PLAN_A_SRC: v32 = &S.a_src; break;
+    case ERS_PLAN_CH_PTR: v32 = &S.ch_ptr; break;
+    case ERS_PLAN_CH_LIST: v32 = &S.ch_list; break;
+    case ERS_PLAN_LVL_SLOT_PTR: v32 = &S.lvl_slot_ptr; break;
+    case ERS_PLAN_LVL_SLOT: v32 = &S.lvl_slot; break;
+    case ERS_PLAN_RPTR: v64 = &S.rptr; break;
+    case ERS_PLAN_FRONT_OFF: v64 = &S.front_off; break;
+    case ERS_PLAN_ASM_DST: v64 = &S.asm_dst; break;
+    case ERS_PLAN_ARENA: v64 = &arena; break;
+    default: return ERS_ERR_INVALID;
+  }
+  *len = v32 ? (int64_t)v32->size() : (int64_t)v64->size();
+  if (out) {
+    if (v32) std::memcpy(out, v32->data(), sizeof(int32_t) * v32->size());
+    else std::memcpy(out, v64->data(), sizeof(int64_t) * v64->size());
+  }
+  return ERS_OK;
+}
+
 ers_status ers_solve_plan_check(const ers_csr* pat, const ers_opts* opts, int64_t* counts) {
   if (!pat || pat->n_rows != pat->n_cols || pat->n_rows <= 0) return ERS_ERR_INVALID;
   if (opts && opts->ordering != 0 && opts->ordering != 1) return ERS_ERR_INVALID;

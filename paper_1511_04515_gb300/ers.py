@@ -94,7 +94,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
            "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check",
-           "ers_wait_selftest"]
+           "ers_wait_selftest", "ers_plan_array"]
 
 _lib = None
 
@@ -137,6 +137,8 @@ def lib():
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(Stats), pi], C.c_int),
+        "ers_plan_array": ([C.POINTER(Csr), C.POINTER(Opts), C.c_int32, C.c_void_p,
+                            C.POINTER(C.c_int64)], C.c_int),
         "ers_solve_plan_check": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(C.c_int64)],
                                  C.c_int),
         "ers_ctrl_features": ([C.POINTER(StepRecord), I32, pf], C.c_int),
@@ -363,6 +365,35 @@ def solve_plan_check(pattern, ordering: int = 0) -> dict:
     keys = ["fwd_entries", "bwd_entries", "fwd_lane_items", "bwd_lane_items",
             "fwd_warp_supernodes", "bwd_warp_supernodes", "fwd_diag", "bwd_diag"]
     return dict(zip(keys, counts.tolist()))
+
+
+PLAN_ARRAYS = [("perm", np.int32), ("sn_start", np.int32), ("sn_parent", np.int32),
+               ("level", np.int32), ("rows", np.int32), ("rel", np.int32), ("a_ptr", np.int32),
+               ("a_idx", np.int32), ("a_src", np.int32), ("ch_ptr", np.int32),
+               ("ch_list", np.int32), ("lvl_slot_ptr", np.int32), ("lvl_slot", np.int32),
+               ("rptr", np.int64), ("front_off", np.int64), ("asm_dst", np.int64),
+               ("arena", np.int64)]
+
+
+def plan_arrays(pattern, ordering: int = 0) -> dict:
+    """Host-only export of the symbolic plan of a square CSR pattern (see ers_plan_array in
+    ers.h): every array by name, in the plan's (new) node order."""
+    h = _CsrHold(pattern)
+    o = make_opts(ordering=ordering)
+    out = {}
+    for which, (name, dt) in enumerate(PLAN_ARRAYS):
+        ln = C.c_int64(0)
+        rc = lib().ers_plan_array(C.byref(h.c), C.byref(o), which, None, C.byref(ln))
+        if rc != 0:
+            raise ErsError(rc, "plan export failed")
+        a = np.zeros(ln.value, dt)
+        if ln.value:
+            rc = lib().ers_plan_array(C.byref(h.c), C.byref(o), which,
+                                      a.ctypes.data_as(C.c_void_p), C.byref(ln))
+            if rc != 0:
+                raise ErsError(rc, "plan export failed")
+        out[name] = a
+    return out
 
 
 class Simulator:
