@@ -217,9 +217,12 @@ ers_status ers_ctrl_propose(const float* y, const ers_step_record* last, double 
  * Parameter vector (FP32, ers_mlp_nparam() entries): W1 (64x32 row-major), b1, W2 (64x64),
  * b2, W3 (64x64), b3, W4 (2x64), b4.  Outputs: y[0] = log2(h_next / h_k), y[1] = m_next/m_max. */
 typedef struct ers_mlp ers_mlp;
+/* Number of parameters (10,562). */
 int32_t ers_mlp_nparam(void);
 /* He-initialised weights (seeded), zero biases, zero Adam moments. */
 ers_status ers_mlp_create(ers_mlp** out, uint64_t seed);
+/* Copy ers_mlp_nparam() FP32 parameters in (the BF16 copy is refreshed; Adam moments are
+ * kept) or out (host buffers, caller-owned). */
 ers_status ers_mlp_set_params(ers_mlp* mlp, const float* params);
 ers_status ers_mlp_get_params(const ers_mlp* mlp, float* params);
 /* Y (n x 2) = network(X (n x 32)); host buffers, row-major. */
@@ -239,7 +242,10 @@ ers_status ers_mlp_adam_step(ers_mlp* mlp, const float* X, const float* T, int32
  * `batch` samples; final_loss = L of the last minibatch before its step. */
 ers_status ers_mlp_train(ers_mlp* mlp, const float* X, const float* T, int32_t n, int32_t epochs,
                          int32_t batch, float lr, uint64_t seed, float* final_loss);
+/* Text of the network's last failure (owned by the network; "" when none, "null" for a NULL
+ * network). */
 const char* ers_mlp_last_error(const ers_mlp* mlp);
+/* Free the network and its device memory; NULL is ignored. */
 void ers_mlp_destroy(ers_mlp* mlp);
 
 /* Use `mlp` (not owned; must outlive the runs, NULL = plain controller) as the step proposer of
@@ -405,7 +411,9 @@ ers_status ers_profile(ers_ctx* ctx, int32_t enable);
 ers_status ers_analyze(const ers_csr* pattern, const ers_opts* opts, ers_stats_t* out,
                        int32_t* perm);
 
+/* Text of the context's last failure (owned by the context, valid until its next call). */
 const char* ers_last_error(const ers_ctx* ctx);
+/* Free the context and all its device memory; a stream set by the caller is left alone. */
 void ers_destroy(ers_ctx* ctx);
 
 #ifdef __cplusplus
