@@ -1012,6 +1012,31 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   for (int q = 0; q < 8; ++q) counts[q] = 0;
   counts[0] = (int64_t)S.fwd.size();
   counts[1] = (int64_t)S.bwd.size();
+  auto nrows = [&](int s) { return (int)(S.rptr[s + 1] - S.rptr[s]); };
+  // a forward unit updating rows [a, b) of supernode s must arrive at exactly the supernodes
+  // that own those rows (else one could start before the update lands)
+  std::vector<int32_t> owners, targets;
+  auto targets_match = [&](int s, int a, int b, int32_t tgt0, int32_t ntgt) {
+    owners.clear();
+    for (int i = a; i < b; ++i) owners.push_back(S.sn_of[S.rows[S.rptr[s] + i]]);
+    std::sort(owners.begin(), owners.end());
+    owners.erase(std::unique(owners.begin(), owners.end()), owners.end());
+    targets.assign(S.fwd_tgt.begin() + tgt0, S.fwd_tgt.begin() + tgt0 + ntgt);
+    std::sort(targets.begin(), targets.end());
+    return owners == targets;
+  };
+  // the row ranges of a supernode solved by a DIAG entry and far chunks, per direction
+  std::vector<std::vector<std::pair<int, int>>> franges(nsn), branges(nsn);
+  auto partitions = [&](std::vector<std::pair<int, int>>& rg, int r) {
+    std::sort(rg.begin(), rg.end());
+    int at = 0;
+    for (auto& q : rg) {
+      if (q.second == q.first) continue;           // an empty range (a root without rows)
+      if (q.first != at || q.second < q.first) return false;
+      at = q.second;
+    }
+    return at == r;
+  };
   // ---- forward: the entry computing each supernode, and the entries of every arrival
   std::vector<int64_t> fpos(nsn, -1);
   std::vector<int64_t> arrive_last(nsn, -1), arrive_cnt(nsn, 0);
@@ -1031,6 +1056,9 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
       fpos[T.sn] = e;
       counts[6]++;
       arrive(T.tgt0, T.ntgt, e);
+      franges[T.sn].push_back({T.r0, T.r1});
+      if (!targets_match(T.sn, T.r0, T.r1, T.tgt0, T.ntgt))
+        return "forward: targets of a DIAG entry differ from the owners of its rows";
     } else if (T.kind == TASK_GROUP || T.kind == TASK_BULK) {
       for (int w = 0; w < T.r0; ++w) {
         const SolveTask& U = S.fwd_small[T.sn + w];
@@ -1039,6 +1067,8 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
           fpos[U.sn] = e;
           counts[4]++;
           arrive(U.tgt0, U.ntgt, e);
+          if (!targets_match(U.sn, 0, nrows(U.sn), U.tgt0, U.ntgt))
+            return "forward: targets of a warp task differ from the owners of its rows";
         } else if (U.kind == TASK_LANES) {
           for (int l = 0; l < U.r0; ++l) {
             const int32_t* it = S.fwd_lane.data() + 4 * ((int64_t)U.sn + l);
@@ -1046,11 +1076,16 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
             fpos[it[0]] = e;
             counts[2]++;
             arrive(it[1], it[2], e);
+            if (!targets_match(it[0], 0, nrows(it[0]), it[1], it[2]))
+              return "forward: targets of a lane item differ from the owners of its rows";
           }
         } else if (U.kind == TASK_OFF) {
           chunk_entry.push_back(e);
           chunk_sn.push_back(U.sn);
           arrive(U.tgt0, U.ntgt, e);
+          franges[U.sn].push_back({U.r0, U.r1});
+          if (!targets_match(U.sn, U.r0, U.r1, U.tgt0, U.ntgt))
+            return "forward: targets of a far chunk differ from the owners of its rows";
         } else {
           return "forward: unknown warp task";
         }
@@ -1066,6 +1101,10 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   }
   for (size_t q = 0; q < chunk_entry.size(); ++q)
     if (fpos[chunk_sn[q]] >= chunk_entry[q]) return "forward: far chunk before its DIAG";
+  for (int s = 0; s < nsn; ++s)
+    if (!franges[s].empty() && !partitions(franges[s], nrows(s)))
+      return "forward: the row chunks of supernode " + std::to_string(s) +
+             " do not cover its rows exactly once";
   // ---- backward
   std::vector<int64_t> bpos(nsn, -1), chunks_last(nsn, -1), chunks_cnt(nsn, 0);
   struct Wait { int64_t e; int32_t on; };
@@ -1076,6 +1115,7 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
       if (bpos[T.sn] >= 0) return "backward: supernode computed twice";
       bpos[T.sn] = e;
       counts[7]++;
+      branges[T.sn].push_back({T.r0, T.r1});
       if (T.wait_sn >= 0) waits.push_back({e, T.wait_sn});
     } else if (T.kind == TASK_GROUP || T.kind == TASK_BULK) {
       for (int w = 0; w < T.r0; ++w) {
@@ -1096,6 +1136,7 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
         } else if (U.kind == TASK_OFF) {
           chunks_last[U.sn] = std::max(chunks_last[U.sn], e);
           chunks_cnt[U.sn]++;
+          branges[U.sn].push_back({U.r0, U.r1});
           if (U.wait_sn >= 0) waits.push_back({e, U.wait_sn});
         } else {
           return "backward: unknown warp task";
@@ -1109,6 +1150,9 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
     if (bpos[s] < 0) return "backward: supernode " + std::to_string(s) + " never computed";
     if (chunks_cnt[s] != S.bwd_nchunk[s]) return "backward: chunk count mismatch";
     if (chunks_last[s] >= bpos[s]) return "backward: a far chunk comes after its DIAG";
+    if (!branges[s].empty() && !partitions(branges[s], nrows(s)))
+      return "backward: the row chunks of supernode " + std::to_string(s) +
+             " do not cover its rows exactly once";
   }
   for (const Wait& w : waits)
     if (bpos[w.on] >= w.e) return "backward: a wait refers to a later entry";
