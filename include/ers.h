@@ -373,8 +373,9 @@ ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, 
  * position, and every relative index of a child's rows points inside its parent's front.
  * Solves: every supernode is computed by exactly one task per direction, the row chunks of a
  * large supernode cover its rows exactly once, every forward unit arrives at exactly the
- * supernodes owning the rows it updates, and every wait of a task refers to an earlier entry
- * of its list (the property that makes the persistent solves deadlock-free).
+ * supernodes owning the rows it updates, every backward unit waits for the nearest owner of
+ * the rows it reads, and every wait of a task refers to an earlier entry of its list (the
+ * property that makes the persistent solves deadlock-free).
  * counts (8 values, may be NULL): forward and backward CTA entries, lane items (fwd, bwd),
  * warp-task supernodes (fwd, bwd), DIAG entries (fwd, bwd).  ERS_ERR_INVALID with a
  * violated property (or a malformed pattern).  opts (may be NULL: defaults) selects the

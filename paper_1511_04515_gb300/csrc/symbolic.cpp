@@ -1106,6 +1106,13 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
       return "forward: the row chunks of supernode " + std::to_string(s) +
              " do not cover its rows exactly once";
   // ---- backward
+  // a backward unit reading x over rows [a, b) of supernode s must wait for the owner of the
+  // smallest of those rows: its nearest ancestor among them (each supernode completes only
+  // after its parent, so that owner's completion implies every higher owner's)
+  auto wait_matches = [&](int s, int a, int b, int32_t wait_sn) {
+    if (a >= b) return true;
+    return wait_sn == S.sn_of[S.rows[S.rptr[s] + a]];
+  };
   std::vector<int64_t> bpos(nsn, -1), chunks_last(nsn, -1), chunks_cnt(nsn, 0);
   struct Wait { int64_t e; int32_t on; };
   std::vector<Wait> waits;
@@ -1116,6 +1123,8 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
       bpos[T.sn] = e;
       counts[7]++;
       branges[T.sn].push_back({T.r0, T.r1});
+      if (!wait_matches(T.sn, T.r0, T.r1, T.wait_sn))
+        return "backward: a DIAG entry waits on the wrong supernode";
       if (T.wait_sn >= 0) waits.push_back({e, T.wait_sn});
     } else if (T.kind == TASK_GROUP || T.kind == TASK_BULK) {
       for (int w = 0; w < T.r0; ++w) {
@@ -1124,6 +1133,8 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
           if (bpos[U.sn] >= 0) return "backward: supernode computed twice";
           bpos[U.sn] = e;
           counts[5]++;
+          if (!wait_matches(U.sn, 0, nrows(U.sn), U.wait_sn))
+            return "backward: a warp task waits on the wrong supernode";
           if (U.wait_sn >= 0) waits.push_back({e, U.wait_sn});
         } else if (U.kind == TASK_LANES) {
           for (int l = 0; l < U.r0; ++l) {
@@ -1131,12 +1142,16 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
             if (bpos[it[0]] >= 0) return "backward: supernode computed twice";
             bpos[it[0]] = e;
             counts[3]++;
+            if (!wait_matches(it[0], 0, nrows(it[0]), it[1]))
+              return "backward: a lane item waits on the wrong supernode";
             if (it[1] >= 0) waits.push_back({e, it[1]});
           }
         } else if (U.kind == TASK_OFF) {
           chunks_last[U.sn] = std::max(chunks_last[U.sn], e);
           chunks_cnt[U.sn]++;
           branges[U.sn].push_back({U.r0, U.r1});
+          if (!wait_matches(U.sn, U.r0, U.r1, U.wait_sn))
+            return "backward: a far chunk waits on the wrong supernode";
           if (U.wait_sn >= 0) waits.push_back({e, U.wait_sn});
         } else {
           return "backward: unknown warp task";
