@@ -6,6 +6,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# keep torch's compile cache (created on import) inside the repository's ignored scratch
+os.environ.setdefault("TORCHINDUCTOR_CACHE_DIR", os.path.join(ROOT, ".bench", "torchinductor"))
 
 
 def pytest_configure(config):
