@@ -338,19 +338,25 @@ ers_status ers_mevp(ers_ctx* ctx, const double* v, double h, int32_t m, double* 
 ers_status ers_phi_small(ers_ctx* ctx, const double* H, int32_t ldh, int32_t m, double h,
                          double* y, double* last);
 
-/* Allocation-free solve, x_dev = G_k^{-1} b_dev (n doubles each, device memory, original
- * node order).  The paper has no counterpart: this exists for callers that must not
- * allocate device memory when they solve -- code recording a CUDA stream capture, code
- * whose device memory is owned by a framework's pool allocator, latency-bound loops.  It
- * calls no cudaMalloc/cudaFree: the solve kernels' scratch (dependency counters) is a
- * fixed 6 MiB static device array of the library, shared by every call on a device and
- * held by every GPU that loads the library until exit.  Limits and rules: contexts whose
- * factor has more than 524288 supernodes are rejected with ERS_ERR_INVALID; the context
- * must hold a factorisation (ers_refactor, ers_dc or a step first, else ERS_ERR_INVALID);
- * calls whose solves overlap on the GPU (on any context of the same device) race on the
- * shared scratch; the first call on a device looks up the array's device address, so make
- * it before any stream capture.  Uses the context's stream and its internal work vector,
- * and waits for the stream before returning. */
+/* Allocation-free solve, x_dev = G_k^{-1} b_dev (n doubles each, device memory of the
+ * context's device, original node order).  The paper has no counterpart: this exists for
+ * callers that may not allocate device memory at the point where they solve -- code whose
+ * device memory is owned by a framework's pool allocator (memory the pool did not hand out
+ * breaks its accounting), and latency-bound loops that forbid allocator calls (cudaMalloc
+ * and cudaFree can synchronise the device and take unbounded time).  It calls no
+ * cudaMalloc/cudaFree: the solve kernels' scratch (dependency counters) is a fixed 6 MiB
+ * static device array of the library, shared by every call on a device and held by every
+ * GPU that loads the library until exit.  Limits and rules: contexts whose factor has more
+ * than 524288 supernodes are rejected with ERS_ERR_INVALID; the context must hold a
+ * factorisation (ers_refactor, ers_dc or a step first, else ERS_ERR_INVALID); b_dev and
+ * x_dev must be device (or managed) memory of the context's device, anything else is
+ * ERS_ERR_INVALID before any kernel runs; calls whose solves overlap on the GPU (on any
+ * context of the same device) race on the shared scratch.  The first call on a device
+ * looks up the array's device address and keeps it for the life of the process (a
+ * cudaDeviceReset invalidates it).  Uses the context's stream and its internal work vector;
+ * the call waits for the stream before returning (it synchronises, so it cannot be made
+ * while the stream is being captured into a CUDA graph).  The caller's current device is
+ * restored on return. */
 ers_status ers_solve_dev_noalloc(ers_ctx* ctx, const double* b_dev, double* x_dev);
 
 /* Failure-path self-test: a kernel waits, with the bounded wait every device-side dependency

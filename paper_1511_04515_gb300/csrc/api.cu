@@ -339,7 +339,8 @@ ers_status step_update(ers_ctx* c, const StepWork& W, double h) {
   return ERS_OK;
 }
 
-// e_rr = -(e^{hJ} - I) G^-1 dF (Eq. 15/19); ER-C correction (Eq. 20) when enabled.
+// e_rr = -(e^{hJ} - I) G^-1 dF (Eq. 15/19), its max-norm in *err_inf; leaves
+// v_e = G^-1 dF in c->ve for the ER-C correction.
 ers_status step_error(ers_ctx* c, double h, int mfixed, double* err_inf) {
   *err_inf = 0.0;
   if (!c->ndev) return ERS_OK;
@@ -356,24 +357,30 @@ ers_status step_error(ers_ctx* c, double h, int mfixed, double* err_inf) {
   CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
   double cb[1] = {-1.0};
   CU(launch_combine(c, c->tmp, nullptr, 0.0, &ge, cb, nullptr, 0.0, nullptr, 0.0, mx));
-  if (c->opts.correction) {
-    // z = G^-1 C v_e; D = (gamma/h) [(e^{hJ} - I) z + h v_e]; x_new -= D
-    launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->ve, c->solve_buf, 1.0);
-    CU(launch_solve(c, c->solve_buf, 1));
-    int zs = 1;
-    const double* zsrc[1] = {c->solve_buf};
-    VecGroup gz = make_group(c, 1, &zs, zsrc);
-    st = build_bases(c, gz, h, mfixed);
-    if (st != ERS_OK) return st;
-    double cz[1] = {-c->opts.gamma / h};
-    CU(launch_combine(c, c->xnew, c->xnew, 1.0, &gz, cz, c->ve, -c->opts.gamma, nullptr, 0.0, nullptr));
-  }
   unsigned long long bits;
   CU(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   double e;
   std::memcpy(&e, &bits, sizeof(e));
   *err_inf = e;
+  return ERS_OK;
+}
+
+// ER-C (Eq. 17 in the form of Eq. 20) of an accepted try: z = G^-1 C v_e,
+// D = (gamma/h) [(e^{hJ} - I) z + h v_e], x_new -= D.  z's basis takes Krylov slot 1, which
+// on a ramp step holds the v2 basis: it is built only once the try is accepted, because a
+// rejected try re-exponentiates the solution bases (slots 0 and 1) at a smaller h.
+ers_status step_correct(ers_ctx* c, double h, int mfixed) {
+  if (!c->ndev || !c->opts.correction) return ERS_OK;
+  launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->ve, c->solve_buf, 1.0);
+  CU(launch_solve(c, c->solve_buf, 1));
+  int zs = 1;
+  const double* zsrc[1] = {c->solve_buf};
+  VecGroup gz = make_group(c, 1, &zs, zsrc);
+  ers_status st = build_bases(c, gz, h, mfixed);
+  if (st != ERS_OK) return st;
+  double cz[1] = {-c->opts.gamma / h};
+  CU(launch_combine(c, c->xnew, c->xnew, 1.0, &gz, cz, c->ve, -c->opts.gamma, nullptr, 0.0, nullptr));
   return ERS_OK;
 }
 
@@ -873,6 +880,8 @@ static ers_status step_core(ers_ctx* c, double h, int32_t m, int32_t* m_used, do
   double err = 0.0;
   st = step_error(c, h, m, &err);
   if (st != ERS_OK) return st;
+  st = step_correct(c, h, m);
+  if (st != ERS_OK) return st;
   st = sync_status(c);
   if (st != ERS_OK) return st;
   if (m_used) {
@@ -944,6 +953,11 @@ ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int3
       ++rejects;
       h *= o.alpha;
       if (h < o.h_min) return fail(c, ERS_ERR_STEP_UNDERFLOW, "step size underflow");
+    }
+    if (c->opts.correction && c->ndev) {
+      st = step_correct(c, h, 0);
+      if (st == ERS_OK) st = sync_status(c);
+      if (st != ERS_OK) return st;
     }
     bool landed = h == nb - c->t;
     c->t = landed ? nb : c->t + h;

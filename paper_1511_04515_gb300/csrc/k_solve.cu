@@ -770,16 +770,17 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
 // ---------------------------------------------------------------------------------------
 // Allocation-free solve (no counterpart in the paper: a deployment convenience).
 //
-// Some callers cannot allocate device memory at the point where they need a solve: code
-// recording a CUDA stream capture (an allocation inside the capture would break it or be
-// replayed wrongly), frameworks whose device memory belongs to their own pool allocator,
-// and latency-bound loops that forbid allocator calls.  ers_solve_dev_noalloc serves them:
-// it runs the same forward/backward kernels as every other solve, but the kernels'
-// scratch (the dependency counters and flags, 2 + 3 * nsn ints) lives in the file-scope
-// array below instead of the context's own buffer.  The array is a fixed 6 MiB that every
-// GPU loading this library keeps until the process exits; contexts with more than
-// NOALLOC_MAX_SN supernodes are rejected.  All calls on a device share the one array, so
-// calls whose solves overlap on the GPU race; the counters are cleared at each call.
+// Some callers cannot allocate device memory at the point where they need a solve:
+// frameworks whose device memory belongs to their own pool allocator, and latency-bound
+// loops that forbid allocator calls (cudaMalloc / cudaFree may synchronise the device).
+// ers_solve_dev_noalloc serves them: it runs the same forward/backward kernels as every
+// other solve, but the kernels' scratch (the dependency counters and flags, 2 + 3 * nsn
+// ints) lives in the file-scope array below instead of the context's own buffer.  The array
+// is a fixed 6 MiB that every GPU loading this library keeps until the process exits;
+// contexts with more than NOALLOC_MAX_SN supernodes are rejected.  All calls on a device
+// share the one array, so calls whose solves overlap on the GPU race; the counters are
+// cleared at each call.  The call ends with a stream synchronisation (it reads the device
+// status), so it is not usable inside a stream capture.
 // ---------------------------------------------------------------------------------------
 namespace ers {
 
@@ -795,7 +796,9 @@ __global__ void k_scatter_perm(int n, const int32_t* perm, const double* src, do
   if (i < n) dst[perm[i]] = src[i];
 }
 
-// Device address of g_noalloc_sync on the current device, looked up once per device.
+// Device address of g_noalloc_sync on the current device, looked up once per device and
+// kept for the life of the process (a cudaDeviceReset or a re-created primary context would
+// leave the cached address stale; the library never resets a device itself).
 static int32_t* noalloc_scratch(int device, cudaError_t* err) {
   static std::mutex mu;
   static int32_t* addr[128] = {};
@@ -820,8 +823,26 @@ extern "C" ers_status ers_solve_dev_noalloc(ers_ctx* c, const double* b_dev, dou
   using namespace ers;
   if (!c) return ERS_ERR_INVALID;
   if (!b_dev || !x_dev) {
-    c->err = "ers_solve_dev_noalloc: b_dev and x_dev must be device pointers";
+    c->err = "ers_solve_dev_noalloc: b_dev and x_dev must not be NULL";
     return ERS_ERR_INVALID;
+  }
+  // both buffers must be device (or managed) memory of the context's device: a host
+  // pointer or another device's memory would make the permutation kernels fault
+  for (const void* ptr : {(const void*)b_dev, (const void*)x_dev}) {
+    cudaPointerAttributes at{};
+    cudaError_t pe = cudaPointerGetAttributes(&at, ptr);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();   // clear the error that the failed query recorded
+      c->err = std::string("ers_solve_dev_noalloc: cannot query a buffer: ") +
+               cudaGetErrorString(pe);
+      return ERS_ERR_INVALID;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        at.device != c->device) {
+      c->err = "ers_solve_dev_noalloc: b_dev and x_dev must be device memory of device " +
+               std::to_string(c->device);
+      return ERS_ERR_INVALID;
+    }
   }
   if (c->plan.nsn > NOALLOC_MAX_SN) {
     c->err = "ers_solve_dev_noalloc: the factor has " + std::to_string(c->plan.nsn) +

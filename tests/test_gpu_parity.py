@@ -388,6 +388,24 @@ def test_adaptive_run_matches_oracle(ers):
     sim.close()
 
 
+def test_adaptive_erc_run_with_rejections_matches_oracle(ers):
+    """ER-C inside Algorithm 2 with rejected tries on PWL-ramp steps: every rejection
+    re-exponentiates the solution bases (v1 and, on a ramp, v2) at the smaller h, so the
+    correction's own basis must not share their storage.  Per-node agreement with the
+    oracle's adaptive ER-C run and matching step counts."""
+    circ = S.inverter_chain(stages=4, tree_nodes=10, seed=6, t_end=0.2e-9)
+    sim = make(ers, circ, correction=1, h_max=5e-12)
+    sim.dc()
+    ns, nr = sim.run(circ.t_end, 1e-6)
+    _, xg, _ = sim.state()
+    xr, tr, st = O.er_run(circ, tol=1e-6, opts=O.Options(correction=True, h_max=5e-12))
+    assert st.rejects > 0 and nr > 0
+    assert abs(ns - st.steps) <= max(2, 0.05 * st.steps), (ns, st.steps)
+    assert abs(nr - st.rejects) <= max(2, 0.05 * st.rejects), (nr, st.rejects)
+    assert np.max(np.abs(xg - xr)) <= 2e-6 * max(1.0, np.max(np.abs(xr)))
+    sim.close()
+
+
 # --- boundary behaviour ------------------------------------------------------------------
 def test_bounded_wait_reports_timeout(ers):
     """Failure detection without a GPU fault: a device wait on a flag that nothing sets gives
