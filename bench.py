@@ -39,7 +39,7 @@ CLOCKS_DIR = os.environ.get("ERS_CLOCKS_DIR") or os.path.join(ROOT, ".bench")   
 L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
 FLUSH_BYTES = 256 * 2 ** 20
 SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same generator
-SAMPLE_STEPS = 10
+SAMPLE_STEPS = 40
 
 
 def parse():
@@ -164,15 +164,15 @@ def run_oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE, kind="mesh", stages=
             if kind == "mesh" else
             f"the {stages}-stage chain ({r['n']} nodes, same generator and seed) from DC")
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"first {r['steps']} adaptive ER steps of {what}, SuperLU + numpy, "
-                       f"1 thread, {r['seconds']:.1f} s; steps/s on the sample, not scaled "
-                       f"to the full workload"),
+            "sample": (f"first {r['steps']} adaptive ER steps of {what}, the oracle's own "
+                       f"sparse LU + numpy, 1 thread, {r['seconds']:.1f} s; steps/s on the "
+                       f"sample, not scaled to the full workload"),
             "krylov_vectors_per_s": r["krylov"] / r["seconds"]}
 
 
 # --------------------------------------------------------------------------------------
 def oracle_args(a):
-    """(steps, size, kind, stages) of the bounded oracle sample: 10 steps of a 24^3 mesh, or
+    """(steps, size, kind, stages) of the bounded oracle sample: 40 steps of a 24^3 mesh, or
     100 steps of a 100-stage chain (about 10 s of one host core each)."""
     if a.workload == "chain":
         return 100, SAMPLE_SIZE, "chain", 100

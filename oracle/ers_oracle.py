@@ -10,12 +10,15 @@ the seeded netlist generator in synth/, which holds none of the method's arithme
 Paper: Zhuang, Yu, Kang, Wang, Cheng, "An Algorithmic Framework for Efficient Large-Scale
 Circuit Simulation Using Exponential Integrators", DAC 2015 (arXiv 1511.04515).
 
-Each function cites the passage it follows.  Library primitives serve as single steps:
-scipy.sparse.linalg.splu (sparse LU with partial pivoting, used for every G_k^{-1} b) and
-scipy.linalg.expm (dense exponential of the small matrix h H_m^{-1}).  The remaining
-arithmetic is written out in the paper's order and notation.
+Each function cites the passage it follows.  The oracle's own pieces: the sparse LU of G_k
+(oracle/olu.c via oracle/sparse_lu.py: minimum-degree ordering, left-looking LU with
+threshold partial pivoting), the dense exponential of h H_m^{-1} (scaling and squaring of the
+[13/13] Pade approximant, Higham 2005; the paper's "scaling and squaring" step) and a dense LU
+with partial pivoting for H_m^{-1} and the Pade denominator.  The singular-C branch uses scipy's ordered Schur form and
+Sylvester solver as single library steps.  The remaining arithmetic is written out in the
+paper's order and notation.
 
-Readings of points the paper leaves open (all listed in the design doc's readings table):
+Readings of points the paper leaves open:
   * F(x) is the Rosenbrock remainder with the device Jacobian frozen at x_k:
     F(x) = G_dev,k x - i_dev(x), so that -G_k x + F(x) = -G_lin x - i_dev(x).
   * Dq/dt = C x' with a constant linear C (grounded capacitors).
@@ -34,13 +37,15 @@ Readings of points the paper leaves open (all listed in the design doc's readings tab
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 from typing import List, Optional
 
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
-import scipy.sparse.linalg as spla
+
+from oracle.sparse_lu import SparseLU
 
 GROUND = -1
 VDD = -2
@@ -142,13 +147,80 @@ def linearize(circ, x) -> Linearization:
         idev, Gdev = np.zeros(circ.n), sp.csr_matrix((circ.n, circ.n))
     Gk = (circ.G + Gdev).tocsc()
     F = Gdev @ x - idev
-    lu = spla.splu(Gk)
+    lu = SparseLU(Gk)
     return Linearization(x=x.copy(), Gdev=Gdev, Gk=Gk.tocsr(), F=F, lu=lu)
 
 
 # ----------------------------------------------------------------------------------------
 # Small dense matrix functions (Sec. IV, Eq. 14 and the residual of Eq. 16).
 # ----------------------------------------------------------------------------------------
+def dense_lu_solve(A, B):
+    """X = A^{-1} B by Gaussian elimination with partial pivoting (row interchanges to the
+    largest remaining entry of each column).  A: m x m, B: m x k; real or complex."""
+    A = np.array(A, dtype=np.result_type(A, B, np.float64))
+    X = np.array(B, dtype=A.dtype).reshape(A.shape[0], -1)
+    m = A.shape[0]
+    for k in range(m):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        if A[p, k] == 0:
+            raise ZeroDivisionError("singular matrix")
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+            X[[k, p]] = X[[p, k]]
+        f = A[k + 1:, k] / A[k, k]
+        A[k + 1:, k:] -= np.outer(f, A[k, k:])
+        X[k + 1:] -= np.outer(f, X[k])
+    for k in range(m - 1, -1, -1):
+        X[k] = (X[k] - A[k, k + 1:] @ X[k + 1:]) / A[k, k]
+    return X.reshape(np.shape(B))
+
+
+def _pade_coefficients(q):
+    """c_j = (2q - j)! q! / ((2q)! j! (q - j)!), the numerator of the [q/q] Pade approximant
+    of e^z (the denominator is the same polynomial at -z)."""
+    return [math.factorial(2 * q - j) * math.factorial(q) /
+            (math.factorial(2 * q) * math.factorial(j) * math.factorial(q - j))
+            for j in range(q + 1)]
+
+
+PADE13 = _pade_coefficients(13)
+THETA13 = 5.371920351148152   # largest ||A||_1 with [13/13] backward error <= 2^-53 (Higham 2005)
+
+
+def expm_pade13(A):
+    """e^A by scaling and squaring of the diagonal [13/13] Pade approximant (N. J. Higham,
+    "The scaling and squaring method for the matrix exponential revisited", SIAM J. Matrix
+    Anal. Appl. 26, 2005): s = max(0, ceil(log2(||A||_1 / theta_13))), X = A / 2^s,
+    U = X [X6 (c13 X6 + c11 X4 + c9 X2) + c7 X6 + c5 X4 + c3 X2 + c1 I],
+    V = X6 (c12 X6 + c10 X4 + c8 X2) + c6 X6 + c4 X4 + c2 X2 + c0 I,
+    e^X ~ (V - U)^-1 (V + U), then squared s times."""
+    A = np.asarray(A)
+    m = A.shape[0]
+    dt = np.result_type(A, np.float64)
+    if m == 0:
+        return np.zeros((0, 0), dtype=dt)
+    nrm = float(np.max(np.sum(np.abs(A), axis=0)))
+    if not np.isfinite(nrm):
+        return np.full(A.shape, np.nan, dtype=dt)
+    s = max(0, int(np.ceil(np.log2(nrm / THETA13)))) if nrm > THETA13 else 0
+    s = min(s, 1000)
+    X = np.ldexp(A.real, -s) + 1j * np.ldexp(A.imag, -s) if np.iscomplexobj(A) \
+        else np.ldexp(A, -s)
+    c = PADE13
+    I = np.eye(m, dtype=dt)
+    X2 = X @ X
+    X4 = X2 @ X2
+    X6 = X4 @ X2
+    U = X @ (X6 @ (c[13] * X6 + c[11] * X4 + c[9] * X2) + c[7] * X6 + c[5] * X4
+             + c[3] * X2 + c[1] * I)
+    V = X6 @ (c[12] * X6 + c[10] * X4 + c[8] * X2) + c[6] * X6 + c[4] * X4 + c[2] * X2 \
+        + c[0] * I
+    E = dense_lu_solve(V - U, V + U)
+    for _ in range(s):
+        E = E @ E
+    return E
+
+
 ALGEBRAIC_EXPONENT = 700.0   # e^{-700} ~ 1e-304: below it e^{h/mu} is zero in FP64
 
 
@@ -168,18 +240,19 @@ def exp_hinv_e1(Hm, h, singular_c=False):
     m = Hm.shape[0]
     tau = h / ALGEBRAIC_EXPONENT
     if not singular_c or np.all(np.abs(np.linalg.eigvals(Hm)) > tau):
-        Hinv = np.linalg.solve(Hm, np.eye(m))
-        E = sla.expm(h * Hinv)
+        Hinv = dense_lu_solve(Hm, np.eye(m))
+        with np.errstate(over="ignore", invalid="ignore"):
+            E = expm_pade13(h * Hinv)
         y = E[:, 0].copy()
         return y, float((Hinv @ y)[m - 1])
     T, Z, s = sla.schur(Hm.astype(complex), output="complex", sort=lambda mu: abs(mu) > tau)
     if s == 0:
         return np.zeros(m), 0.0
     T11, T12, T22 = T[:s, :s], T[:s, s:], T[s:, s:]
-    T11inv = np.linalg.solve(T11, np.eye(s))
+    T11inv = dense_lu_solve(T11, np.eye(s, dtype=complex))
     fT = np.zeros((m, m), complex)
     gT = np.zeros((m, m), complex)
-    fT[:s, :s] = sla.expm(h * T11inv)
+    fT[:s, :s] = expm_pade13(h * T11inv)
     gT[:s, :s] = T11inv @ fT[:s, :s]
     fT[:s, s:] = sla.solve_sylvester(T11, -T22, fT[:s, :s] @ T12)
     gT[:s, s:] = sla.solve_sylvester(T11, -T22, gT[:s, :s] @ T12)
@@ -443,7 +516,7 @@ class RunStats:
 def er_run(circ, t_end=None, tol=1e-6, opts: Options = None, x0=None, max_steps=10 ** 7,
            trace=False):
     """Adaptive ER / ER-C transient of Algorithm 2 from the DC solution to t_end.
-    One LU per step; a rejected step shrinks h by alpha and reuses the Krylov bases of
+    One LU per step (a linear circuit keeps its single LU of G); a rejected step shrinks h by alpha and reuses the Krylov bases of
     the solution (no new LU, no new basis for v1/v2, same m; only exp(h H_m^{-1}) is
     re-evaluated); h grows by beta when i < i_grow."""
     opts = opts or Options()
@@ -456,12 +529,18 @@ def er_run(circ, t_end=None, tol=1e-6, opts: Options = None, x0=None, max_steps=
     t = 0.0
     stats = RunStats()
     C = circ.C
+    lin = None
     while t < t_end * (1 - 1e-12) and stats.steps < max_steps:
         nb = bps[bps > t * (1 + 1e-14) + 1e-30]
         t_next = min(nb[0], t_end) if nb.size else t_end
         h = min(h_prop, h_max, t_next - t)
-        lin = linearize(circ, x)
-        stats.lu += 1
+        if lin is None or circ.dev.size:
+            # one LU of G_k per step; a linear circuit has G_k = G_lin at every step, so its
+            # single factorisation is kept (the same factors a refactor would produce)
+            lin = linearize(circ, x)
+            stats.lu += 1
+        else:
+            lin = Linearization(x=x.copy(), Gdev=lin.Gdev, Gk=lin.Gk, F=lin.F, lu=lin.lu)
         st = step_setup(circ, lin, t, pwl_slope(circ, t, h))
         if opts.combined:
             st.v1 = st.v1 + st.v2
@@ -521,7 +600,7 @@ def be_run(circ, h, t_end=None, x0=None, newton_tol=1e-12, max_newton=50, record
                 idev, Gdev = np.zeros(circ.n), sp.csr_matrix((circ.n, circ.n))
             T = Ch @ (x - xk) + circ.G @ x + idev - bu
             Jac = (Ch + circ.G + Gdev).tocsc()
-            dx = spla.splu(Jac).solve(-T)
+            dx = SparseLU(Jac).solve(-T)
             x = x + dx
             if np.max(np.abs(dx)) <= newton_tol * max(1.0, np.max(np.abs(x))):
                 break
