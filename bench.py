@@ -9,6 +9,7 @@ phi_2 Krylov spaces, the update, the controller).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch      (batched Monte Carlo inverter chains, plain vs learned)
+  python bench.py --workload solve --size 70   (the supernodal solves alone, for profiling)
 
 Prints one JSON line (rank 0).  The value is accepted ER steps per second of the whole job;
 N > 1 runs independent replicas (a single circuit does not shard: every G^-1 couples all
@@ -52,7 +53,9 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--workload", default="mesh", choices=["mesh", "chain", "batch"])
+    p.add_argument("--workload", default="mesh", choices=["mesh", "chain", "batch", "solve"])
+    p.add_argument("--ordering", type=int, default=0, help="ers_opts.ordering (0 or 1)")
+    p.add_argument("--nrhs", type=int, default=2, help="solve: right-hand sides per pass")
     p.add_argument("--stages", type=int, default=2000, help="chain: inverter stages")
     p.add_argument("--batch-n", type=int, default=64, help="batch: instances")
     p.add_argument("--stage-lo", type=int, default=4)
@@ -229,7 +232,7 @@ def run_ours(a):
     kind = "chain" if a.workload == "chain" else "mesh"
     circ = workload(a.size, kind, a.stages)
     t_end = workload_t_end(kind)
-    opts = ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100)
+    opts = ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100, ordering=a.ordering)
     tc = time.perf_counter()
     sim = ers.Simulator.from_circuit(circ, opts=opts)
     create_s = time.perf_counter() - tc
@@ -372,6 +375,48 @@ def run_ours(a):
             line["cpu_baseline"] = run_oracle_sample(*oracle_args(a))
         except Exception as ex:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "error": str(ex)[-300:]}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
+# --------------------------------------------------------------------------------------
+# the triangular solves alone: G_k x = b passes over the factor of a 3D mesh (for timing and
+# profiling the solve kernels in isolation; not the metric's workload)
+# --------------------------------------------------------------------------------------
+def run_solve_workload(a):
+    import numpy as np
+    import torch
+    from paper_1511_04515_gb300 import build
+    build.build()
+    from paper_1511_04515_gb300 import ers
+    circ = workload(a.size, "mesh")
+    tc = time.perf_counter()
+    sim = ers.Simulator.from_circuit(circ, opts=ers.make_opts(ordering=a.ordering))
+    create_s = time.perf_counter() - tc
+    sim.set_state(0.0, np.zeros(circ.n))
+    tf = time.perf_counter()
+    sim.refactor()
+    factor_s = time.perf_counter() - tf
+    for _ in range(max(1, a.warmup)):
+        sim.solve(np.ones(circ.n))
+    chosen, ms = sim.autotune(nrhs=a.nrhs, passes=max(1, a.steps))
+    b = np.random.default_rng(0).normal(size=circ.n)
+    x = sim.solve(b)
+    G = circ.G.tocsr()
+    eta = float(np.max(np.abs(G @ x - b)) /
+                (abs(G).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    st = sim.stats()
+    best = min(ms)
+    fma = st["solve_fma_per_rhs"] * a.nrhs
+    line = {"workload": f"solve passes, rc3d_{a.size}^3 mesh ({circ.n} nodes), "
+                        f"ordering {a.ordering}, {a.nrhs} right-hand sides",
+            "ms_per_pass_at_1_2_3_ctas_per_sm": ms, "chosen_ctas_per_sm": chosen,
+            "fp64_tflops": 2 * fma / (best * 1e-3) / 1e12,
+            "hbm_GBps": (st["solve_bytes_per_pass"] + 16.0 * circ.n * a.nrhs) / (best * 1e-3) / 1e9,
+            "fma_per_pass": fma, "bytes_per_pass": st["solve_bytes_per_pass"],
+            "nnz_L": st["nnz_L"], "nsn": st["nsn"], "factor_doubles": st["factor_doubles"],
+            "create_s": create_s, "refactor_s": factor_s, "backward_error": eta,
+            "passes_timed": a.steps}
     print(json.dumps(line), flush=True)
     sim.close()
 
@@ -605,6 +650,8 @@ def main():
         run_reference(a)
     elif a.workload == "batch":
         run_batch_workload(a)
+    elif a.workload == "solve":
+        run_solve_workload(a)
     else:
         run_ours(a)
 

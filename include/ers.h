@@ -17,8 +17,10 @@
  *  - Every call returns an ers_status and never aborts the process; on failure
  *    ers_last_error() returns a message.  No call traps or hangs the GPU: device-side
  *    waits are bounded and report ERS_ERR_TIMEOUT.
- *  - A context is bound to the CUDA device that was current at ers_create and to one
- *    CUDA stream (ers_set_stream); calls on one context must not overlap.
+ *  - A context is bound to one CUDA device (the first entry of the device list given at
+ *    creation, or the device current then) and to one CUDA stream (ers_set_stream).  Every
+ *    call makes the context's device current for its duration and restores the caller's
+ *    current device before returning.  Calls on one context must not overlap.
  */
 #ifndef ERS_H
 #define ERS_H
@@ -123,16 +125,21 @@ typedef struct {
 ers_status ers_default_opts(ers_opts* opts);
 
 /* Create a simulation context (Alg. 2 "initialization phase": load netlist, build linear
- * matrices).  G_lin, C: n x n; B: n x p; dev: ndev MOSFETs (may be NULL if ndev = 0);
- * u: p PWL inputs.  Performs the one-time symbolic analysis of G_k's pattern (the union of
- * G_lin and the device stamps) and allocates device memory.  The state starts at t = 0,
- * x = 0; call ers_dc for the DC operating point.  opts may be NULL (defaults).
+ * matrices; Sec. II problem statement C x' + G x + i(x) = B u).  G_lin, C: n x n; B: n x p;
+ * dev: ndev MOSFETs (may be NULL if ndev = 0); u: p PWL inputs.  devices / ndevices: the
+ * CUDA device list; ndevices = 0 (devices may be NULL) uses the current device, 1 uses
+ * devices[0]; a single circuit does not shard (every G_k^-1 of Algorithm 1 couples all of its
+ * nodes), so ndevices > 1 is ERS_ERR_INVALID -- create one context per device for replicas.
+ * A device id that does not exist is ERS_ERR_INVALID.  Performs the one-time symbolic
+ * analysis of G_k's pattern (the union of G_lin and the device stamps) and allocates device
+ * memory.  The state starts at t = 0, x = 0; call ers_dc for the DC operating point.
+ * opts may be NULL (defaults).
  * Every node needs a capacitance (a nonzero entry in its row of C): a node without one
  * makes C singular and H_m of Eq. 14 singular with it, which the small dense stage does not
  * handle; such a C is refused with ERS_ERR_INVALID before any device work. */
 ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, const ers_csr* B,
                       const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
-                      const ers_opts* opts);
+                      const int32_t* devices, int32_t ndevices, const ers_opts* opts);
 
 /* Batched context over ninst independent circuits (Monte Carlo corners, parameter sweeps;
  * the paper simulates one circuit at a time).  The instances are concatenated into one
@@ -140,9 +147,19 @@ ers_status ers_create(ers_ctx** out, const ers_csr* G_lin, const ers_csr* C, con
  * cover all of them, while Algorithm 1 and 2 run per instance (own Krylov spaces and
  * dimensions, step sizes, times, PWL corners and error tests).  State access: ers_dc,
  * ers_set_state / ers_get_state act on the concatenated vector (instance k's nodes follow
- * instance k-1's); ers_get_state_inst reads one instance. */
+ * instance k-1's); ers_get_state_inst reads one instance.
+ * devices / ndevices: the CUDA device list (0 = the current device).  With ndevices > 1 the
+ * instances are split over the listed devices by longest-processing-time-first
+ * (ers_partition_lpt) on the estimated cost nnz(G_lin) + n + 6 ndev of each instance, with no
+ * exchange between devices on the data path: each share is a batched context of its own on
+ * its device, shares on different devices run concurrently (one host thread per device),
+ * shares listed on the same device one after the other, and every call gathers per-instance
+ * results on the host in input order.  Such a context refuses ers_set_stream, ers_mevp,
+ * ers_solve_dev_noalloc and the _dev state calls (ERS_ERR_INVALID); ers_stats adds the
+ * shares' counters (steps: the largest share's rounds); a network given to
+ * ers_batch_set_controller is copied once per share. */
 ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
-                            const ers_opts* opts);
+                            const int32_t* devices, int32_t ndevices, const ers_opts* opts);
 /* (opts->correction and opts->combined_vector are single-context options: ERS_ERR_INVALID
  * here.  ers_step / ers_run on a batched context return ERS_ERR_INVALID: it steps with
  * ers_run_batch.) */
@@ -404,6 +421,13 @@ enum { ERS_PLAN_PERM = 0, ERS_PLAN_SN_START, ERS_PLAN_SN_PARENT, ERS_PLAN_LEVEL,
        ERS_PLAN_FRONT_OFF, ERS_PLAN_ASM_DST, ERS_PLAN_ARENA };
 ers_status ers_plan_array(const ers_csr* pattern, const ers_opts* opts, int32_t which, void* out,
                           int64_t* len);
+
+/* Host-only: longest-processing-time-first partition of n jobs with costs cost[i] >= 0 over
+ * nparts >= 1 parts (the device split of ers_create_batch): jobs by decreasing cost (ties:
+ * lower index first) each onto the least-loaded part (ties: lower part), which keeps the
+ * largest load within (4/3 - 1/(3 nparts)) of the optimum (Graham 1969).  part_of receives
+ * n part numbers.  ERS_ERR_INVALID for a negative or non-finite cost. */
+ers_status ers_partition_lpt(const double* cost, int32_t n, int32_t nparts, int32_t* part_of);
 
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);

@@ -777,15 +777,25 @@ extern "C" {
 
 ers_status ers_create(ers_ctx** out, const ers_csr* G, const ers_csr* C, const ers_csr* B,
                       const ers_mosfet* dev, int32_t ndev, const ers_pwl* u, int32_t p,
-                      const ers_opts* opts) {
+                      const int32_t* devices, int32_t ndevices, const ers_opts* opts) {
   if (!out) return ERS_ERR_INVALID;
   ers_ctx* c = new ers_ctx();
   *out = c;
+  std::string bad = check_device_list(devices, ndevices);
+  if (!bad.empty()) return fail(c, ERS_ERR_INVALID, bad);
+  if (ndevices > 1)
+    return fail(c, ERS_ERR_INVALID,
+                "a single circuit does not shard (every G_k^-1 couples all nodes): give one "
+                "device, and create one context per device for replicas");
+  DeviceGuard dg(ndevices == 1 ? devices[0] : -1);
   return ers::create_context(c, G, C, B, dev, ndev, u, p, opts);
 }
 
 ers_status ers_set_stream(ers_ctx* c, void* stream) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return fail(c, ERS_ERR_INVALID, "a batch over several devices has one stream per device");
+  DeviceGuard dg(c->device);
   if (stream) {
     c->stream = (cudaStream_t)stream;   // the caller's; never destroyed by the library
   } else {
@@ -797,6 +807,8 @@ ers_status ers_set_stream(ers_ctx* c, void* stream) {
 
 ers_status ers_refactor(ers_ctx* c) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_call(c, [](ers_ctx* s, int) { return ers_refactor(s); });
+  DeviceGuard dg(c->device);
   ers_status st = clear_status(c);
   if (st != ERS_OK) return st;
   st = do_refactor(c);
@@ -835,6 +847,8 @@ static ers_status dc_newton(ers_ctx* c, double tol, int maxit, double* res) {
 
 ers_status ers_dc(ers_ctx* c, const double* x0) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_dc(c, x0);
+  DeviceGuard dg(c->device);
   ers_status st = clear_status(c);
   if (st != ERS_OK) return st;
   if (x0) {
@@ -894,7 +908,9 @@ static ers_status step_core(ers_ctx* c, double h, int32_t m, int32_t* m_used, do
 
 ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* err_inf) {
   if (!c) return ERS_ERR_INVALID;
-  if (c->bks) return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
+  if (c->bks || c->is_group())
+    return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
+  DeviceGuard dg(c->device);
   ers_status st = step_core(c, h, m, m_used, err_inf);
   if (st != ERS_OK) return st;
   CU(cudaMemcpyAsync(c->x, c->xnew, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
@@ -908,7 +924,9 @@ ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* er
 ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int32_t* nsteps,
                    int32_t* nreject) {
   if (!c) return ERS_ERR_INVALID;
-  if (c->bks) return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
+  if (c->bks || c->is_group())
+    return fail(c, ERS_ERR_INVALID, "a batched context steps with ers_run_batch");
+  DeviceGuard dg(c->device);
   if (!(t_end > c->t)) return fail(c, ERS_ERR_INVALID, "t_end must exceed the current time");
   if (!(tol > 0.0)) return fail(c, ERS_ERR_INVALID, "tol must be positive");
   const ers_opts& o = c->opts;
@@ -978,6 +996,8 @@ ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int3
 ers_status ers_get_state(const ers_ctx* cc, double* t, double* x, double* h) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_get_state(c, t, x, h);
+  DeviceGuard dg(c->device);
   if (t) *t = c->t;
   if (h) *h = c->h;
   if (x) {
@@ -991,6 +1011,8 @@ ers_status ers_get_state(const ers_ctx* cc, double* t, double* x, double* h) {
 
 ers_status ers_set_state(ers_ctx* c, double t, const double* x, double h) {
   if (!c || !x) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_set_state(c, t, x, h);
+  DeviceGuard dg(c->device);
   if (!std::isfinite(t) || !std::isfinite(h)) return fail(c, ERS_ERR_NONFINITE, "non-finite t or h");
   std::vector<double> xp(c->n);
   for (int k = 0; k < c->n; ++k) {
@@ -1011,6 +1033,10 @@ ers_status ers_set_state(ers_ctx* c, double t, const double* x, double h) {
 ers_status ers_get_state_dev(const ers_ctx* cc, double* x_dev) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c || !x_dev) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return fail(c, ERS_ERR_INVALID, "device buffers of a batch over several devices: use the "
+                                    "host state calls");
+  DeviceGuard dg(c->device);
   // scatter back to the original order on the device
   k_permute<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->d_perm, c->x, x_dev, 1);
   c->stats.kernel_launches++;
@@ -1020,6 +1046,10 @@ ers_status ers_get_state_dev(const ers_ctx* cc, double* x_dev) {
 
 ers_status ers_set_state_dev(ers_ctx* c, double t, const double* x_dev, double h) {
   if (!c || !x_dev) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return fail(c, ERS_ERR_INVALID, "device buffers of a batch over several devices: use the "
+                                    "host state calls");
+  DeviceGuard dg(c->device);
   k_permute<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->d_perm, x_dev, c->x, 0);
   c->stats.kernel_launches++;
   CU(cudaGetLastError());
@@ -1049,6 +1079,8 @@ static ers_status from_dev_perm(ers_ctx* c, const double* dev, double* host) {
 
 ers_status ers_solve(ers_ctx* c, const double* b, double* x) {
   if (!c || !b || !x) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_apply(c, b, x, true);
+  DeviceGuard dg(c->device);
   ers_status st = clear_status(c);
   if (st != ERS_OK) return st;
   if (!c->factored) {
@@ -1065,6 +1097,8 @@ ers_status ers_solve(ers_ctx* c, const double* b, double* x) {
 
 ers_status ers_spmv_C(ers_ctx* c, const double* v, double* y) {
   if (!c || !v || !y) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_apply(c, v, y, false);
+  DeviceGuard dg(c->device);
   ers_status st = to_dev_perm(c, v, c->tmp);
   if (st != ERS_OK) return st;
   launch_spmv(c, c->C_ptr, c->C_idx, c->C_val, c->tmp, c->rhs, 1.0);
@@ -1074,6 +1108,8 @@ ers_status ers_spmv_C(ers_ctx* c, const double* v, double* y) {
 
 ers_status ers_mevp(ers_ctx* c, const double* v, double h, int32_t m, double* out, int32_t* m_used) {
   if (!c || !v || !out) return ERS_ERR_INVALID;
+  if (c->is_group()) return fail(c, ERS_ERR_INVALID, "ers_mevp takes a single circuit");
+  DeviceGuard dg(c->device);
   if (!(h > 0.0)) return fail(c, ERS_ERR_INVALID, "h must be positive");
   if (m < 0 || m > MAX_M) return fail(c, ERS_ERR_INVALID, "m must be in 0..64");
   ers_status st = clear_status(c);
@@ -1104,7 +1140,12 @@ ers_status ers_mevp(ers_ctx* c, const double* v, double h, int32_t m, double* ou
 ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, double h, double* y,
                          double* last) {
   if (!c || !H || !y || !last) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return group_call(c, [&](ers_ctx* s, int q) {
+      return q == 0 ? ers_phi_small(s, H, ldh, m, h, y, last) : ERS_OK;
+    });
   if (m < 1 || m > MAX_M || ldh < m) return fail(c, ERS_ERR_INVALID, "bad m / ldh");
+  DeviceGuard dg(c->device);
   struct DevBuf {   // freed on every return path
     double* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
@@ -1124,6 +1165,17 @@ ers_status ers_phi_small(ers_ctx* c, const double* H, int32_t ldh, int32_t m, do
 
 ers_status ers_wait_selftest(ers_ctx* c) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) {
+    ers_status worst = ERS_OK;
+    ers_status st = group_call(c, [&](ers_ctx* s, int) {
+      ers_status r = ers_wait_selftest(s);
+      if (r != ERS_ERR_TIMEOUT) worst = r == ERS_OK ? ERS_ERR_INVALID : r;
+      return ERS_OK;
+    });
+    if (st != ERS_OK) return st;
+    return worst == ERS_OK ? ERS_ERR_TIMEOUT : worst;
+  }
+  DeviceGuard dg(c->device);
   ers_status st = clear_status(c);
   if (st != ERS_OK) return st;
   // the flag: a zeroed word of the device reduction scratch that no kernel is using now
@@ -1138,6 +1190,11 @@ ers_status ers_wait_selftest(ers_ctx* c) {
 
 ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())    // every share tunes its own solves; ms and chosen report the first
+    return group_call(c, [&](ers_ctx* s, int q) {
+      return ers_autotune(s, nrhs, passes, q == 0 ? ms : nullptr, q == 0 ? chosen : nullptr);
+    });
+  DeviceGuard dg(c->device);
   if (nrhs < 1 || nrhs > MAX_RHS || passes < 1)
     return fail(c, ERS_ERR_INVALID, "autotune: nrhs in 1..3 and passes >= 1");
   ers_status st = clear_status(c);
@@ -1183,6 +1240,8 @@ ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, in
 ers_status ers_stats(const ers_ctx* cc, ers_stats_t* out) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c || !out) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_stats(c, out);
+  DeviceGuard dg(c->device);
   CU(cudaStreamSynchronize(c->stream));
   for (auto& ev : c->ev_used) {
     float ms = 0.f;
@@ -1196,6 +1255,9 @@ ers_status ers_stats(const ers_ctx* cc, ers_stats_t* out) {
 
 ers_status ers_profile(ers_ctx* c, int32_t enable) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return group_call(c, [&](ers_ctx* s, int) { return ers_profile(s, enable); });
+  DeviceGuard dg(c->device);
   ers_stats_t tmp;
   ers_status st = ers_stats(c, &tmp);
   if (st != ERS_OK) return st;
@@ -1279,6 +1341,12 @@ ers_status ers_solve_plan_check(const ers_csr* pat, const ers_opts* opts, int64_
 
 void ers_destroy(ers_ctx* c) {
   if (!c) return;
+  if (c->is_group()) {
+    group_destroy(c);
+    delete c;
+    return;
+  }
+  DeviceGuard dg(c->device);
   auto f = [](void* p) { if (p) cudaFree(p); };
   DevicePlan& P = c->plan;
   for (void* p : {(void*)P.sn_start, (void*)P.sn_parent, (void*)P.rows, (void*)P.rel, (void*)P.rptr,

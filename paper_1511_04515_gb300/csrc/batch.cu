@@ -627,10 +627,9 @@ double next_bp(const std::vector<double>& bp, double t) {
 
 }  // namespace
 
-extern "C" {
-
-ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
-                            const ers_opts* opts) {
+// A batched context of ninst instances on the current device.
+ers_status ers::create_batch_here(ers_ctx** out, const ers_instance* inst, int32_t ninst,
+                                  const ers_opts* opts) {
   if (!out) return ERS_ERR_INVALID;
   ers_ctx* c = new ers_ctx();
   *out = c;
@@ -773,9 +772,32 @@ ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t nin
   return ERS_OK;
 }
 
+extern "C" {
+
+ers_status ers_create_batch(ers_ctx** out, const ers_instance* inst, int32_t ninst,
+                            const int32_t* devices, int32_t ndevices, const ers_opts* opts) {
+  if (!out) return ERS_ERR_INVALID;
+  *out = nullptr;
+  std::string bad = check_device_list(devices, ndevices);
+  if (!bad.empty()) {
+    ers_ctx* c = new ers_ctx();
+    *out = c;
+    return ctx_fail(c, ERS_ERR_INVALID, bad);
+  }
+  if (ndevices > 1 && inst && ninst >= 1) {
+    ers_ctx* g = new ers_ctx();
+    *out = g;
+    return group_create(g, inst, ninst, devices, ndevices, opts);
+  }
+  DeviceGuard dg(ndevices == 1 ? devices[0] : -1);
+  return create_batch_here(out, inst, ninst, opts);
+}
+
 ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps,
                          int32_t* nsteps, int32_t* nreject) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_run_batch(c, t_end, tol, max_steps, nsteps, nreject);
+  DeviceGuard dg(c->device);
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   if (!(tol > 0.0)) return ctx_fail(c, ERS_ERR_INVALID, "tol must be positive");
   const int ninst = c->ninst, n = c->n;
@@ -991,6 +1013,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
 
 ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts, double margin) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_set_controller(c, mlp, parts, margin);
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   if (mlp && (parts & ~(ERS_CTRL_H | ERS_CTRL_M)) != 0)
     return ctx_fail(c, ERS_ERR_INVALID, "unknown controller parts");
@@ -1006,6 +1029,8 @@ ers_status ers_batch_set_controller(ers_ctx* c, ers_mlp* mlp, int32_t parts, dou
 
 ers_status ers_batch_set_graphs(ers_ctx* c, int32_t enable) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return group_call(c, [&](ers_ctx* s, int) { return ers_batch_set_graphs(s, enable); });
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   c->batch_graphs = enable != 0;
   return ERS_OK;
@@ -1013,6 +1038,8 @@ ers_status ers_batch_set_graphs(ers_ctx* c, int32_t enable) {
 
 ers_status ers_batch_trace(ers_ctx* c, int32_t enable) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return group_call(c, [&](ers_ctx* s, int) { return ers_batch_trace(s, enable); });
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   c->trace = enable != 0;
   for (auto& R : c->recs) R.clear();
@@ -1023,6 +1050,7 @@ ers_status ers_batch_records(const ers_ctx* cc, int32_t k, ers_step_record* out,
                              int32_t* count) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_records(c, k, out, cap, count);
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   if (k < 0 || k >= c->ninst) return ctx_fail(c, ERS_ERR_INVALID, "instance index out of range");
   const auto& R = c->recs[k];
@@ -1035,6 +1063,7 @@ ers_status ers_batch_records(const ers_ctx* cc, int32_t k, ers_step_record* out,
 ers_status ers_batch_samples(const ers_ctx* cc, float* X, float* T, int32_t cap, int32_t* count) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_samples(c, X, T, cap, count);
   if (!c->bks) return ctx_fail(c, ERS_ERR_INVALID, "context was not created by ers_create_batch");
   int64_t ns = 0;
   for (const auto& R : c->recs) {
@@ -1056,6 +1085,8 @@ ers_status ers_batch_samples(const ers_ctx* cc, float* X, float* T, int32_t cap,
 ers_status ers_batch_ctrl_stats(const ers_ctx* c, int64_t* proposals, int64_t* rejected,
                                 int64_t* krylov_vectors) {
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group())
+    return group_ctrl_stats(const_cast<ers_ctx*>(c), proposals, rejected, krylov_vectors);
   if (proposals) *proposals = c->ctrl_proposals;
   if (rejected) *rejected = c->ctrl_rejected;
   if (krylov_vectors) *krylov_vectors = c->stats.krylov_vectors;
@@ -1065,6 +1096,8 @@ ers_status ers_batch_ctrl_stats(const ers_ctx* c, int64_t* proposals, int64_t* r
 ers_status ers_get_state_inst(const ers_ctx* cc, int32_t k, double* t, double* x, double* h) {
   ers_ctx* c = const_cast<ers_ctx*>(cc);
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) return group_get_state_inst(c, k, t, x, h);
+  DeviceGuard dg(c->device);
   if (k < 0 || k >= c->ninst) return ctx_fail(c, ERS_ERR_INVALID, "instance index out of range");
   if (c->bks) {
     if (t) *t = c->t_inst[k];

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -86,6 +87,49 @@ ers_status ctx_fail(ers_ctx* c, ers_status st, const std::string& msg);
 ers_status ctx_refactor(ers_ctx* c);
 ers_status ctx_sync_status(ers_ctx* c);
 ers_status ctx_clear_status(ers_ctx* c);
+// batch.cu: a batched context on the current device
+ers_status create_batch_here(ers_ctx** out, const ers_instance* inst, int32_t ninst,
+                             const ers_opts* opts);
+
+// Makes `dev` the current device for the guard's lifetime and restores the caller's device
+// (dev < 0: no change).  Every public call on a context runs under one.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+      changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// devices.cu: a batch split over several devices (group context)
+// "" if the device list is usable: ndevices >= 0, ids valid on this machine, devices != NULL
+// when ndevices > 0
+std::string check_device_list(const int32_t* devices, int32_t ndevices);
+void lpt_partition(const double* cost, int n, int nparts, int32_t* part_of);
+ers_status group_create(ers_ctx* g, const ers_instance* inst, int32_t ninst,
+                        const int32_t* devices, int32_t ndevices, const ers_opts* opts);
+void group_destroy(ers_ctx* g);
+ers_status group_run_batch(ers_ctx* g, double t_end, double tol, int32_t max_steps,
+                           int32_t* nsteps, int32_t* nreject);
+ers_status group_dc(ers_ctx* g, const double* x0);
+ers_status group_set_state(ers_ctx* g, double t, const double* x, double h);
+ers_status group_get_state(ers_ctx* g, double* t, double* x, double* h);
+ers_status group_apply(ers_ctx* g, const double* b, double* x, bool solve);
+ers_status group_get_state_inst(ers_ctx* g, int32_t k, double* t, double* x, double* h);
+ers_status group_records(ers_ctx* g, int32_t k, ers_step_record* out, int32_t cap,
+                         int32_t* count);
+ers_status group_samples(ers_ctx* g, float* X, float* T, int32_t cap, int32_t* count);
+ers_status group_set_controller(ers_ctx* g, ers_mlp* mlp, int32_t parts, double margin);
+ers_status group_stats(ers_ctx* g, ers_stats_t* out);
+ers_status group_ctrl_stats(ers_ctx* g, int64_t* proposals, int64_t* rejected, int64_t* kv);
+// f(share, index) on every share with its device current (one host thread per device)
+ers_status group_call(ers_ctx* g, const std::function<ers_status(ers_ctx*, int)>& f);
 }  // namespace ers
 
 // the opaque context of the public C ABI
@@ -182,6 +226,16 @@ struct ers_ctx {
   int32_t* d_mused = nullptr;          // ninst
   double* bdf = nullptr;               // ninst
   float *d_feat = nullptr, *d_pred = nullptr;   // ninst x 32, ninst x 2
+  // a batch over several devices (ers_create_batch with ndevices > 1): the per-device batched
+  // contexts; this context holds no device memory and only dispatches
+  std::vector<ers_ctx*> group;
+  std::vector<int32_t> group_dev;                 // device of each share
+  std::vector<std::vector<int32_t>> group_inst;   // input-order instances of each share
+  std::vector<int32_t> inst_grp, inst_loc;        // share and local index of each instance
+  std::vector<int32_t> inst_n, inst_off;          // node count / offset of each instance
+  std::vector<ers_mlp*> group_nets;               // network copies, one per share (owned)
+  bool grouped = false;                           // set by group_create, even on failure
+  bool is_group() const { return grouped; }
   // profiling of the solve kernels (CUDA events on the context's stream)
   bool profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;

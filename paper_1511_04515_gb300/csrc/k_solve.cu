@@ -822,6 +822,10 @@ static int32_t* noalloc_scratch(int device, cudaError_t* err) {
 extern "C" ers_status ers_solve_dev_noalloc(ers_ctx* c, const double* b_dev, double* x_dev) {
   using namespace ers;
   if (!c) return ERS_ERR_INVALID;
+  if (c->is_group()) {
+    c->err = "ers_solve_dev_noalloc: takes a context on one device";
+    return ERS_ERR_INVALID;
+  }
   if (!b_dev || !x_dev) {
     c->err = "ers_solve_dev_noalloc: b_dev and x_dev must not be NULL";
     return ERS_ERR_INVALID;

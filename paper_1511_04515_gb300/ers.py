@@ -94,7 +94,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
            "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check",
-           "ers_wait_selftest", "ers_plan_array"]
+           "ers_wait_selftest", "ers_plan_array", "ers_partition_lpt"]
 
 _lib = None
 
@@ -114,7 +114,8 @@ def lib():
     sig = {
         "ers_default_opts": ([C.POINTER(Opts)], C.c_int),
         "ers_create": ([C.POINTER(P), C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr),
-                        C.POINTER(Mosfet), I32, C.POINTER(Pwl), I32, C.POINTER(Opts)], C.c_int),
+                        C.POINTER(Mosfet), I32, C.POINTER(Pwl), I32, pi, I32, C.POINTER(Opts)],
+                       C.c_int),
         "ers_set_stream": ([P, P], C.c_int),
         "ers_dc": ([P, pd], C.c_int),
         "ers_refactor": ([P], C.c_int),
@@ -133,7 +134,9 @@ def lib():
         "ers_wait_selftest": ([P], C.c_int),
         "ers_profile": ([P, I32], C.c_int),
         "ers_solve_dev_noalloc": ([P, P, P], C.c_int),
-        "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, C.POINTER(Opts)], C.c_int),
+        "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, pi, I32, C.POINTER(Opts)],
+                             C.c_int),
+        "ers_partition_lpt": ([pd, I32, I32, pi], C.c_int),
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(Stats), pi], C.c_int),
@@ -171,6 +174,28 @@ def lib():
         f.restype = res
     _lib = L
     return L
+
+
+def _device_list(devices):
+    """(int32 pointer or None, count) for a device list argument; keeps the array alive on
+    the returned pointer's _keep attribute."""
+    if not devices:
+        return None, 0
+    arr = np.ascontiguousarray(np.asarray(devices, np.int32))
+    ptr = arr.ctypes.data_as(C.POINTER(C.c_int32))
+    ptr._keep = arr
+    return ptr, int(arr.size)
+
+
+def partition_lpt(costs, nparts: int) -> np.ndarray:
+    """Part of each job under longest-processing-time-first over nparts parts (host-only;
+    the device split of ers_create_batch, see ers.h)."""
+    c = np.ascontiguousarray(np.asarray(costs, np.float64))
+    out = np.zeros(c.size, np.int32)
+    rc = lib().ers_partition_lpt(_dptr(c), int(c.size), int(nparts), _iptr(out))
+    if rc != 0:
+        raise ErsError(rc, "partition: costs must be finite and >= 0, nparts >= 1")
+    return out
 
 
 def _dptr(a: np.ndarray):
@@ -400,7 +425,7 @@ class Simulator:
     """One circuit on one GPU: C x' + G_lin x + i_dev(x) = B u(t) (see include/ers.h)."""
 
     def __init__(self, G, Cmat, B, dev=None, pwl: Sequence = (), opts: Optional[Opts] = None,
-                 stream=None):
+                 stream=None, device: Optional[int] = None):
         L = lib()
         n = G.shape[0]
         self.n = n
@@ -423,9 +448,10 @@ class Simulator:
             pw[q] = Pwl(int(tt.size), _dptr(tt), _dptr(vv))
         self.opts = opts if opts is not None else default_opts()
         self._ctx = C.c_void_p()
+        dl, nd = _device_list(None if device is None else [device])
         rc = L.ers_create(C.byref(self._ctx), C.byref(self._G.c), C.byref(self._C.c),
                           C.byref(self._B.c), devs if ndev else None, ndev,
-                          pw if p else None, p, C.byref(self.opts))
+                          pw if p else None, p, dl, nd, C.byref(self.opts))
         if rc != 0:
             msg = L.ers_last_error(self._ctx).decode() if self._ctx else ""
             if self._ctx:
@@ -436,8 +462,10 @@ class Simulator:
             self.set_stream(stream)
 
     @classmethod
-    def from_circuit(cls, circ, opts: Optional[Opts] = None, stream=None):
-        return cls(circ.G, circ.C, circ.B, circ.dev, circ.pwl, opts=opts, stream=stream)
+    def from_circuit(cls, circ, opts: Optional[Opts] = None, stream=None,
+                     device: Optional[int] = None):
+        return cls(circ.G, circ.C, circ.B, circ.dev, circ.pwl, opts=opts, stream=stream,
+                   device=device)
 
     def _check(self, rc):
         if rc != 0:
@@ -576,7 +604,10 @@ class BatchSimulator(Simulator):
     """Many independent circuits in one context (ers_create_batch): one refactor and one
     solve pass per step cover all of them; each keeps its own Algorithm-2 controller."""
 
-    def __init__(self, circuits, opts: Optional[Opts] = None, stream=None):
+    def __init__(self, circuits, opts: Optional[Opts] = None, stream=None,
+                 devices: Optional[Sequence[int]] = None):
+        """devices: the CUDA device list (None: the current device); with several entries
+        the instances are split over them by ers_partition_lpt (see ers.h)."""
         L = lib()
         self._parts = [_circuit_parts(c) for c in circuits]
         self.sizes = [pt["n"] for pt in self._parts]
@@ -589,7 +620,8 @@ class BatchSimulator(Simulator):
                                pt["pw"] if pt["p"] else None, pt["p"])
         self.opts = opts if opts is not None else default_opts()
         self._ctx = C.c_void_p()
-        rc = L.ers_create_batch(C.byref(self._ctx), inst, self.ninst, C.byref(self.opts))
+        dl, nd = _device_list(devices)
+        rc = L.ers_create_batch(C.byref(self._ctx), inst, self.ninst, dl, nd, C.byref(self.opts))
         if rc != 0:
             msg = L.ers_last_error(self._ctx).decode() if self._ctx else ""
             if self._ctx:

@@ -8,7 +8,6 @@ optimum.  A single circuit does not shard (every G^-1 couples all its nodes): re
 """
 from __future__ import annotations
 
-import heapq
 from typing import Callable, List, Sequence
 
 
@@ -19,18 +18,18 @@ def instance_cost(circ) -> float:
 
 
 def lpt_partition(costs: Sequence[float], nparts: int) -> List[List[int]]:
-    """Indices of `costs` split into nparts lists, largest first onto the least-loaded part;
-    each list is returned in increasing index order.  Ties go to the lowest part number."""
+    """Indices of `costs` split into nparts lists by the library's longest-processing-time-
+    first rule (ers_partition_lpt: largest first onto the least-loaded part, ties to the
+    lowest part number); each list is returned in increasing index order."""
     if nparts < 1:
         raise ValueError("nparts must be >= 1")
-    order = sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i))
-    heap = [(0.0, p) for p in range(nparts)]
+    from paper_1511_04515_gb300 import build, ers
+    build.build()                     # host-only entry point of the library
+    part = ers.partition_lpt(list(costs), nparts) if len(costs) else []
     parts: List[List[int]] = [[] for _ in range(nparts)]
-    for i in order:
-        load, p = heapq.heappop(heap)
-        parts[p].append(i)
-        heapq.heappush(heap, (load + float(costs[i]), p))
-    return [sorted(p) for p in parts]
+    for i, p in enumerate(part):
+        parts[int(p)].append(i)
+    return parts
 
 
 def run_sharded(circuits: Sequence, run: Callable[[Sequence], list], rank: int, world: int,

@@ -190,3 +190,51 @@ def test_gmin_option_default_and_validation(E):
         with pytest.raises(E.ErsError) as ei:
             E.Simulator.from_circuit(circ, opts=E.make_opts(gmin=bad))
         assert ei.value.status == 1 and "gmin" in str(ei.value)
+
+
+def _opt_makespan(costs, m):
+    """Smallest largest-part load over all assignments (brute force, tiny inputs)."""
+    import itertools
+    best = float("inf")
+    for assign in itertools.product(range(m), repeat=len(costs)):
+        loads = [0.0] * m
+        for c, p in zip(costs, assign):
+            loads[p] += c
+        best = min(best, max(loads))
+    return best
+
+
+def test_partition_lpt_rule_and_bound(E):
+    """ers_partition_lpt, the device split of ers_create_batch: the hand-worked LPT assignment
+    of a small case, and Graham's bound (4/3 - 1/(3m)) OPT against brute force."""
+    # costs 7, 5, 4, 3, 3, 2 over 2 parts, each onto the lighter part (loads in brackets):
+    # 7 -> 0 [7, 0]; 5 -> 1 [7, 5]; 4 -> 1 [7, 9]; 3 -> 0 [10, 9]; 3 -> 1 [10, 12];
+    # 2 -> 0 [12, 12]
+    part = E.partition_lpt([7, 5, 4, 3, 3, 2], 2)
+    assert part.tolist() == [0, 1, 1, 0, 1, 0]
+    rng = np.random.default_rng(4)
+    for trial in range(30):
+        m = int(rng.integers(2, 4))
+        costs = rng.integers(1, 20, size=int(rng.integers(1, 8))).astype(float)
+        part = E.partition_lpt(costs, m)
+        loads = np.bincount(part, weights=costs, minlength=m)
+        assert part.min() >= 0 and part.max() < m
+        assert loads.max() <= (4 / 3 - 1 / (3 * m)) * _opt_makespan(costs, m) + 1e-9
+    # ties: equal costs go to parts in order, lower index first
+    assert E.partition_lpt([1, 1, 1, 1], 3).tolist() == [0, 1, 2, 0]
+    with pytest.raises(E.ErsError):
+        E.partition_lpt([1.0, -1.0], 2)
+    with pytest.raises(E.ErsError):
+        E.partition_lpt([1.0], 0)
+
+
+def test_device_list_refusals_without_a_gpu(E):
+    """A single circuit refuses more than one device; a device id that does not exist (or no
+    device at all, as on a CPU-only host) is refused before any device work."""
+    c = S.rc_mesh_2d(4, 4, seed=1)
+    with pytest.raises(E.ErsError) as ei:
+        E.Simulator.from_circuit(c, device=10 ** 6)
+    assert ei.value.status == 1
+    with pytest.raises(E.ErsError) as ei:
+        E.BatchSimulator([c, c], devices=[0, 10 ** 6])
+    assert ei.value.status == 1
