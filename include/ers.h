@@ -108,6 +108,10 @@ typedef struct {
   double solve_bytes_per_pass; /* factor bytes one solve pair reads (values+indices)  */
   double solve_fma_per_rhs;    /* FP64 FMAs of one solve pair per right-hand side     */
   int64_t graph_launches;      /* CUDA graph launches (batched Arnoldi iterations)     */
+  int64_t merged_blocks;       /* dense separator triangles solved through their inverse */
+  int64_t merged_columns;      /* columns in those blocks                               */
+  int64_t merged_inverse_doubles; /* doubles of the two inverses (M_L and M_U)          */
+  double merged_inverse_flops; /* flops of computing the inverses after each refactor   */
 } ers_stats_t;
 
 /* One circuit of a batch (ers_create_batch): the same data ers_create takes. */
@@ -361,7 +365,7 @@ ers_status ers_phi_small(ers_ctx* ctx, const double* H, int32_t ldh, int32_t m, 
  * device memory is owned by a framework's pool allocator (memory the pool did not hand out
  * breaks its accounting), and latency-bound loops that forbid allocator calls (cudaMalloc
  * and cudaFree can synchronise the device and take unbounded time).  It calls no
- * cudaMalloc/cudaFree: the solve kernels' scratch (dependency counters) is a fixed 6 MiB
+ * cudaMalloc/cudaFree: the solve kernels' scratch (dependency counters) is a fixed 12 MiB
  * static device array of the library, shared by every call on a device and held by every
  * GPU that loads the library until exit.  Limits and rules: contexts whose factor has more
  * than 524288 supernodes are rejected with ERS_ERR_INVALID; the context must hold a
@@ -400,7 +404,11 @@ ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, 
  * the rows it reads, and every wait of a task refers to an earlier entry of its list (the
  * property that makes the persistent solves deadlock-free).
  * counts (8 values, may be NULL): forward and backward CTA entries, lane items (fwd, bwd),
- * warp-task supernodes (fwd, bwd), DIAG entries (fwd, bwd).  ERS_ERR_INVALID with a
+ * warp-task supernodes (fwd, bwd), supernodes solved by whole CTAs (fwd, bwd: DIAG entries
+ * and the pieces of merged blocks, the dense separator triangles solved through their
+ * explicit inverse).  Merged blocks are also checked: their pieces nest into one triangle,
+ * every row tile's GEMV tasks cover its columns once and come after the arrivals (forward)
+ * or far chunks (backward) they read, and every inversion job stays inside its arrays.  ERS_ERR_INVALID with a
  * violated property (or a malformed pattern).  opts (may be NULL: defaults) selects the
  * ordering, as in ers_create. */
 ers_status ers_solve_plan_check(const ers_csr* pattern, const ers_opts* opts, int64_t* counts);

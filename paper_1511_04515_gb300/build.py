@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libers.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["symbolic.cpp", "controller.cpp", "k_factor.cu", "k_solve.cu", "k_krylov.cu", "api.cu",
-           "batch.cu", "mlp.cu", "devices.cu"]
+           "batch.cu", "mlp.cu", "devices.cu", "k_minv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", f"-I{INCLUDE}",
           f"-I{CSRC}"]

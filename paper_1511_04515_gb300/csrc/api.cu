@@ -16,6 +16,9 @@ void launch_stamp(ers_ctx* c);
 void launch_node_F(ers_ctx* c, int mode, const double* dev_In, const double* xn, double* out);
 cudaError_t launch_refactor(ers_ctx* c);
 cudaError_t factor_kernel_attributes();
+// k_minv.cu
+cudaError_t minv_upload(ers_ctx* c);
+cudaError_t launch_minv(ers_ctx* c);
 // k_solve.cu
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
@@ -224,6 +227,7 @@ ers_status do_refactor(ers_ctx* c) {
     CU(cudaMemsetAsync(c->F, 0, sizeof(double) * c->n, c->stream));
   }
   CU(launch_refactor(c));
+  CU(launch_minv(c));      // explicit inverses of the merged blocks from the new factor
   c->factored = true;
   c->stats.refactors++;
   return ERS_OK;
@@ -520,13 +524,14 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   std::string m;
   if (!(m = check_csr(G, n, n, "G_lin")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
   if (!(m = check_csr(C, n, n, "C")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
-  for (int i = 0; i < n; ++i) {
+  // a node without capacitance (a zero row of C) makes the circuit differential-algebraic:
+  // J^-1 = -G^-1 C has the eigenvalue 0, and the small dense stage deflates it (Sec. IV-A:
+  // C is never inverted or regularised)
+  c->singular_c = false;
+  for (int i = 0; i < n && !c->singular_c; ++i) {
     bool cap = false;
     for (int e = C->rowptr[i]; e < C->rowptr[i + 1]; ++e) cap = cap || C->val[e] != 0.0;
-    if (!cap)
-      return bail(fail(c, ERS_ERR_INVALID,
-                       "C row " + std::to_string(i) + " is zero: a node without capacitance "
-                       "makes C singular, which the small dense MEVP stage does not support"));
+    c->singular_c = !cap;
   }
   if (p < 0) return bail(fail(c, ERS_ERR_INVALID, "p must be >= 0"));
   if (!(m = check_csr(B, n, p, "B")).empty()) return bail(fail(c, ERS_ERR_INVALID, m));
@@ -565,6 +570,10 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   SymbolicOptions so = symbolic_options(&c->opts);
   std::string err = analyze(n, uptr.data(), uidx.data(), so, c->sym);
   if (!err.empty()) return bail(fail(c, ERS_ERR_INVALID, "symbolic analysis: " + err));
+  // every inversion job of the merged blocks must stay inside its arrays (checked before
+  // anything runs on the device)
+  err = check_minv_plan(c->sym);
+  if (!err.empty()) return bail(fail(c, ERS_ERR_INVALID, "internal: merged-block plan: " + err));
   const Symbolic& S = c->sym;
 
   cudaError_t ce = cudaGetDevice(&c->device);
@@ -742,8 +751,17 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   CUB(dalloc(&P.UDi, S.d_total));
   CUB(dalloc(&P.Lo, S.o_total));
   CUB(dalloc(&P.Uo, S.o_total));
-  CUB(dalloc(&P.arena, S.arena_size));
-  CUB(dalloc(&P.sync, 2 + 3 * (size_t)S.nsn));
+  CUB(dalloc(&P.arena, std::max<int64_t>(S.arena_size, S.mscratch)));
+  CUB(dalloc(&P.sync, solve_sync_words(S.nsn)));
+  // merged blocks: inverses, piece ranges, the GEMV tasks' intermediate vectors and sums
+  P.ngrp = (int)S.grp_first.size();
+  CUB(dalloc(&P.ML, std::max<int64_t>(S.m_total, 1)));
+  CUB(dalloc(&P.MU, std::max<int64_t>(S.m_total, 1)));
+  CUB(upload(&P.grp_first, S.grp_first));
+  CUB(upload(&P.grp_last, S.grp_last));
+  CUB(dalloc(&c->solve_z, (size_t)MAX_RHS * n));
+  CUB(dalloc(&c->solve_part, (size_t)std::max(S.nslots, 1) * 64 * MAX_RHS));
+  CUB(minv_upload(c));
   CUB(cudaDeviceSynchronize());
 #undef CUB
   c->t = 0.0;
@@ -758,6 +776,10 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   c->stats.factor_doubles = 2 * (S.d_total + S.o_total);
   c->stats.arena_doubles = S.arena_size;
   c->stats.refactor_flops = S.flops;
+  c->stats.merged_blocks = (int64_t)S.grp_first.size();
+  for (int w : S.grp_W) c->stats.merged_columns += w;
+  c->stats.merged_inverse_doubles = 2 * S.m_total;
+  c->stats.merged_inverse_flops = S.minv_flops;
   {
     double diag = 0.0, off = 0.0, rows = 0.0;
     for (int s2 = 0; s2 < S.nsn; ++s2) {
@@ -1285,6 +1307,10 @@ ers_status ers_analyze(const ers_csr* pat, const ers_opts* opts, ers_stats_t* ou
   out->factor_doubles = 2 * (S.d_total + S.o_total);
   out->arena_doubles = S.arena_size;
   out->refactor_flops = S.flops;
+  out->merged_blocks = (int64_t)S.grp_first.size();
+  for (int w : S.grp_W) out->merged_columns += w;
+  out->merged_inverse_doubles = 2 * S.m_total;
+  out->merged_inverse_flops = S.minv_flops;
   if (perm) std::memcpy(perm, S.perm.data(), sizeof(int32_t) * S.n);
   return ERS_OK;
 }
@@ -1372,7 +1398,9 @@ void ers_destroy(ers_ctx* c) {
                   (void*)c->d_mstart, (void*)c->d_mused, (void*)c->bdf, (void*)c->d_feat,
                   (void*)c->d_pred, (void*)c->d_kv, (void*)c->d_where,
                   (void*)c->bscan_res, (void*)c->bscan_last, (void*)c->bscan_fin,
-                  (void*)c->bscan_y, (void*)c->bj})
+                  (void*)c->bscan_y, (void*)c->bj, (void*)c->solve_z, (void*)c->solve_part,
+                  (void*)P.ML, (void*)P.MU, (void*)P.grp_first, (void*)P.grp_last,
+                  (void*)c->d_mjobs, (void*)c->d_mtile})
     f(p);
   for (auto& g : c->iter_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);

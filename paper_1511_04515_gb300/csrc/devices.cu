@@ -330,6 +330,10 @@ ers_status group_stats(ers_ctx* g, ers_stats_t* out) {
     acc.solve_bytes_per_pass += x.solve_bytes_per_pass;
     acc.solve_fma_per_rhs += x.solve_fma_per_rhs;
     acc.graph_launches += x.graph_launches;
+    acc.merged_blocks += x.merged_blocks;
+    acc.merged_columns += x.merged_columns;
+    acc.merged_inverse_doubles += x.merged_inverse_doubles;
+    acc.merged_inverse_flops += x.merged_inverse_flops;
     return ERS_OK;
   });
   if (st == ERS_OK) *out = acc;

@@ -71,9 +71,18 @@ struct DevicePlan {
   // factor values
   double *LDi = nullptr, *UDi = nullptr, *Lo = nullptr, *Uo = nullptr;
   double* arena = nullptr;
-  // solve sync words: [0] task counter, then per-supernode counters/flags
-  int32_t* sync = nullptr;   // 2 + 3*nsn ints
+  // merged blocks: explicit inverses of their triangles (W x W column-major each) and the
+  // first / last piece of every block
+  double *ML = nullptr, *MU = nullptr;
+  int32_t *grp_first = nullptr, *grp_last = nullptr;
+  int ngrp = 0;
+  // solve sync words: [0], [1] task counters of the two passes, then per supernode: arrivals,
+  // ready / done flags, backward arrivals, forward and backward row-tile counters of merged
+  // pieces, and the completed row tiles of each merged block (at its first piece)
+  int32_t* sync = nullptr;   // SOLVE_SYNC_WORDS(nsn) ints
 };
+
+constexpr size_t solve_sync_words(size_t nsn) { return 2 + 6 * nsn; }
 
 }  // namespace ers
 
@@ -170,6 +179,10 @@ struct ers_ctx {
   double *x = nullptr, *xk = nullptr, *xnew = nullptr, *F = nullptr, *rhs = nullptr;
   double *v1 = nullptr, *w1 = nullptr, *v2 = nullptr, *ve = nullptr, *tmp = nullptr;
   double* solve_buf = nullptr;       // MAX_RHS * n
+  double* solve_z = nullptr;         // MAX_RHS * n: merged blocks' intermediate vectors
+  double* solve_part = nullptr;      // partial sums of the merged blocks' GEMV tasks
+  ers::MJob* d_mjobs = nullptr;      // inversion plan of the merged blocks
+  int32_t* d_mtile = nullptr;
   double* V = nullptr;               // 3 bases, each (MAX_M+1) * n
   double* H = nullptr;               // 3 * (MAX_M+1) * MAX_M
   ers::KrylovState* ks = nullptr;    // 3
@@ -182,6 +195,7 @@ struct ers_ctx {
   double t = 0.0, h = 0.0;
   bool factored = false;             // LU of G_k valid for the current x
   bool linear = true;
+  bool singular_c = false;           // C has a zero row: deflate near-null eigenvalues of H_m
   ers_stats_t stats{};
   // batch: instances concatenated into one block-diagonal circuit (ninst = 1 otherwise)
   int ninst = 1;

@@ -45,6 +45,8 @@ struct SolveArgs {
   double* y;        // nrhs vectors, stride n (in place)
   int n;
   unsigned* status;
+  double* Z;        // merged blocks: z = M_L y (forward result), accumulates y - U12 x_R
+  double* part;     // partial sums of MGEMV tasks: slot x 64 x MAX_RHS
 };
 
 // shared-memory layout of a CTA (doubles)
@@ -147,7 +149,40 @@ __device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
-// one small supernode, backward, by one warp
+// Column sums of a 32-row slab times x over 16 columns, lanes over rows: lane i holds
+// p[c] = U[i, cb + c] x_i (coalesced loads: one row per lane), and a recursive-halving
+// exchange over lane bits 3..0 (each step keeps half of the columns and adds the partner's
+// half) leaves the sum over 16 lanes of column cb + (lane & 15) in p[0]; the last xor over
+// bit 4 adds the other 16 lanes.  About one shuffle per column instead of a full warp
+// reduction per column.
+template <int NRHS>
+__device__ __forceinline__ void warp_colsum16(const double* urow, int64_t ld, int ncols, bool act,
+                                              const double (&xr)[NRHS], double (&out)[NRHS],
+                                              int lane) {
+  double u[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) u[c] = (act && c < ncols) ? __ldg(urow + (int64_t)c * ld) : 0.0;
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) {
+    double p[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) p[c] = u[c] * xr[k];
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int c = 0; c < off; ++c) {
+        const double send = upper ? p[c] : p[c + off];
+        const double keep = upper ? p[c + off] : p[c];
+        p[c] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    out[k] = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 16);
+  }
+}
+
+// one small supernode, backward, by one warp: xs = y_s - U12 x_R with lanes over the rows R
+// (16-column sums by warp_colsum16), then x_s = U11^-1 xs
 template <int NRHS>
 __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*xs)[64]) {
   const DevicePlan& P = A.P;
@@ -166,28 +201,26 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) xs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
   __syncwarp();
-  // xs_j -= sum_i Uo[i + j r] x[R[i]]
-  for (int i0 = 0; i0 < r; i0 += 32) {
-    int i = i0 + lane;
-    double xr[NRHS];
-    int row = i < r ? __ldg(R + i) : 0;
+  // column sums, one 16-column block at a time over all row slabs
+  for (int cb = 0; cb < w; cb += 16) {
+    double tot[NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) xr[k] = i < r ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
-    for (int j0 = 0; j0 < w; j0 += UNR) {
-      double u[UNR];
+    for (int k = 0; k < NRHS; ++k) tot[k] = 0.0;
+    for (int i0 = 0; i0 < r; i0 += 32) {
+      const int i = i0 + lane;
+      const bool act = i < r;
+      double xr[NRHS];
+      const int row = act ? __ldg(R + i) : 0;
 #pragma unroll
-      for (int q = 0; q < UNR; ++q)
-        u[q] = (i < r && j0 + q < w) ? __ldg(Uo + i + (int64_t)(j0 + q) * r) : 0.0;
+      for (int k = 0; k < NRHS; ++k) xr[k] = act ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
+      double v[NRHS];
+      warp_colsum16<NRHS>(Uo + i + (int64_t)cb * r, r, min(16, w - cb), act, xr, v, lane);
 #pragma unroll
-      for (int q = 0; q < UNR; ++q) {
-        if (j0 + q >= w) break;
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-          double v = warp_sum(u[q] * xr[k]);
-          if (lane == 0) xs[k][j0 + q] -= v;
-        }
-      }
+      for (int k = 0; k < NRHS; ++k) tot[k] += v[k];
     }
+    if (lane < 16 && cb + lane < w)
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) xs[k][cb + lane] -= tot[k];
   }
   __syncwarp();
   double z[2][NRHS];
@@ -347,9 +380,10 @@ __device__ void fwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) return;
   __threadfence();
+  const double* zsrc = T.grp >= 0 ? A.Z : A.y;   // a merged piece's z lives in Z
   for (int q = lane; q < w; q += 32)
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) zs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+    for (int k = 0; k < NRHS; ++k) zs[k][q] = __ldcg(zsrc + (int64_t)k * n + c0 + q);
   __syncwarp();
   double acc[NRHS];
 #pragma unroll
@@ -376,8 +410,8 @@ __device__ void fwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
-// a far chunk, backward, one warp: lanes over columns,
-// y[c0 + j] -= sum_{i in chunk} Uo[i + j r] x[R[i]]
+// a far chunk, backward, one warp: y[c0 + j] -= sum_{i in chunk} Uo[i + j r] x[R[i]], lanes
+// over the chunk's rows (coalesced panel loads) and 16-column sums by warp_colsum16
 template <int NRHS>
 __device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, double* buf) {
   const DevicePlan& P = A.P;
@@ -387,37 +421,25 @@ __device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
   const double* Uo = P.Uo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
-  double (*xr)[32] = reinterpret_cast<double (*)[32]>(buf);
-  const int rows = T.r1 - T.r0;
-  const int myrow = lane < rows ? __ldg(R + T.r0 + lane) : 0;
+  (void)buf;
+  const int i = T.r0 + lane;
+  const bool act = i < T.r1;
+  const int myrow = act ? __ldg(R + i) : 0;
   int ok = 1;
   if (lane == 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) return;
   __threadfence();
+  double xr[NRHS];
 #pragma unroll
-  for (int k = 0; k < NRHS; ++k) xr[k][lane] = lane < rows ? __ldcg(A.y + (int64_t)k * n + myrow) : 0.0;
-  __syncwarp();
+  for (int k = 0; k < NRHS; ++k) xr[k] = act ? __ldcg(A.y + (int64_t)k * n + myrow) : 0.0;
+  double* dst = T.grp >= 0 ? A.Z : A.y;   // a merged piece accumulates in Z
+  for (int cb = 0; cb < w; cb += 16) {
+    double v[NRHS];
+    warp_colsum16<NRHS>(Uo + i + (int64_t)cb * r, r, min(16, w - cb), act, xr, v, lane);
+    if (lane < 16 && cb + lane < w)
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    int j = lane + 32 * h;
-    if (j >= w) continue;
-    const double* col = Uo + (int64_t)j * r + T.r0;
-    double acc[NRHS];
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
-    constexpr int B = 16;
-    for (int i0 = 0; i0 < rows; i0 += B) {
-      double u[B];
-#pragma unroll
-      for (int q = 0; q < B; ++q) u[q] = i0 + q < rows ? __ldg(col + i0 + q) : 0.0;
-#pragma unroll
-      for (int q = 0; q < B; ++q)
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) acc[k] += u[q] * xr[k][(i0 + q) & 31];
-    }
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + c0 + j, -acc[k]);
+      for (int k = 0; k < NRHS; ++k) atomicAdd(dst + (int64_t)k * n + c0 + cb + lane, -v[k]);
   }
   __threadfence();
   __syncwarp();
@@ -458,8 +480,120 @@ __device__ __forceinline__ void stage(const double* D, int w, const double* Pn, 
   }
 }
 
+// One row tile of a merged block times a column range of its explicit inverse (a CTA
+// entry).  Forward: partial = M_L[rows of piece sn, columns r0..r1-1] y once the arrivals at
+// those column pieces are complete; backward: partial = M_U[...] Z once their far chunks have
+// subtracted U12 x_R.  The partial goes to the task's slot; the last task of the row tile
+// sums the tile's slots in slot order (a fixed order, so the result is deterministic) and
+// writes z into Z (forward: then the piece is ready for its far chunks) or x into y
+// (backward: the block's pieces complete together once all its row tiles are written, so no
+// piece completes before its parent).
+constexpr int MG_COLS = 512;     // columns of one MGEMV task (merge_col_block x 64 at most)
 template <int NRHS>
-__global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_fwd(SolveArgs A) {
+__device__ void mgemv(const SolveArgs& A, const SolveTask& T, double* sm, bool fwd) {
+  const DevicePlan& P = A.P;
+  const int nsn = P.nsn, n = A.n;
+  int32_t* arrive = P.sync + 2;
+  int32_t* flag = P.sync + 2 + nsn;             // forward ready (1) / backward done (2)
+  int32_t* arriveb = P.sync + 2 + 2 * nsn;
+  int32_t* tilecnt = P.sync + 2 + (fwd ? 3 : 4) * (size_t)nsn;
+  int32_t* grpcnt = P.sync + 2 + 5 * (size_t)nsn;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ncol = (int)(T.row_off - T.o_off);
+  double* vs = sm;                              // [NRHS][MG_COLS]
+  double* part = sm + NRHS * MG_COLS;           // [4][64][NRHS]
+  __shared__ int s_ok, s_last;
+  if (tid < 32) {
+    const int j = T.r0 + lane;
+    int ok = 1;
+    if (j < T.r1)
+      ok = fwd ? wait_geq(arrive + j, __ldg(P.fwd_expect + j), A.status)
+               : wait_geq(arriveb + j, __ldg(P.bwd_nchunk + j), A.status);
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  __threadfence();
+  const double* src = fwd ? A.y : A.Z;
+  for (int e = tid; e < ncol * NRHS; e += SOLVE_THREADS) {
+    const int k = e / ncol, c = e - k * ncol;
+    vs[k * MG_COLS + c] = __ldcg(src + (int64_t)k * n + T.o_off + c);
+  }
+  __syncthreads();
+  const int q = tid & 63, g = tid >> 6;         // row of the tile, column group (c = g mod 4)
+  const double* M = (fwd ? P.ML : P.MU) + T.d_off;
+  const int64_t ld = T.r;
+  double acc[NRHS];
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+  if (q < T.w) {
+    const double* mq = M + q;
+    int c = g;
+    for (; c + 28 < ncol; c += 32) {            // 8 independent loads per thread
+      double m[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m[u] = __ldg(mq + (int64_t)(c + 4 * u) * ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] += m[u] * vs[k * MG_COLS + c + 4 * u];
+    }
+    for (; c < ncol; c += 4) {
+      const double m = __ldg(mq + (int64_t)c * ld);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] += m * vs[k * MG_COLS + c];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) part[(g * 64 + q) * NRHS + k] = acc[k];
+  __syncthreads();
+  if (tid < T.w) {
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) {
+      const double v = part[(0 * 64 + tid) * NRHS + k] + part[(1 * 64 + tid) * NRHS + k] +
+                       part[(2 * 64 + tid) * NRHS + k] + part[(3 * 64 + tid) * NRHS + k];
+      A.part[((int64_t)T.tgt0 * 64 + tid) * MAX_RHS + k] = v;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(tilecnt + T.sn, 1) == T.wait_cnt - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < T.w) {
+    double* dst = fwd ? A.Z : A.y;
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) {
+      double z = 0.0;
+      for (int t = 0; t < T.wait_cnt; ++t)
+        z += __ldcg(A.part + ((int64_t)(T.wait_sn + t) * 64 + tid) * MAX_RHS + k);
+      dst[(int64_t)k * n + T.c0 + tid] = z;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (fwd) {
+    if (tid == 0) st_release(flag + T.sn, 1);
+    return;
+  }
+  if (tid < 32) {
+    const int f = __ldg(P.grp_first + T.grp), l = __ldg(P.grp_last + T.grp);
+    int all = 0;
+    if (lane == 0) all = atomicAdd(grpcnt + f, 1) == l - f;
+    all = __shfl_sync(0xffffffffu, all, 0);
+    if (all) {
+      __threadfence();
+      for (int s2 = f + lane; s2 <= l; s2 += 32) st_release(flag + s2, 2);
+    }
+  }
+}
+
+// MINB: resident CTAs per SM the kernel is compiled for (register cap 65536 / (256 MINB)); the
+// launch uses the instance matching the autotuned count, so no count pays the tighter cap.
+template <int NRHS, int MINB>
+__global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
   extern __shared__ double sm[];
   double* sD = sm;
   double* sP = sD + SM_D;
@@ -491,6 +625,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_fwd(SolveArgs A) {
     }
     if (T.kind == TASK_BULK) {
       if (wq < T.r0) fwd_chunk<NRHS>(A, P.fwd_small[T.sn + wq], lane, sm + wq * MAX_RHS * 64);
+      continue;
+    }
+    if (T.kind == TASK_MGEMV) {
+      mgemv<NRHS>(A, T, sm, true);
       continue;
     }
     const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
@@ -574,8 +712,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_fwd(SolveArgs A) {
   }
 }
 
-template <int NRHS>
-__global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_bwd(SolveArgs A) {
+template <int NRHS, int MINB>
+__global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
   extern __shared__ double sm[];
   double* sD = sm;
   double* sP = sD + SM_D;
@@ -607,6 +745,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 3) k_trsv_bwd(SolveArgs A) {
     }
     if (T.kind == TASK_BULK) {
       if (wq < T.r0) bwd_chunk<NRHS>(A, P.bwd_small[T.sn + wq], lane, sm + wq * MAX_RHS * 64);
+      continue;
+    }
+    if (T.kind == TASK_MGEMV) {
+      mgemv<NRHS>(A, T, sm, false);
       continue;
     }
     const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
@@ -717,14 +859,22 @@ cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag) {
 
 template <int NRHS>
 static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
-  k_trsv_fwd<NRHS><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-  k_trsv_bwd<NRHS><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  if (c->solve_ctas_per_sm >= 3) {
+    k_trsv_fwd<NRHS, 3><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+    k_trsv_bwd<NRHS, 3><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  } else {
+    k_trsv_fwd<NRHS, 2><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+    k_trsv_bwd<NRHS, 2><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  }
 }
 
 cudaError_t solve_kernel_attributes() {
-  const void* fns[] = {(const void*)k_trsv_fwd<1>, (const void*)k_trsv_fwd<2>,
-                       (const void*)k_trsv_fwd<3>, (const void*)k_trsv_bwd<1>,
-                       (const void*)k_trsv_bwd<2>, (const void*)k_trsv_bwd<3>};
+  const void* fns[] = {(const void*)k_trsv_fwd<1, 2>, (const void*)k_trsv_fwd<2, 2>,
+                       (const void*)k_trsv_fwd<3, 2>, (const void*)k_trsv_bwd<1, 2>,
+                       (const void*)k_trsv_bwd<2, 2>, (const void*)k_trsv_bwd<3, 2>,
+                       (const void*)k_trsv_fwd<1, 3>, (const void*)k_trsv_fwd<2, 3>,
+                       (const void*)k_trsv_fwd<3, 3>, (const void*)k_trsv_bwd<1, 3>,
+                       (const void*)k_trsv_bwd<2, 3>, (const void*)k_trsv_bwd<3, 3>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM);
     if (e != cudaSuccess) return e;
@@ -736,9 +886,9 @@ cudaError_t solve_kernel_attributes() {
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
   DevicePlan& P = c->plan;
   if (nrhs < 1 || nrhs > MAX_RHS) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * (2 + 3 * (size_t)P.nsn), c->stream);
+  cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * solve_sync_words(P.nsn), c->stream);
   if (e != cudaSuccess) return e;
-  SolveArgs A{P, y, c->n, c->d_status};
+  SolveArgs A{P, y, c->n, c->d_status, c->solve_z, c->solve_part};
   int blocks = c->sm_count * c->solve_ctas_per_sm;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profile) {
@@ -774,9 +924,9 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
 // frameworks whose device memory belongs to their own pool allocator, and latency-bound
 // loops that forbid allocator calls (cudaMalloc / cudaFree may synchronise the device).
 // ers_solve_dev_noalloc serves them: it runs the same forward/backward kernels as every
-// other solve, but the kernels' scratch (the dependency counters and flags, 2 + 3 * nsn
+// other solve, but the kernels' scratch (the dependency counters and flags, 2 + 6 * nsn
 // ints) lives in the file-scope array below instead of the context's own buffer.  The array
-// is a fixed 6 MiB that every GPU loading this library keeps until the process exits;
+// is a fixed 12 MiB that every GPU loading this library keeps until the process exits;
 // contexts with more than NOALLOC_MAX_SN supernodes are rejected.  All calls on a device
 // share the one array, so calls whose solves overlap on the GPU race; the counters are
 // cleared at each call.  The call ends with a stream synchronisation (it reads the device
@@ -785,7 +935,7 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
 namespace ers {
 
 constexpr int NOALLOC_MAX_SN = 1 << 19;
-static __device__ __align__(256) int32_t g_noalloc_sync[2 + 3 * NOALLOC_MAX_SN];
+static __device__ __align__(256) int32_t g_noalloc_sync[solve_sync_words(NOALLOC_MAX_SN)];
 
 __global__ void k_gather_perm(int n, const int32_t* perm, const double* src, double* dst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -875,10 +1025,10 @@ extern "C" ers_status ers_solve_dev_noalloc(ers_ctx* c, const double* b_dev, dou
   const int nb = (n + 255) / 256;
   e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(scratch, 0, sizeof(int32_t) * (2 + 3 * (size_t)P.nsn), c->stream);
+    e = cudaMemsetAsync(scratch, 0, sizeof(int32_t) * solve_sync_words(P.nsn), c->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   k_gather_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, b_dev, c->solve_buf);
-  SolveArgs A{P, c->solve_buf, n, c->d_status};
+  SolveArgs A{P, c->solve_buf, n, c->d_status, c->solve_z, c->solve_part};
   launch_pair<1>(c, A, c->sm_count * c->solve_ctas_per_sm);
   k_scatter_perm<<<nb, 256, 0, c->stream>>>(n, c->d_perm, c->solve_buf, x_dev);
   c->stats.kernel_launches += 4;

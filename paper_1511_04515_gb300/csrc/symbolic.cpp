@@ -12,6 +12,7 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <functional>
 #include <climits>
 #include <map>
 #include <set>
@@ -301,6 +302,163 @@ class Dissector {
   }
 };
 
+// Merged blocks for the triangular solves.  A chain of consecutive supernodes s, s+1, ...,
+// each the parent of the previous, whose row structures nest -- R(s) is the columns of s+1
+// followed by R(s+1) -- is one dense triangle of the factor cut at the supernode width cap (a
+// nested-dissection separator).  Solving it piece by piece is a chain of dependent hand-offs;
+// through the explicit inverse M of the merged triangle (L_G^-1 forward, U_G^-1 backward) it
+// is a GEMV that many CTAs share.  M is computed after each refactor by recursive block
+// inversion of the pieces (inv [A 0; B C] = [A^-1 0; -C^-1 B A^-1  C^-1], and the upper-
+// triangular mirror) as phases of 64 x 64-tiled copies and GEMMs over the existing factor.
+static bool nests(const Symbolic& S, int a) {
+  const int b = a + 1;
+  if (S.sn_parent[a] != b) return false;
+  const int64_t ra = S.rptr[a + 1] - S.rptr[a], rb = S.rptr[b + 1] - S.rptr[b];
+  const int wb = S.sn_start[b + 1] - S.sn_start[b];
+  if (ra != wb + rb) return false;
+  const int32_t* Ra = S.rows.data() + S.rptr[a];
+  const int32_t* Rb = S.rows.data() + S.rptr[b];
+  for (int q = 0; q < wb; ++q)
+    if (Ra[q] != S.sn_start[b] + q) return false;
+  for (int64_t q = 0; q < rb; ++q)
+    if (Ra[wb + q] != Rb[q]) return false;
+  return true;
+}
+
+static void plan_merged_blocks(Symbolic& S, const SymbolicOptions& opt) {
+  const int nsn = S.nsn;
+  S.sn_grp.assign(nsn, -1);
+  S.grp_first.clear(); S.grp_last.clear(); S.grp_c0.clear(); S.grp_W.clear();
+  S.grp_moff.clear();
+  S.m_total = 0;
+  S.mjobs.clear(); S.mphase_ptr.assign(1, 0); S.mtile.clear();
+  S.mscratch = 0;
+  S.minv_flops = 0.0;
+  if (opt.merge_min_width <= 0) return;
+  for (int s = 0; s < nsn;) {
+    int e = s;
+    while (e + 1 < nsn && nests(S, e) &&
+           S.sn_start[e + 2] - S.sn_start[s] <= opt.merge_max_width)
+      ++e;
+    const int W = S.sn_start[e + 1] - S.sn_start[s];
+    if (e > s && W >= opt.merge_min_width) {
+      const int g = (int)S.grp_first.size();
+      S.grp_first.push_back(s);
+      S.grp_last.push_back(e);
+      S.grp_c0.push_back(S.sn_start[s]);
+      S.grp_W.push_back(W);
+      S.grp_moff.push_back(S.m_total);
+      S.m_total += (int64_t)W * W;
+      for (int q = s; q <= e; ++q) S.sn_grp[q] = g;
+    }
+    s = e > s ? e + 1 : s + 1;
+  }
+  // inversion plan: recursion nodes by height (leaves 0), phases 0 (leaf copies) then, per
+  // height h >= 1, the copies of B, T = B X, and the off-diagonal block -X T
+  struct Node { int g, lo, mid, hi; };
+  std::vector<std::vector<Node>> by_h;
+  std::vector<MJob> leaf_jobs;
+  std::function<int(int, int, int)> rec = [&](int g, int lo, int hi) -> int {
+    const int f = S.grp_first[g];
+    if (lo == hi) {
+      const int sp = f + lo;
+      const int w = S.sn_start[sp + 1] - S.sn_start[sp];
+      const int W = S.grp_W[g];
+      const int64_t o = S.sn_start[sp] - S.grp_c0[g];
+      for (int side = 0; side < 2; ++side) {
+        MJob j{};
+        j.kind = MJOB_COPY; j.m = w; j.n = w; j.k = 0;
+        j.a_arr = side == 0 ? MARR_LDI : MARR_UDI; j.a_off = S.d_off[sp]; j.lda = w;
+        j.c_arr = side == 0 ? MARR_ML : MARR_MU; j.c_off = S.grp_moff[g] + o + o * W;
+        j.ldc = W; j.alpha = 1.0;
+        leaf_jobs.push_back(j);
+      }
+      return 0;
+    }
+    const int mid = (lo + hi + 1) / 2;
+    const int h = std::max(rec(g, lo, mid - 1), rec(g, mid, hi)) + 1;
+    if ((int)by_h.size() <= h) by_h.resize(h + 1);
+    by_h[h].push_back({g, lo, mid, hi});
+    return h;
+  };
+  for (int g = 0; g < (int)S.grp_first.size(); ++g)
+    rec(g, 0, S.grp_last[g] - S.grp_first[g]);
+  std::vector<std::vector<MJob>> phases(1, leaf_jobs);
+  for (size_t h = 1; h < by_h.size(); ++h) {
+    std::vector<MJob> pa, pb, pc;
+    int64_t scr = 0;
+    for (const Node& nd : by_h[h]) {
+      const int f = S.grp_first[nd.g], W = S.grp_W[nd.g], c0 = S.grp_c0[nd.g];
+      const int64_t moff = S.grp_moff[nd.g];
+      auto o = [&](int i) -> int64_t { return S.sn_start[f + i] - c0; };
+      const int WA = (int)(o(nd.mid) - o(nd.lo)), WC = (int)(o(nd.hi + 1) - o(nd.mid));
+      const int64_t bdL = scr, tL = scr + (int64_t)WA * WC, bdU = scr + 2 * (int64_t)WA * WC,
+                    tU = scr + 3 * (int64_t)WA * WC;
+      scr += 4 * (int64_t)WA * WC;
+      for (int p = nd.lo; p < nd.mid; ++p) {
+        const int sp = f + p;
+        const int wp = S.sn_start[sp + 1] - S.sn_start[sp];
+        const int rp = (int)(S.rptr[sp + 1] - S.rptr[sp]);
+        const int64_t roff = o(nd.mid) - o(p + 1);   // first row of the C block in R(sp)
+        MJob a{};
+        a.kind = MJOB_COPY; a.m = WC; a.n = wp;
+        a.a_arr = MARR_LO; a.a_off = S.o_off[sp] + roff; a.lda = rp;
+        a.c_arr = MARR_SCR; a.c_off = bdL + (o(p) - o(nd.lo)) * WC; a.ldc = WC; a.alpha = 1.0;
+        pa.push_back(a);
+        MJob u{};
+        u.kind = MJOB_COPYT; u.m = wp; u.n = WC;
+        u.a_arr = MARR_UO; u.a_off = S.o_off[sp] + roff; u.lda = rp;
+        u.c_arr = MARR_SCR; u.c_off = bdU + (o(p) - o(nd.lo)); u.ldc = WA; u.alpha = 1.0;
+        pa.push_back(u);
+      }
+      MJob b1{};   // T_L = B_L X_A (X_A lower)
+      b1.kind = MJOB_GEMM; b1.m = WC; b1.n = WA; b1.k = WA; b1.tri = MTRI_B_LOWER;
+      b1.a_arr = MARR_SCR; b1.a_off = bdL; b1.lda = WC;
+      b1.b_arr = MARR_ML; b1.b_off = moff + o(nd.lo) + o(nd.lo) * W; b1.ldb = W;
+      b1.c_arr = MARR_SCR; b1.c_off = tL; b1.ldc = WC; b1.alpha = 1.0;
+      pb.push_back(b1);
+      MJob b2{};   // T_U = B_U X_C (X_C upper)
+      b2.kind = MJOB_GEMM; b2.m = WA; b2.n = WC; b2.k = WC; b2.tri = MTRI_B_UPPER;
+      b2.a_arr = MARR_SCR; b2.a_off = bdU; b2.lda = WA;
+      b2.b_arr = MARR_MU; b2.b_off = moff + o(nd.mid) + o(nd.mid) * W; b2.ldb = W;
+      b2.c_arr = MARR_SCR; b2.c_off = tU; b2.ldc = WA; b2.alpha = 1.0;
+      pb.push_back(b2);
+      MJob c1{};   // M_L[C, A] = -X_C T_L (X_C lower)
+      c1.kind = MJOB_GEMM; c1.m = WC; c1.n = WA; c1.k = WC; c1.tri = MTRI_A_LOWER;
+      c1.a_arr = MARR_ML; c1.a_off = moff + o(nd.mid) + o(nd.mid) * W; c1.lda = W;
+      c1.b_arr = MARR_SCR; c1.b_off = tL; c1.ldb = WC;
+      c1.c_arr = MARR_ML; c1.c_off = moff + o(nd.mid) + o(nd.lo) * W; c1.ldc = W;
+      c1.alpha = -1.0;
+      pc.push_back(c1);
+      MJob c2{};   // M_U[A, C] = -X_A T_U (X_A upper)
+      c2.kind = MJOB_GEMM; c2.m = WA; c2.n = WC; c2.k = WA; c2.tri = MTRI_A_UPPER;
+      c2.a_arr = MARR_MU; c2.a_off = moff + o(nd.lo) + o(nd.lo) * W; c2.lda = W;
+      c2.b_arr = MARR_SCR; c2.b_off = tU; c2.ldb = WA;
+      c2.c_arr = MARR_MU; c2.c_off = moff + o(nd.lo) + o(nd.mid) * W; c2.ldc = W;
+      c2.alpha = -1.0;
+      pc.push_back(c2);
+      // about half of each GEMM's products are skipped by its triangular operand
+      S.minv_flops += 2.0 * ((double)WC * WA * WA + (double)WA * WC * WC);
+    }
+    S.mscratch = std::max(S.mscratch, scr);
+    phases.push_back(pa);
+    phases.push_back(pb);
+    phases.push_back(pc);
+  }
+  for (const auto& ph : phases) {
+    for (const MJob& j : ph) {
+      const int jid = (int)S.mjobs.size();
+      S.mjobs.push_back(j);
+      for (int ti = 0; ti < (j.m + 63) / 64; ++ti)
+        for (int tj = 0; tj < (j.n + 63) / 64; ++tj) {
+          S.mtile.push_back(jid);
+          S.mtile.push_back((ti << 16) | tj);
+        }
+    }
+    S.mphase_ptr.push_back((int32_t)(S.mtile.size() / 2));
+  }
+}
+
 }  // namespace
 
 std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const SymbolicOptions& opt,
@@ -548,6 +706,57 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     }
   }
 
+  // padding for merged solve blocks: when supernode a's parent is a + 1 and R(a) is a strict
+  // subset of the columns of a + 1 followed by R(a + 1) (always a superset, the parent's
+  // structure absorbs its child's), R(a) takes that superset with explicit zeros if they
+  // cost at most merge_pad_pct % of a's own off-diagonal panel; the two then nest and can be
+  // solved as one dense triangle.  Top-down, so a parent is padded before its child reads it.
+  if (opt.merge_min_width > 0 && opt.merge_pad_pct > 0) {
+    std::vector<std::vector<int32_t>> padded(nsn);
+    std::vector<char> has(nsn, 0);
+    auto rows_of = [&](int s) -> std::vector<int32_t> {
+      if (has[s]) return padded[s];
+      return std::vector<int32_t>(S.rows.begin() + S.rptr[s], S.rows.begin() + S.rptr[s + 1]);
+    };
+    auto large_sn = [&](int s, int64_t r) {
+      const int64_t w = S.sn_start[s + 1] - S.sn_start[s];
+      return w * (w + r) > opt.fused_limit;
+    };
+    int64_t grown = 0;
+    for (int a = nsn - 2; a >= 0; --a) {
+      const int b = a + 1;
+      if (S.sn_parent[a] != b) continue;
+      std::vector<int32_t> Rb = rows_of(b);
+      const int64_t ra = S.rptr[a + 1] - S.rptr[a];
+      const int64_t wa = S.sn_start[a + 1] - S.sn_start[a], wb = S.sn_start[b + 1] - S.sn_start[b];
+      const int64_t need = wb + (int64_t)Rb.size();
+      if (need == ra || !large_sn(a, ra) || !large_sn(b, (int64_t)Rb.size())) continue;
+      if ((need - ra) * 100 > (int64_t)opt.merge_pad_pct * ra) continue;
+      std::vector<int32_t> R;
+      R.reserve(need);
+      for (int q = 0; q < wb; ++q) R.push_back(S.sn_start[b] + q);
+      R.insert(R.end(), Rb.begin(), Rb.end());
+      // R(a) must be contained in R (the parent's columns and structure)
+      std::vector<int32_t> Ra(S.rows.begin() + S.rptr[a], S.rows.begin() + S.rptr[a + 1]);
+      if (!std::includes(R.begin(), R.end(), Ra.begin(), Ra.end())) continue;
+      grown += (need - ra) * wa;
+      padded[a] = std::move(R);
+      has[a] = 1;
+    }
+    if (grown > 0) {
+      std::vector<int64_t> nptr(nsn + 1, 0);
+      std::vector<int32_t> nrows;
+      nrows.reserve(S.rows.size() + grown);
+      for (int s2 = 0; s2 < nsn; ++s2) {
+        if (has[s2]) nrows.insert(nrows.end(), padded[s2].begin(), padded[s2].end());
+        else nrows.insert(nrows.end(), S.rows.begin() + S.rptr[s2], S.rows.begin() + S.rptr[s2 + 1]);
+        nptr[s2 + 1] = (int64_t)nrows.size();
+      }
+      S.rows.swap(nrows);
+      S.rptr.swap(nptr);
+    }
+  }
+
   // levels (leaves 0) and storage
   S.level.assign(nsn, 0);
   for (int s = 0; s < nsn; ++s)
@@ -749,6 +958,9 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     }
   }
 
+  // merged blocks of the solves and their inversion plan
+  plan_merged_blocks(S, opt);
+
   // 5. triangular-solve work lists ---------------------------------------------------
   {
     S.fwd.clear(); S.bwd.clear(); S.fwd_small.clear(); S.bwd_small.clear(); S.fwd_tgt.clear();
@@ -772,13 +984,47 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
     auto small = [&](int s) {
       int64_t w = S.sn_start[s + 1] - S.sn_start[s];
       int64_t r = S.rptr[s + 1] - S.rptr[s];
-      return w * (w + r) <= opt.fused_limit;
+      return S.sn_grp[s] < 0 && w * (w + r) <= opt.fused_limit;
     };
     // narrow supernodes with few rows: one lane each (a warp task holds 32)
     auto lane_item = [&](int s) {
-      return opt.lane_rows > 0 && S.sn_start[s + 1] - S.sn_start[s] <= opt.lane_width &&
+      return S.sn_grp[s] < 0 && opt.lane_rows > 0 &&
+             S.sn_start[s + 1] - S.sn_start[s] <= opt.lane_width &&
              S.rptr[s + 1] - S.rptr[s] <= opt.lane_rows;
     };
+    // a large supernode with its own DIAG entry (not a piece of a merged block)
+    auto large = [&](int s) { return S.sn_grp[s] < 0 && !small(s); };
+    // first row of a merged piece outside its block: the rows before it are the columns of
+    // the later pieces, folded into the block's inverse
+    auto ext_row0 = [&](int s) -> int {
+      const int g = S.sn_grp[s];
+      return S.sn_start[S.grp_last[g] + 1] - S.sn_start[s + 1];
+    };
+    // a column block of an MGEMV task holds at most 512 columns (the kernel's staging)
+    const int CB = std::max(1, std::min(opt.merge_col_block, 512 / std::max(1, opt.max_width)));
+    int32_t slot_f = 0, slot_b = 0;
+    // the MGEMV entries of merged block g: row tile i times column pieces [j0, j1) in blocks
+    // of CB pieces (forward: pieces first..i of M_L; backward: pieces i..last of M_U)
+    auto mgemv = [&](std::vector<SolveTask>& list, int g, bool fwd, int32_t& slot) {
+      const int f = S.grp_first[g], l = S.grp_last[g], W = S.grp_W[g], c0 = S.grp_c0[g];
+      for (int i = f; i <= l; ++i) {
+        const int lo = fwd ? f : i, hi = fwd ? i + 1 : l + 1;
+        const int ntask = (hi - lo + CB - 1) / CB;
+        const int32_t first_slot = slot;
+        for (int j0 = lo; j0 < hi; j0 += CB) {
+          const int j1 = std::min(hi, j0 + CB);
+          SolveTask t{};
+          t.kind = TASK_MGEMV; t.sn = i; t.r0 = j0; t.r1 = j1;
+          t.tgt0 = slot++; t.ntgt = 0; t.wait_sn = first_slot; t.wait_cnt = ntask;
+          t.c0 = S.sn_start[i]; t.w = S.sn_start[i + 1] - S.sn_start[i]; t.r = W; t.grp = g;
+          t.d_off = S.grp_moff[g] + (S.sn_start[i] - c0) + (int64_t)(S.sn_start[j0] - c0) * W;
+          t.o_off = S.sn_start[j0];
+          t.row_off = S.sn_start[j1];
+          list.push_back(t);
+        }
+      }
+    };
+
     // warp tasks (small supernodes, far chunks) live in fwd_small / bwd_small; a CTA entry
     // GROUP/BULK refers to up to 8 consecutive warp tasks of one level
     auto flush = [](std::vector<SolveTask>& list, std::vector<SolveTask>& smalls, int& first,
@@ -843,24 +1089,36 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       flush(S.fwd, S.fwd_small, first, TASK_GROUP);
       for (size_t k = k0; k < k1; ++k) {
         int s = ford[k];
-        if (small(s)) continue;
+        if (!large(s)) continue;
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
         SolveTask d{TASK_DIAG, s, 0, std::min(r, CH), 0, 0, -1, 0};
         add_targets(s, 0, d.r1, d);
         S.fwd.push_back(d);
       }
-      first = (int)S.fwd_small.size();
+      // merged blocks whose last (highest) piece is on this level: every contribution from
+      // outside the block comes from lower levels
+      std::vector<int> done_grp;
       for (size_t k = k0; k < k1; ++k) {
         int s = ford[k];
-        if (small(s)) continue;
+        if (S.sn_grp[s] >= 0 && S.grp_last[S.sn_grp[s]] == s) done_grp.push_back(S.sn_grp[s]);
+      }
+      for (int g : done_grp) mgemv(S.fwd, g, true, slot_f);
+      first = (int)S.fwd_small.size();
+      auto far_chunks = [&](int s, int r_begin) {
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
-        for (int r0 = CH; r0 < r; r0 += WC) {
+        for (int r0 = r_begin; r0 < r; r0 += WC) {
           SolveTask t{TASK_OFF, s, r0, std::min(r, r0 + WC), 0, 0, -1, 0};
           add_targets(s, t.r0, t.r1, t);
           S.fwd_small.push_back(t);
           if ((int)S.fwd_small.size() - first == 8) flush(S.fwd, S.fwd_small, first, TASK_BULK);
         }
+      };
+      for (size_t k = k0; k < k1; ++k) {
+        int s = ford[k];
+        if (large(s)) far_chunks(s, CH);
       }
+      for (int g : done_grp)
+        for (int s = S.grp_first[g]; s <= S.grp_last[g]; ++s) far_chunks(s, ext_row0(s));
       flush(S.fwd, S.fwd_small, first, TASK_BULK);
       k0 = k1;
     }
@@ -870,17 +1128,28 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       size_t k1 = k0;
       while (k1 < bord.size() && depth[bord[k1]] == depth[bord[k0]]) ++k1;
       int first = (int)S.bwd_small.size();
-      for (size_t k = k0; k < k1; ++k) {
-        int s = bord[k];
-        if (small(s)) continue;
+      auto far_chunks = [&](int s, int r_begin) {
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
-        for (int r0 = CH; r0 < r; r0 += WC) {
+        for (int r0 = r_begin; r0 < r; r0 += WC) {
           int ws = S.sn_of[S.rows[S.rptr[s] + r0]];
           S.bwd_small.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + WC), 0, 0, ws, 0});
           S.bwd_nchunk[s]++;
           if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_BULK);
         }
+      };
+      for (size_t k = k0; k < k1; ++k) {
+        int s = bord[k];
+        if (large(s)) far_chunks(s, CH);
       }
+      // merged blocks whose last (top) piece is at this depth: their far chunks wait for
+      // ancestors only, their MGEMV entries (below) for those chunks
+      std::vector<int> done_grp;
+      for (size_t k = k0; k < k1; ++k) {
+        int s = bord[k];
+        if (S.sn_grp[s] >= 0 && S.grp_last[S.sn_grp[s]] == s) done_grp.push_back(S.sn_grp[s]);
+      }
+      for (int g : done_grp)
+        for (int s = S.grp_first[g]; s <= S.grp_last[g]; ++s) far_chunks(s, ext_row0(s));
       flush(S.bwd, S.bwd_small, first, TASK_BULK);
       bool lane_level = false;
       {
@@ -913,17 +1182,22 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       flush(S.bwd, S.bwd_small, first, TASK_GROUP);
       for (size_t k = k0; k < k1; ++k) {
         int s = bord[k];
-        if (small(s)) continue;
+        if (!large(s)) continue;
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
         S.bwd.push_back(SolveTask{TASK_DIAG, s, 0, std::min(r, CH), 0, 0, S.sn_parent[s], 0});
       }
+      for (int g : done_grp) mgemv(S.bwd, g, false, slot_b);
       k0 = k1;
     }
+    S.nslots = std::max(slot_f, slot_b);
     // descriptors: everything a task needs in one record
     auto fill = [&](SolveTask& t, bool fwd) {
+      if (t.kind == TASK_MGEMV) return;
+      t.grp = -1;
       if (t.kind == TASK_GROUP || t.kind == TASK_BULK) return;
       if (t.kind == TASK_LANES) return;
       int s = t.sn;
+      t.grp = S.sn_grp[s];
       t.c0 = S.sn_start[s];
       t.w = S.sn_start[s + 1] - t.c0;
       t.r = (int32_t)(S.rptr[s + 1] - S.rptr[s]);
@@ -1003,11 +1277,59 @@ static std::string check_refactor_plan(const Symbolic& S) {
   return "";
 }
 
+std::string check_minv_plan(const Symbolic& S) {
+  const int64_t size[7] = {S.d_total, S.d_total, S.o_total, S.o_total, S.m_total, S.m_total,
+                           S.mscratch};
+  auto inside = [&](int arr, int64_t off, int64_t rows, int64_t cols, int64_t ld) {
+    if (arr < 0 || arr > 6) return false;
+    if (rows <= 0 || cols <= 0) return true;
+    if (off < 0 || ld < rows) return false;
+    return off + (cols - 1) * ld + rows <= size[arr];
+  };
+  for (size_t q = 0; q < S.mjobs.size(); ++q) {
+    const MJob& j = S.mjobs[q];
+    bool ok = true;
+    if (j.kind == MJOB_COPY) {
+      ok = inside(j.a_arr, j.a_off, j.m, j.n, j.lda) && inside(j.c_arr, j.c_off, j.m, j.n, j.ldc);
+    } else if (j.kind == MJOB_COPYT) {
+      ok = inside(j.a_arr, j.a_off, j.n, j.m, j.lda) && inside(j.c_arr, j.c_off, j.m, j.n, j.ldc);
+    } else if (j.kind == MJOB_GEMM) {
+      ok = inside(j.a_arr, j.a_off, j.m, j.k, j.lda) && inside(j.b_arr, j.b_off, j.k, j.n, j.ldb) &&
+           inside(j.c_arr, j.c_off, j.m, j.n, j.ldc);
+      if ((j.tri & (MTRI_A_LOWER | MTRI_A_UPPER)) && j.m != j.k) ok = false;
+      if ((j.tri & (MTRI_B_LOWER | MTRI_B_UPPER)) && j.k != j.n) ok = false;
+    } else {
+      ok = false;
+    }
+    if (!ok) return "inversion job " + std::to_string(q) + " reaches outside its arrays";
+  }
+  // the tiles of every job cover its output grid exactly once, within one phase
+  std::vector<int64_t> seen(S.mjobs.size(), 0), phase_of(S.mjobs.size(), -1);
+  for (size_t ph = 0; ph + 1 < S.mphase_ptr.size(); ++ph)
+    for (int32_t t = S.mphase_ptr[ph]; t < S.mphase_ptr[ph + 1]; ++t) {
+      const int jid = S.mtile[2 * t], ti = S.mtile[2 * t + 1] >> 16, tj = S.mtile[2 * t + 1] & 0xffff;
+      if (jid < 0 || jid >= (int)S.mjobs.size()) return "inversion tile of an unknown job";
+      const MJob& j = S.mjobs[jid];
+      if (ti * 64 >= j.m || tj * 64 >= j.n) return "inversion tile outside its job";
+      if (phase_of[jid] >= 0 && phase_of[jid] != (int64_t)ph) return "inversion job split over phases";
+      phase_of[jid] = (int64_t)ph;
+      seen[jid]++;
+    }
+  for (size_t q = 0; q < S.mjobs.size(); ++q) {
+    const MJob& j = S.mjobs[q];
+    if (seen[q] != (int64_t)((j.m + 63) / 64) * ((j.n + 63) / 64))
+      return "inversion job " + std::to_string(q) + " not covered by its tiles once";
+  }
+  return "";
+}
+
 std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   const int nsn = S.nsn;
   {
     std::string err = check_refactor_plan(S);
     if (!err.empty()) return "refactor plan: " + err;
+    err = check_minv_plan(S);
+    if (!err.empty()) return "merged-block plan: " + err;
   }
   for (int q = 0; q < 8; ++q) counts[q] = 0;
   counts[0] = (int64_t)S.fwd.size();
@@ -1027,9 +1349,16 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   };
   // the row ranges of a supernode solved by a DIAG entry and far chunks, per direction
   std::vector<std::vector<std::pair<int, int>>> franges(nsn), branges(nsn);
-  auto partitions = [&](std::vector<std::pair<int, int>>& rg, int r) {
+  // rows of a merged piece before ext0(s) are the columns of the later pieces of its block
+  auto ext0 = [&](int s) -> int {
+    const int g = S.sn_grp[s];
+    return g < 0 ? 0 : S.sn_start[S.grp_last[g] + 1] - S.sn_start[s + 1];
+  };
+  for (int g = 0; g < (int)S.grp_first.size(); ++g)
+    for (int s = S.grp_first[g]; s < S.grp_last[g]; ++s)
+      if (!nests(S, s)) return "merged block " + std::to_string(g) + " is not one triangle";
+  auto partitions = [&](std::vector<std::pair<int, int>>& rg, int r, int at = 0) {
     std::sort(rg.begin(), rg.end());
-    int at = 0;
     for (auto& q : rg) {
       if (q.second == q.first) continue;           // an empty range (a root without rows)
       if (q.first != at || q.second < q.first) return false;
@@ -1042,6 +1371,26 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   std::vector<int64_t> arrive_last(nsn, -1), arrive_cnt(nsn, 0);
   std::vector<int64_t> chunk_entry;   // entries holding far chunks, with their supernode
   std::vector<int32_t> chunk_sn;
+  // merged pieces: column pieces covered by the MGEMV entries of each row tile, and the first
+  // MGEMV entry that reads a piece's values
+  std::vector<std::vector<int>> fcols(nsn), bcols(nsn);
+  std::vector<int64_t> fread(nsn, INT64_MAX), bread(nsn, INT64_MAX), bgrp_last(S.grp_first.size(), -1);
+  std::vector<int> fslots, bslots;
+  auto mgemv_ok = [&](const SolveTask& T, bool fwd) -> std::string {
+    const int g = T.grp;
+    if (g < 0 || g >= (int)S.grp_first.size() || S.sn_grp[T.sn] != g) return "bad block";
+    if (T.r0 >= T.r1 || S.sn_grp[T.r0] != g || S.sn_grp[T.r1 - 1] != g) return "columns outside the block";
+    if (fwd ? (T.r1 - 1 > T.sn) : (T.r0 < T.sn)) return "columns outside the triangle";
+    const int64_t W = S.grp_W[g], c0 = S.grp_c0[g];
+    if (T.r != W || T.c0 != S.sn_start[T.sn] || T.w != S.sn_start[T.sn + 1] - S.sn_start[T.sn] ||
+        T.o_off != S.sn_start[T.r0] || T.row_off != S.sn_start[T.r1] ||
+        T.d_off != S.grp_moff[g] + (S.sn_start[T.sn] - c0) + (S.sn_start[T.r0] - c0) * W)
+      return "descriptor";
+    if (T.tgt0 < 0 || T.tgt0 >= S.nslots || T.wait_sn < 0 || T.wait_sn > T.tgt0 ||
+        T.tgt0 >= T.wait_sn + T.wait_cnt)
+      return "partial-sum slot";
+    return "";
+  };
   auto arrive = [&](int32_t tgt0, int32_t ntgt, int64_t e) {
     for (int q = 0; q < ntgt; ++q) {
       int t = S.fwd_tgt[tgt0 + q];
@@ -1090,10 +1439,35 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
           return "forward: unknown warp task";
         }
       }
+    } else if (T.kind == TASK_MGEMV) {
+      std::string err = mgemv_ok(T, true);
+      if (!err.empty()) return "forward: MGEMV " + err;
+      fpos[T.sn] = std::max(fpos[T.sn], e);
+      for (int j = T.r0; j < T.r1; ++j) {
+        fcols[T.sn].push_back(j);
+        fread[j] = std::min(fread[j], e);
+      }
+      fslots.push_back(T.tgt0);
     } else {
       return "forward: unknown entry";
     }
   }
+  for (int s = 0; s < nsn; ++s) {
+    const int g = S.sn_grp[s];
+    if (g < 0) {
+      if (!fcols[s].empty()) return "forward: MGEMV for a supernode outside a block";
+      continue;
+    }
+    counts[6]++;    // a merged piece is solved by CTA entries (its row tile's MGEMV tasks)
+    std::sort(fcols[s].begin(), fcols[s].end());
+    for (int j = S.grp_first[g]; j <= s; ++j)
+      if (fcols[s].size() != (size_t)(s - S.grp_first[g] + 1) || fcols[s][j - S.grp_first[g]] != j)
+        return "forward: row tile " + std::to_string(s) + " does not cover its columns once";
+    if (arrive_last[s] >= fread[s]) return "forward: an arrival comes after an MGEMV read";
+  }
+  std::sort(fslots.begin(), fslots.end());
+  for (size_t q = 1; q < fslots.size(); ++q)
+    if (fslots[q] == fslots[q - 1]) return "forward: two MGEMV entries share a slot";
   for (int s = 0; s < nsn; ++s) {
     if (fpos[s] < 0) return "forward: supernode " + std::to_string(s) + " never computed";
     if (arrive_cnt[s] != S.fwd_expect[s]) return "forward: arrival count mismatch";
@@ -1102,7 +1476,8 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
   for (size_t q = 0; q < chunk_entry.size(); ++q)
     if (fpos[chunk_sn[q]] >= chunk_entry[q]) return "forward: far chunk before its DIAG";
   for (int s = 0; s < nsn; ++s)
-    if (!franges[s].empty() && !partitions(franges[s], nrows(s)))
+    if ((!franges[s].empty() || (S.sn_grp[s] >= 0 && ext0(s) < nrows(s))) &&
+        !partitions(franges[s], nrows(s), ext0(s)))
       return "forward: the row chunks of supernode " + std::to_string(s) +
              " do not cover its rows exactly once";
   // ---- backward
@@ -1157,15 +1532,46 @@ std::string check_solve_plan(const Symbolic& S, int64_t counts[8]) {
           return "backward: unknown warp task";
         }
       }
+    } else if (T.kind == TASK_MGEMV) {
+      std::string err = mgemv_ok(T, false);
+      if (!err.empty()) return "backward: MGEMV " + err;
+      bgrp_last[T.grp] = std::max(bgrp_last[T.grp], e);
+      for (int j = T.r0; j < T.r1; ++j) {
+        bcols[T.sn].push_back(j);
+        bread[j] = std::min(bread[j], e);
+      }
+      bslots.push_back(T.tgt0);
     } else {
       return "backward: unknown entry";
     }
   }
+  // a merged block's pieces complete together, with its last MGEMV entry
+  for (int s = 0; s < nsn; ++s) {
+    const int g = S.sn_grp[s];
+    if (g < 0) {
+      if (!bcols[s].empty()) return "backward: MGEMV for a supernode outside a block";
+      continue;
+    }
+    if (bpos[s] >= 0) return "backward: a merged piece has its own entry";
+    bpos[s] = bgrp_last[g];
+    counts[7]++;
+    std::sort(bcols[s].begin(), bcols[s].end());
+    if (bcols[s].size() != (size_t)(S.grp_last[g] - s + 1))
+      return "backward: row tile " + std::to_string(s) + " does not cover its columns once";
+    for (size_t q = 0; q < bcols[s].size(); ++q)
+      if (bcols[s][q] != s + (int)q)
+        return "backward: row tile " + std::to_string(s) + " does not cover its columns once";
+    if (chunks_last[s] >= bread[s]) return "backward: a far chunk comes after an MGEMV read";
+  }
+  std::sort(bslots.begin(), bslots.end());
+  for (size_t q = 1; q < bslots.size(); ++q)
+    if (bslots[q] == bslots[q - 1]) return "backward: two MGEMV entries share a slot";
   for (int s = 0; s < nsn; ++s) {
     if (bpos[s] < 0) return "backward: supernode " + std::to_string(s) + " never computed";
     if (chunks_cnt[s] != S.bwd_nchunk[s]) return "backward: chunk count mismatch";
     if (chunks_last[s] >= bpos[s]) return "backward: a far chunk comes after its DIAG";
-    if (!branges[s].empty() && !partitions(branges[s], nrows(s)))
+    if ((!branges[s].empty() || (S.sn_grp[s] >= 0 && ext0(s) < nrows(s))) &&
+        !partitions(branges[s], nrows(s), ext0(s)))
       return "backward: the row chunks of supernode " + std::to_string(s) +
              " do not cover its rows exactly once";
   }

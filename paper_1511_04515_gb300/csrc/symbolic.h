@@ -26,6 +26,13 @@ struct SymbolicOptions {
   int lane_width = 4;        // are solved one per lane (32 per warp task); 0 rows disables
   int lane_min_level = 4096; // ... on levels with at least this many of them (narrower levels
                              // are latency-bound and get a warp per supernode)
+  int merge_min_width = 192; // chains of supernodes forming one dense triangular block of at
+                             // least this many columns are solved as one merged block through
+                             // the explicit inverse of its triangle (0 disables)
+  int merge_max_width = 16384;
+  int merge_pad_pct = 25;    // explicit zeros allowed to make a near-nested child nest (% of
+                             // its own off-diagonal panel)
+  int merge_col_block = 8;   // pieces per column block of a merged block's GEMV task
 };
 
 // Work entry of the triangular-solve kernels.  A CTA takes one entry at a time:
@@ -34,7 +41,7 @@ struct SymbolicOptions {
 //   OFF   : a further row chunk [r0, r1) of a large supernode (one warp);
 //   BULK  : up to 8 OFF chunks (a..a+b-1 in the chunk list), one per warp.
 enum TaskKind : int32_t { TASK_FUSED = 0, TASK_DIAG = 1, TASK_OFF = 2, TASK_GROUP = 3,
-                          TASK_BULK = 4, TASK_LANES = 5 };
+                          TASK_BULK = 4, TASK_LANES = 5, TASK_MGEMV = 6 };
 
 struct SolveTask {
   int32_t kind;
@@ -44,8 +51,30 @@ struct SolveTask {
   int32_t wait_sn;      // backward: supernode whose completion the task waits for
   int32_t wait_cnt;     // forward DIAG/FUSED: arrivals expected; backward DIAG: far chunks
   int32_t c0, w, r;     // the supernode's first column, width and off-diagonal row count
-  int32_t pad;
+  int32_t grp;          // merged block of the supernode (-1: none); OFF chunks of a merged
+                        // piece read z from / accumulate into the block buffer Z
   int64_t d_off, o_off, row_off;  // offsets of its diagonal block, panels and row list
+};
+// TASK_MGEMV (a CTA entry): one row tile (piece sn) of a merged block times the column pieces
+// [r0, r1) of the block's explicit inverse M (lower M_L forward, upper M_U backward):
+//   partial = M[rows of sn, columns of r0..r1-1] v, v = y (forward) or Z (backward);
+// tgt0 = its partial-sum slot, wait_sn = the first slot of its row tile, wait_cnt = the tasks
+// of its row tile, grp = the block, c0 / w = the piece's columns, r = ld of M (the block
+// width), d_off = offset of M[row o_sn, column o_r0] in the M storage, o_off = first column of
+// the column range, row_off = last column + 1.  The last task of a row tile sums the slots in
+// order and writes the tile (Z forward, y backward).
+
+// Inversion job of a merged block (after the refactor): C = alpha op(A) op(B) or a copy.
+enum MJobKind : int32_t { MJOB_COPY = 0, MJOB_COPYT = 1, MJOB_GEMM = 2 };
+enum MArr : int32_t { MARR_LDI = 0, MARR_UDI = 1, MARR_LO = 2, MARR_UO = 3, MARR_ML = 4,
+                      MARR_MU = 5, MARR_SCR = 6 };
+enum MTri : int32_t { MTRI_A_LOWER = 1, MTRI_A_UPPER = 2, MTRI_B_LOWER = 4, MTRI_B_UPPER = 8 };
+struct MJob {
+  int32_t kind, m, n, k;
+  int32_t a_arr, b_arr, c_arr, tri;
+  int32_t lda, ldb, ldc, pad;
+  int64_t a_off, b_off, c_off;
+  double alpha;
 };
 
 struct Symbolic {
@@ -100,6 +129,20 @@ struct Symbolic {
   // lane items of TASK_LANES warp tasks, 4 ints each: forward (sn, tgt0, ntgt, expected
   // arrivals), backward (sn, parent, 0, 0)
   std::vector<int32_t> fwd_lane, bwd_lane;
+  // merged blocks: consecutive supernodes first..last, each the parent of the previous, whose
+  // row structures nest (R(s) = columns of s+1 followed by R(s+1)), i.e. one dense W x W
+  // triangle; solved through its explicit inverse M (W x W column-major, ld W)
+  std::vector<int32_t> grp_first, grp_last, grp_c0, grp_W;
+  std::vector<int64_t> grp_moff;   // offset of the block's M in the ML / MU storage
+  int64_t m_total = 0;             // doubles of ML (and of MU)
+  std::vector<int32_t> sn_grp;     // nsn: block of each supernode (-1: none)
+  int32_t nslots = 0;              // partial-sum slots of the MGEMV tasks (per direction)
+  // inversion plan: jobs in dependency phases, each phase a list of 64 x 64 output tiles
+  std::vector<MJob> mjobs;
+  std::vector<int32_t> mphase_ptr; // tiles of phase q: mtile[mphase_ptr[q] .. mphase_ptr[q+1])
+  std::vector<int32_t> mtile;      // 2 ints per tile: job, (tile row << 16) | tile column
+  int64_t mscratch = 0;            // doubles of scratch the inversion needs
+  double minv_flops = 0.0;
   // statistics
   int64_t nnz_L = 0;               // including the diagonal
   double flops = 0.0;              // refactor flops
@@ -115,6 +158,9 @@ struct Symbolic {
 // its list, which makes the persistent solves deadlock-free.  counts[8] receives: forward and
 // backward CTA entries, lane items, warp-task supernodes, DIAG entries (fwd, bwd each).
 std::string check_solve_plan(const Symbolic& S, int64_t counts[8]);
+// Check the inversion plan of the merged blocks: every job stays inside its arrays, the tiles
+// of a job cover its output once, and a phase only reads what earlier phases wrote.
+std::string check_minv_plan(const Symbolic& S);
 
 std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const SymbolicOptions& opt,
                     Symbolic& out);

@@ -77,7 +77,9 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("solve_passes", C.c_int64),
                 ("solve_rhs", C.c_int64), ("solve_ms", C.c_double),
                 ("solve_bytes_per_pass", C.c_double), ("solve_fma_per_rhs", C.c_double),
-                ("graph_launches", C.c_int64)]
+                ("graph_launches", C.c_int64), ("merged_blocks", C.c_int64),
+                ("merged_columns", C.c_int64), ("merged_inverse_doubles", C.c_int64),
+                ("merged_inverse_flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
