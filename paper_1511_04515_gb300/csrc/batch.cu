@@ -451,7 +451,7 @@ BArgs make_bargs(ers_ctx* c, int nb, const int* slots, double* const* src, int a
   A.m_min = c->opts.m_min;
   A.m_max = c->opts.m_max;
   A.status = c->d_status;
-  A.pade = pade_coefficients();
+  A.pade = pade_coefficients(c->singular_c);
   A.mstart = c->ctrl ? c->d_mstart : nullptr;
   A.kv = c->d_kv;
   A.where = c->d_where;
@@ -460,8 +460,7 @@ BArgs make_bargs(ers_ctx* c, int nb, const int* slots, double* const* src, int a
 
 ers_status launch_bsmall(ers_ctx* c, BArgs A, int mode) {
   A.mode = mode;
-  size_t mm = (size_t)c->opts.m_max;
-  size_t sm = (6 * mm * mm + 2 * mm) * 8;
+  size_t sm = small_smem_doubles((size_t)c->opts.m_max) * 8;
   k_bsmall<<<c->ninst * A.nb, 256, sm, c->stream>>>(A);
   c->stats.kernel_launches++;
   BCU(cudaGetLastError());
@@ -492,7 +491,7 @@ cudaError_t enqueue_iteration(ers_ctx* c, const BArgs& A, int nb, int j, bool us
   BArgs S = A;
   S.mode = SMALL_RESID;
   size_t mm = (size_t)c->opts.m_max;
-  k_bsmall<<<c->ninst * nb, 256, (6 * mm * mm + 2 * mm) * 8, c->stream>>>(S);
+  k_bsmall<<<c->ninst * nb, 256, small_smem_doubles(mm) * 8, c->stream>>>(S);
   c->stats.kernel_launches++;
   if (use_jdev) {
     k_binc<<<1, 1, 0, c->stream>>>(c->bj);
@@ -597,7 +596,7 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
       if (any) {
         const int nd = j + 1 - c->opts.m_min + 1;
         size_t mm = (size_t)c->opts.m_max;
-        size_t sm = (6 * mm * mm + 2 * mm) * 8;
+        size_t sm = small_smem_doubles(mm) * 8;
         k_bscan<<<dim3(c->ninst, nb, nd), 256, sm, c->stream>>>(A, scan_buf(c), c->opts.m_min);
         k_bpick<<<c->ninst * nb, 32, 0, c->stream>>>(A, scan_buf(c));
         c->stats.kernel_launches += 2;
@@ -759,9 +758,9 @@ ers_status ers::create_batch_here(ers_ctx** out, const ers_instance* inst, int32
   c->mstart_inst.assign(ninst, c->opts.m_min);
   c->proposed_inst.assign(ninst, 0);
   BCU(cudaFuncSetAttribute(k_bsmall, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
+                           small_smem_doubles(MAX_M) * 8));
   BCU(cudaFuncSetAttribute(k_bscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (6 * MAX_M * MAX_M + 2 * MAX_M) * 8));
+                           small_smem_doubles(MAX_M) * 8));
   {
     const size_t nq = (size_t)3 * ninst * (MAX_M + 1);
     BCU(cudaMalloc((void**)&c->bscan_res, sizeof(double) * nq));

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(KB) k_absmax(int n, const double* x, unsigned 
 // ---------------------------------------------------------------------------------------
 cudaError_t krylov_init_constants() {
   return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (6 * MAX_M * MAX_M + 2 * MAX_M) * 8);
+                              small_smem_doubles(MAX_M) * 8);
 }
 
 // Grid of the cooperative vector kernels: every inner product of MGS is a grid-wide reduction
@@ -347,7 +347,7 @@ cudaError_t launch_mgs(ers_ctx* c, const VecGroup& g, int j, int adaptive) {
 
 cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int m_max) {
   SmallArgs A{};
-  A.pade = pade_coefficients();
+  A.pade = pade_coefficients(c->singular_c);
   A.mode = mode;
   A.nb = g.nb;
   for (int b = 0; b < g.nb; ++b) { A.slot[b] = g.slot[b]; A.H[b] = g.H[b]; }
@@ -357,8 +357,7 @@ cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int 
   A.m_min = c->opts.m_min;
   A.m_max = m_max;
   A.status = c->d_status;
-  size_t mm = (size_t)c->opts.m_max;
-  size_t sm = (6 * mm * mm + 2 * mm) * 8;
+  size_t sm = small_smem_doubles((size_t)c->opts.m_max) * 8;
   k_small<<<g.nb, KB, sm, c->stream>>>(A);
   c->stats.kernel_launches++;
   return cudaGetLastError();
@@ -367,7 +366,7 @@ cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int 
 cudaError_t launch_small_test(ers_ctx* c, const double* H, int ldh, int m, double h, double* y,
                               double* last) {
   SmallArgs A{};
-  A.pade = pade_coefficients();
+  A.pade = pade_coefficients(c->singular_c);
   A.mode = SMALL_TEST;
   A.h = h;
   A.Htest = H;
@@ -375,7 +374,7 @@ cudaError_t launch_small_test(ers_ctx* c, const double* H, int ldh, int m, doubl
   A.m_test = m;
   A.y_out = y;
   A.last_out = last;
-  size_t sm = (6 * (size_t)m * m + 2 * (size_t)m) * 8;
+  size_t sm = small_smem_doubles((size_t)m) * 8;
   k_small<<<1, KB, sm, c->stream>>>(A);
   return cudaGetLastError();
 }

@@ -7,13 +7,20 @@
 
 namespace ers {
 
+// Constants of the small dense stage: the [13/13] Pade coefficients, and whether the
+// near-null eigenvalues of H_m are deflated first (a C with capacitor-free nodes).
 struct PadeCoef {
   double c[14];
+  int deflate = 0;
 };
 
+// shared memory (doubles) of the small dense stage for dimension m
+constexpr size_t small_smem_doubles(size_t m) { return 6 * m * m + 10 * m; }
+
 // [q/q] Pade approximant of exp: c_k = (2q-k)! q! / ((2q)! k! (q-k)!), q = 13
-inline PadeCoef pade_coefficients() {
+inline PadeCoef pade_coefficients(int deflate = 0) {
   PadeCoef P;
+  P.deflate = deflate;
   const int q = 13;
   for (int k = 0; k <= q; ++k) {
     double v = 1.0;
@@ -40,7 +47,7 @@ __device__ inline void sm_matmul(double* C, const double* A, const double* B, in
 // LU with partial pivoting of M (m x m, column-major, in place); piv[k] = row swapped with k.
 // The pivot search is a warp arg-max (ties to the lowest row), the row swap, the scaling of
 // column k and the trailing update are spread over the CTA: two barriers per column.
-__device__ inline void sm_lu(double* M, int* piv, int m) {
+__device__ inline void sm_lu(double* M, int* piv, int m, double floor = 0.0) {
   __shared__ int s_p;
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < m; ++k) {
@@ -68,6 +75,11 @@ __device__ inline void sm_lu(double* M, int* piv, int m) {
         M[p + jj * m] = t;
       }
     __syncthreads();
+    if (floor > 0.0) {          // a pivot below the floor is raised to it (sign kept)
+      if (threadIdx.x == 0 && fabs(M[k + k * m]) < floor)
+        M[k + k * m] = M[k + k * m] < 0.0 ? -floor : floor;
+      __syncthreads();
+    }
     const double inv = 1.0 / M[k + k * m];
     const int rem = m - k - 1;
     // trailing update with the multipliers l_i = M[i,k] / M[k,k] formed on the fly (column k
@@ -112,9 +124,145 @@ __device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, 
   }
 }
 
+// x <- A^-1 x (trans = false) or A^-T x (trans = true) with the LU of sm_lu (P A = L U, L
+// unit lower; A^T = U^T L^T P).  Run by one warp; the caller synchronises around it.
+__device__ inline void warp_lu_solve_vec(const double* LU, const int* piv, double* x, int m,
+                                         bool trans) {
+  const int lane = threadIdx.x & 31;
+  if (!trans) {
+    if (lane == 0)
+      for (int k = 0; k < m; ++k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    __syncwarp();
+    for (int k = 0; k < m; ++k) {              // L y = P x
+      const double xk = x[k];
+      for (int i = k + 1 + lane; i < m; i += 32) x[i] -= LU[i + k * m] * xk;
+      __syncwarp();
+    }
+    for (int k = m - 1; k >= 0; --k) {         // U z = y
+      if (lane == 0) x[k] /= LU[k + k * m];
+      __syncwarp();
+      const double xk = x[k];
+      for (int i = lane; i < k; i += 32) x[i] -= LU[i + k * m] * xk;
+      __syncwarp();
+    }
+  } else {
+    for (int k = 0; k < m; ++k) {              // U^T w = x
+      if (lane == 0) x[k] /= LU[k + k * m];
+      __syncwarp();
+      const double xk = x[k];
+      for (int i = k + 1 + lane; i < m; i += 32) x[i] -= LU[k + i * m] * xk;
+      __syncwarp();
+    }
+    for (int k = m - 1; k >= 0; --k) {         // L^T v = w
+      const double xk = x[k];
+      for (int i = lane; i < k; i += 32) x[i] -= LU[k + i * m] * xk;
+      __syncwarp();
+    }
+    if (lane == 0)                             // x = P^T v: the row swaps undone in reverse
+      for (int k = m - 1; k >= 0; --k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    __syncwarp();
+  }
+}
+
+__device__ inline double warp_dot(const double* a, const double* b, int m) {
+  double acc = 0.0;
+  for (int i = threadIdx.x & 31; i < m; i += 32) acc += a[i] * b[i];
+  return warp_sum(acc);
+}
+
+// Deflation of the near-null eigenvalues of A = H_m (in place) for a C with capacitor-free
+// nodes, where J^-1 = -G^-1 C has the eigenvalue 0 and exp(h H^-1) takes its limit from the
+// stable side: an eigenvalue mu0 with |mu0| <= h/700 (e^{h/mu} < 1e-304 for a stiff real
+// mode; a tiny one of either sign is the rounding image of a zero) is moved to -h/800, where
+// e^{h/mu} = e^-800 is 0 in FP64, by the rank-one Wielandt update
+//     A <- A + (-h/800 - mu0) r l^T / (l^T r)
+// with r, l its right and left eigenvectors.  l^T is orthogonal to every other right
+// eigenvector, so the rest of the spectrum and its eigenvectors are unchanged.  r and l come
+// from 8 inverse iterations on the LU of A (pivots floored at 2^-52 max|A| so that an exactly
+// singular A still gives a direction), with the already deflated pairs projected out so that
+// each pass finds the next smallest eigenvalue; mu0 is the two-sided Rayleigh quotient
+// l^T A r / l^T r.  The loop stops at the first eigenvalue above h/700, or when the pair is
+// not converged (residual above 1e-8 max|A|, l^T r below 1e-10).  W: m x m scratch, R, Lv:
+// m x m (deflated pairs by column), vec: 8 m doubles.
+__device__ inline void sm_deflate(double* A, int m, double h, double* W, double* R, double* Lv,
+                                  double* vec, int* ipiv) {
+  const double tau = h / 700.0, delta = h / 800.0;
+  double* x = vec;
+  double* y = vec + m;
+  double* t = vec + 2 * m;
+  double* dk = vec + 3 * m;
+  __shared__ double s_nrm, s_mu, s_d;
+  __shared__ int s_ok;
+  if (threadIdx.x < 32) {
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < m * m; e += 32) mx = fmax(mx, fabs(A[e]));
+    mx = warp_max(mx);
+    if (threadIdx.x == 0) s_nrm = mx;
+  }
+  __syncthreads();
+  const double nrm = s_nrm;
+  const double floor = fmax(1e-300, 2.220446049250313e-16 * nrm);
+  for (int nd = 0; nd < m; ++nd) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) W[e] = A[e];
+    __syncthreads();
+    sm_lu(W, ipiv, m, floor);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const double v0 = rsqrt((double)m);
+      for (int i = lane; i < m; i += 32) { x[i] = v0; y[i] = v0; }
+      __syncwarp();
+      for (int it = 0; it < 8; ++it) {
+        warp_lu_solve_vec(W, ipiv, x, m, false);
+        warp_lu_solve_vec(W, ipiv, y, m, true);
+        for (int q = 0; q < nd; ++q) {          // project out the deflated pairs
+          const double* rq = R + q * m;
+          const double* lq = Lv + q * m;
+          const double cx = warp_dot(lq, x, m) / dk[q];
+          const double cy = warp_dot(rq, y, m) / dk[q];
+          for (int i = lane; i < m; i += 32) { x[i] -= cx * rq[i]; y[i] -= cy * lq[i]; }
+          __syncwarp();
+        }
+        const double nx = sqrt(warp_dot(x, x, m)), ny = sqrt(warp_dot(y, y, m));
+        for (int i = lane; i < m; i += 32) { x[i] /= nx; y[i] /= ny; }
+        __syncwarp();
+      }
+      for (int i = lane; i < m; i += 32) {     // t = A x
+        double acc = 0.0;
+        for (int j = 0; j < m; ++j) acc += A[i + j * m] * x[j];
+        t[i] = acc;
+      }
+      __syncwarp();
+      const double d = warp_dot(y, x, m);
+      const double mu = warp_dot(y, t, m) / d;
+      double res = 0.0;
+      for (int i = lane; i < m; i += 32) res = fmax(res, fabs(t[i] - mu * x[i]));
+      res = warp_max(res);
+      if (lane == 0) {
+        s_ok = isfinite(d) && isfinite(mu) && fabs(d) >= 1e-10 && fabs(mu) <= tau &&
+               res <= 1e-8 * nrm;
+        s_mu = mu;
+        s_d = d;
+      }
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const double c = (-delta - s_mu) / s_d;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      A[e] += c * x[i] * y[j];
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) { R[nd * m + i] = x[i]; Lv[nd * m + i] = y[i]; }
+    if (threadIdx.x == 0) dk[nd] = s_d;
+    __syncthreads();
+  }
+}
+
 // y = exp(h H^-1) e_1 for the leading m x m block of H (ld ldh); last = e_m^T H^-1 y.
-// Scaling and squaring of the diagonal [13/13] Pade approximant (theta_13 = 5.37).
-// Returns true when y and last are finite.  smem: 6 m^2 doubles + scratch.
+// Scaling and squaring of the diagonal [13/13] Pade approximant (theta_13 = 5.37), after the
+// deflation of near-null eigenvalues when pade.deflate is set (C with capacitor-free nodes).
+// Returns true when y and last are finite.  smem: small_smem_doubles(m) doubles.
 __device__ inline bool phi_small(const double* H, int ldh, int m, double h, double* y,
                                  double* last, double* smem, int* ipiv, const PadeCoef& pade) {
   const double* c_pade = pade.c;
@@ -134,6 +282,7 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
     M1[e] = (i == jj) ? h : 0.0;
   }
   __syncthreads();
+  if (pade.deflate) sm_deflate(M0, m, h, M2, M3, M4, vec + m, ipiv);
   sm_lu(M0, ipiv, m);
   sm_lu_solve(M0, ipiv, M1, m);          // M1 = X = h H^-1
   for (int k = threadIdx.x; k < m; k += blockDim.x) lastrow[k] = M1[(m - 1) + k * m] / h;
