@@ -35,7 +35,8 @@ FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32
 # the 70^3 mesh (2.663 GB measured vs 2.553 GB algorithmic); the full-size traffic is this ratio
 # times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
 # k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
-SOLVE_TRAFFIC_RATIO = 2.6626 / 2.5525
+SOLVE_TRAFFIC_RATIO = None
+SOLVE_TRAFFIC_SOURCE = "ncu dram bytes of the 70^3 pair scaled by algorithmic bytes"
 CLOCKS_DIR = os.environ.get("ERS_CLOCKS_DIR") or os.path.join(ROOT, ".bench")   # nvidia-smi samples
 L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
 FLUSH_BYTES = 256 * 2 ** 20
@@ -52,6 +53,8 @@ def parse():
     p.add_argument("--size", type=int, default=100, help="mesh edge (workload: 100)")
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    p.add_argument("--no-extras", action="store_true",
+                   help="main line only (no accuracy run, config [0] / [2] / batch sub-lines)")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--workload", default="mesh", choices=["mesh", "chain", "batch", "solve"])
     p.add_argument("--ordering", type=int, default=0, help="ers_opts.ordering (0 or 1)")
@@ -166,7 +169,7 @@ def run_oracle_sample(steps=SAMPLE_STEPS, size=SAMPLE_SIZE, kind="mesh", stages=
     what = (f"the {size}^3 mesh ({r['n']} nodes, same generator and seed) from x = 0"
             if kind == "mesh" else
             f"the {stages}-stage chain ({r['n']} nodes, same generator and seed) from DC")
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "n_sample": r["n"],
             "sample": (f"first {r['steps']} adaptive ER steps of {what}, the oracle's own "
                        f"sparse LU + numpy, 1 thread, {r['seconds']:.1f} s; steps/s on the "
                        f"sample, not scaled to the full workload"),
@@ -214,6 +217,99 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def timed_adaptive(sim, t_end, tol, steps, stream, factor_bytes):
+    """Time `steps` accepted Algorithm-2 steps on the library's stream with CUDA events: back to
+    back when the factor exceeds L2, else each step after a 256 MB write that evicts L2 (the
+    write outside the per-step events).  Returns (ms, steps, rejects, l2 note)."""
+    import torch
+    if factor_bytes > L2_BYTES:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ns, nr = sim.run(t_end, 1e-6 if tol is None else tol, max_steps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), ns, nr, "inputs larger than L2 (factor values alone exceed 129 MB)"
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    ns = nr = 0
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k)
+        evs[k][0].record(stream)
+        s_k, r_k = sim.run(t_end, tol, max_steps=1)
+        evs[k][1].record(stream)
+        ns += s_k
+        nr += r_k
+    torch.cuda.synchronize()
+    note = (f"L2 flushed before every step ({FLUSH_BYTES >> 20} MB write on the library's "
+            f"stream, outside the per-step events): the factor is {factor_bytes / 1e6:.1f} MB")
+    return sum(b.elapsed_time(c) for b, c in evs), ns, nr, note
+
+
+def chain_line(ers, stream, steps=10, warmup=3):
+    """Config [2]: the 2000-stage inverter chain with 100-node RC trees, refactor of G_k every
+    step, adaptive h (tol 1e-6, eps 1e-7), steps from DC on the first input edge."""
+    import torch
+    circ = workload(0, "chain", 2000)
+    t_end = workload_t_end("chain")
+    sim = ers.Simulator.from_circuit(circ, opts=ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100))
+    sim.set_stream(stream)
+    sim.dc(circ.nodeset)
+    tuned, _ = sim.autotune(nrhs=2, passes=3)
+    sim.run(t_end, 1e-6, max_steps=warmup)
+    torch.cuda.synchronize()
+    st0 = sim.stats()
+    ms, ns, nr, note = timed_adaptive(sim, t_end, 1e-6, steps, stream, st0["factor_doubles"] * 8)
+    st1 = sim.stats()
+    out = {"workload": workload_name(0, "chain", 2000), "n": circ.n, "steps": int(ns),
+           "rejects": int(nr), "ms_per_step": ms / max(ns, 1), "steps_per_s": ns / (ms * 1e-3),
+           "krylov_vectors_per_s": (st1["krylov_vectors"] - st0["krylov_vectors"]) / (ms * 1e-3),
+           "refactors": st1["refactors"] - st0["refactors"],
+           "gpu_launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / max(ns, 1),
+           "solve_ctas_per_sm": tuned, "l2_flush": note}
+    sim.close()
+    return out
+
+
+def mesh2d_line(ers, stream, steps=1000):
+    """Config [0]: the 32 x 32 RC mesh, plain ER at fixed h = 1 ps and m = 20 from x = 0 over
+    1 ns (1000 steps; the pulse corners lie on the 1 ps grid)."""
+    import numpy as np
+    import torch
+    from synth import circuits as S
+    circ = S.rc_mesh_2d(32, 32, seed=0)
+    sim = ers.Simulator.from_circuit(circ)
+    sim.set_stream(stream)
+    sim.set_state(0.0, np.zeros(circ.n))
+    sim.step(1e-12, 20)                       # factor G once, warm the kernels
+    sim.set_state(0.0, np.zeros(circ.n))
+    torch.cuda.synchronize()
+    st0 = sim.stats()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        flush.fill_(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(1e-12, 20)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = sim.stats()
+    out = {"workload": "rc2d_32x32: linear 2D RC mesh (1024 nodes), 16 pulse sources, fixed "
+                       "h = 1 ps, Krylov m = 20, 1000 steps over 1 ns from x = 0",
+           "steps": steps, "ms_per_step": ms / steps, "steps_per_s": steps / (ms * 1e-3),
+           "krylov_vectors_per_s": (st1["krylov_vectors"] - st0["krylov_vectors"]) / (ms * 1e-3),
+           "gpu_launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / steps,
+           "l2_flush": ("one 256 MB write before the run; the 1024-node factor stays in L2 "
+                        "across the 1000 steps of the run, as in any use of this size")}
+    sim.close()
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -245,6 +341,7 @@ def run_ours(a):
     tuned, tune_ms = sim.autotune(nrhs=2, passes=3)     # resident CTAs per SM of the solves
     if a.warmup:
         sim.run(t_end, a.tol, max_steps=a.warmup)
+    t_start, x_start, h_start = sim.state()   # start of the timed window (accuracy check)
     sim.profile(True)
     st0 = sim.stats()
     if world > 1:
@@ -255,37 +352,7 @@ def run_ours(a):
     proc, fh = clocks_start(local, clk_path)
     factor_bytes = st0["factor_doubles"] * 8
     torch.cuda.nvtx.range_push("ers_timed")
-    if factor_bytes > L2_BYTES:
-        # the factor streams from HBM on every solve: steps run back to back
-        l2_note = "inputs larger than L2 (factor values alone exceed 129 MB)"
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ns, nr = sim.run(t_end, a.tol, max_steps=a.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-    else:
-        # the factor fits in L2: write 256 MB on the library's stream before every step and
-        # time each step with its own events, so no step starts from the previous one's cache
-        l2_note = (f"L2 flushed before every step ({FLUSH_BYTES >> 20} MB write on the "
-                   f"library's stream, outside the per-step events): the factor is "
-                   f"{factor_bytes / 1e6:.1f} MB")
-        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(a.steps)]
-        ns = nr = 0
-        for k in range(a.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k)
-            evs[k][0].record(stream)
-            s_k, r_k = sim.run(t_end, a.tol, max_steps=1)
-            evs[k][1].record(stream)
-            ns += s_k
-            nr += r_k
-        torch.cuda.synchronize()
-        ms = sum(b.elapsed_time(c) for b, c in evs)
-        del flush
+    ms, ns, nr, l2_note = timed_adaptive(sim, t_end, a.tol, a.steps, stream, factor_bytes)
     torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
@@ -329,7 +396,15 @@ def run_ours(a):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = (clocks or {}).get("sm_max_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = nsm * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
+    derived_peak = nsm * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    try:          # the FP64 FMA rate measured on this GPU now (a library kernel)
+        alu_peak = ers.fp64_fma_peak(local)
+        peak_src = ("measured: ers_fp64_fma_peak on this GPU (8 independent FMA chains per "
+                    "thread, 8 x 256 threads per SM, best of 5, CUDA events)")
+    except Exception:
+        alu_peak = derived_peak
+        peak_src = (f"derived: {nsm} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 flops x "
+                    f"{sm_max:.0f} MHz")
     solve_bytes = st1["solve_bytes_per_pass"] * passes + 16.0 * n * rhs
     solve_flops = 2.0 * st1["solve_fma_per_rhs"] * rhs
     avg_ms = solve_ms / max(passes, 1)
@@ -339,14 +414,14 @@ def run_ours(a):
                if SOLVE_TRAFFIC_RATIO is not None else None)
     if tfs / alu_peak >= gbs / hbm:
         roof = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": tfs / alu_peak, "traffic": traffic,
-                "peak_source": (f"derived: {nsm} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 "
-                                f"flops x {sm_max:.0f} MHz")}
+                "frac": tfs / alu_peak, "traffic": traffic, "peak_source": peak_src,
+                "derived_peak": derived_peak}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof.update({"kernel": "k_trsv_fwd + k_trsv_bwd (one supernodal solve pair)",
-                 "traffic_source": "ncu dram bytes of the 70^3 pair scaled by algorithmic bytes",
+                 "traffic_source": (SOLVE_TRAFFIC_SOURCE if traffic is not None else
+                                    "no capture of the current solve kernels"),
                  "launches": passes, "avg_ms": avg_ms, "bytes_per_launch": solve_bytes / max(passes, 1),
                  "flops_per_launch": solve_flops / max(passes, 1), "hbm_GBps": gbs,
                  "share_of_step_time": solve_ms / ms if ms else None})
@@ -370,13 +445,39 @@ def run_ours(a):
             "clocks": clocks,
             "e2e": {"value": k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n}}
+    line["node_steps_per_s"] = line["value"] * n
+    # accuracy of the timed window ("rel err 1e-6" of the metric): the same window from the
+    # same start state in a second context with a Krylov eps 1000x and a tol 10x tighter
+    t_stop, x_stop, _ = sim.state()
+    sim.close()
+    if world == 1 and not a.no_extras:
+        ref = ers.Simulator.from_circuit(
+            circ, opts=ers.make_opts(eps_krylov=1e-10, h_max=t_end / 100, ordering=a.ordering))
+        ref.set_stream(stream)
+        ref.set_state(t_start, x_start, h_start)
+        ref.run(t_stop, a.tol / 10)
+        _, x_ref, _ = ref.state()
+        ref.close()
+        line["accuracy"] = {
+            "rel_err_vs_tight_run": float(np.max(np.abs(x_stop - x_ref)) / np.max(np.abs(x_ref))),
+            "window_s": [t_start, t_stop],
+            "reference": "same start state and window, Krylov eps 1e-10 and tol 1e-7"}
     if not a.no_baseline and world == 1:
         try:
-            line["cpu_baseline"] = run_oracle_sample(*oracle_args(a))
+            cb = run_oracle_sample(*oracle_args(a))
+            cb["node_steps_per_s"] = cb["value"] * cb.pop("n_sample")
+            line["cpu_baseline"] = cb
         except Exception as ex:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "error": str(ex)[-300:]}
+    if world == 1 and not a.no_extras and kind == "mesh":
+        # the metric's other configurations, each under its own key
+        line["config0_mesh2d"] = mesh2d_line(ers, stream)
+        line["config2_chain"] = chain_line(ers, stream)
+        ba = argparse.Namespace(**vars(a))
+        ba.seq_sample = min(a.seq_sample, 2)
+        ba.warmup = max(a.warmup, 3)
+        line["batched_plain_vs_learned"] = run_batch_workload(ba, emit=False)
     print(json.dumps(line), flush=True)
-    sim.close()
 
 
 # --------------------------------------------------------------------------------------
@@ -463,12 +564,14 @@ def batch_oracle_baseline(circs, idx, t_end, tol):
                        f"{[round(r[1], 1) for r in res]}")}
 
 
-def run_batch_workload(a):
+def run_batch_workload(a, emit=True):
+    """The batch comparison; prints its JSON line (emit) or returns it (embedded in the main
+    line, rank 0 of a one-rank job)."""
     import numpy as np
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1511_04515_gb300 import build
@@ -638,6 +741,8 @@ def run_batch_workload(a):
             "krylov_vectors_per_s": learned["krylov_vectors"] / learned["seconds"],
             "gpu_launches": learned["gpu_launches"],
             "clocks": clocks}
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
 
 

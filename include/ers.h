@@ -437,6 +437,14 @@ ers_status ers_plan_array(const ers_csr* pattern, const ers_opts* opts, int32_t 
  * n part numbers.  ERS_ERR_INVALID for a negative or non-finite cost. */
 ers_status ers_partition_lpt(const double* cost, int32_t n, int32_t nparts, int32_t* part_of);
 
+/* Measured FP64 FMA rate of a device, the roofline denominator of the FP64 solves (not in the
+ * paper; GB300 issues FP64 at 1/64 of its FP32 rate, so the supernodal solves, one FMA per
+ * 8-byte factor value, are bound by it rather than by HBM).  Times a kernel of 8 independent
+ * FMA chains per thread on 8 CTAs of 256 threads per SM with CUDA events, best of 5 after a
+ * warm-up launch; *tflops receives 2 x FMAs / time.  ERS_ERR_INVALID for a device that does
+ * not exist. */
+ers_status ers_fp64_fma_peak(int32_t device, double* tflops);
+
 /* Statistics and symbolic-analysis figures.  Synchronises the context's stream. */
 ers_status ers_stats(const ers_ctx* ctx, ers_stats_t* out);
 /* Turn CUDA-event timing of the triangular-solve kernels on (1) or off (0); resets the

@@ -127,6 +127,22 @@ __global__ void k_rhs_C(RhsArgs A, const int32_t* ptr, const int32_t* idx, const
   }
 }
 
+// FP64 FMA rate probe: 8 independent dependency chains per thread (enough independent work to
+// keep the FP64 pipe busy at full occupancy), the result kept live through a store.
+__global__ void __launch_bounds__(256) k_fma_probe(double* out, int iters) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-9 * (threadIdx.x + 37 * k);
+  const double b = 0.9999999999, c = 1e-13;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == 12345.0) out[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
 }  // namespace ers
 
 using namespace ers;
@@ -1285,6 +1301,43 @@ ers_status ers_profile(ers_ctx* c, int32_t enable) {
   if (st != ERS_OK) return st;
   c->profile = enable != 0;
   c->stats.solve_ms = 0.0;
+  return ERS_OK;
+}
+
+ers_status ers_fp64_fma_peak(int32_t device, double* tflops) {
+  if (!tflops) return ERS_ERR_INVALID;
+  *tflops = 0.0;
+  if (!check_device_list(&device, 1).empty()) return ERS_ERR_INVALID;
+  DeviceGuard dg(device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    return ERS_ERR_CUDA;
+  const int blocks = sms * 8, iters = 4096;
+  double* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, sizeof(double) * blocks);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = INFINITY;
+  for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {   // the first launch warms up
+    e = cudaEventRecord(e0, st);
+    k_fma_probe<<<blocks, 256, 0, st>>>(out, iters);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess || !(best > 0.f)) return ERS_ERR_CUDA;
+  const double fma = (double)blocks * 256 * 8 * iters;
+  *tflops = 2.0 * fma / (best * 1e-3) / 1e12;
   return ERS_OK;
 }
 

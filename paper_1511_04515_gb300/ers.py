@@ -96,7 +96,7 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
            "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check",
-           "ers_wait_selftest", "ers_plan_array", "ers_partition_lpt"]
+           "ers_wait_selftest", "ers_plan_array", "ers_partition_lpt", "ers_fp64_fma_peak"]
 
 _lib = None
 
@@ -139,6 +139,7 @@ def lib():
         "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, pi, I32, C.POINTER(Opts)],
                              C.c_int),
         "ers_partition_lpt": ([pd, I32, I32, pi], C.c_int),
+        "ers_fp64_fma_peak": ([I32, pd], C.c_int),
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
         "ers_analyze": ([C.POINTER(Csr), C.POINTER(Opts), C.POINTER(Stats), pi], C.c_int),
@@ -187,6 +188,15 @@ def _device_list(devices):
     ptr = arr.ctypes.data_as(C.POINTER(C.c_int32))
     ptr._keep = arr
     return ptr, int(arr.size)
+
+
+def fp64_fma_peak(device: int = 0) -> float:
+    """Measured FP64 FMA rate of a device in TFLOP/s (see ers.h)."""
+    v = C.c_double(0.0)
+    rc = lib().ers_fp64_fma_peak(int(device), C.byref(v))
+    if rc != 0:
+        raise ErsError(rc, "FP64 peak probe failed")
+    return v.value
 
 
 def partition_lpt(costs, nparts: int) -> np.ndarray:

@@ -22,7 +22,7 @@ def E():
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "ers.h")).read()
-    return sorted(set(re.findall(r"\b(ers_[A-Za-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ers_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_binding_exports(E):
