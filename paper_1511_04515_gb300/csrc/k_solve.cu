@@ -149,40 +149,57 @@ __device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
-// Column sums of a 32-row slab times x over 16 columns, lanes over rows: lane i holds
-// p[c] = U[i, cb + c] x_i (coalesced loads: one row per lane), and a recursive-halving
-// exchange over lane bits 3..0 (each step keeps half of the columns and adds the partner's
-// half) leaves the sum over 16 lanes of column cb + (lane & 15) in p[0]; the last xor over
-// bit 4 adds the other 16 lanes.  About one shuffle per column instead of a full warp
-// reduction per column.
-template <int NRHS>
-__device__ __forceinline__ void warp_colsum16(const double* urow, int64_t ld, int ncols, bool act,
-                                              const double (&xr)[NRHS], double (&out)[NRHS],
-                                              int lane) {
-  double u[16];
+// Cross-lane sums of 8 per-lane accumulators: lane i holds p[c] (its rows' contribution to
+// column cb + c); a recursive-halving exchange over lane bits 2..0 (each step keeps half of
+// the columns and adds the partner's half) leaves the sum over 8 lanes of column
+// cb + (lane & 7) in p[0], and xors over bits 3 and 4 add the other 24 lanes: 9 adds and
+// 9 shuffles for 8 columns, once per column block after the FMAs of all its rows.
+__device__ __forceinline__ double warp_reduce8(double (&p)[8], int lane) {
 #pragma unroll
-  for (int c = 0; c < 16; ++c) u[c] = (act && c < ncols) ? __ldg(urow + (int64_t)c * ld) : 0.0;
+  for (int off = 4; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
 #pragma unroll
-  for (int k = 0; k < NRHS; ++k) {
-    double p[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) p[c] = u[c] * xr[k];
-#pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
-      const bool upper = (lane & off) != 0;
-#pragma unroll
-      for (int c = 0; c < off; ++c) {
-        const double send = upper ? p[c] : p[c + off];
-        const double keep = upper ? p[c + off] : p[c];
-        p[c] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-      }
+    for (int c = 0; c < off; ++c) {
+      const double send = upper ? p[c] : p[c + off];
+      const double keep = upper ? p[c + off] : p[c];
+      p[c] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
-    out[k] = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 16);
   }
+  double v = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 8);
+  return v + __shfl_xor_sync(0xffffffffu, v, 16);
+}
+
+// Column sums over the slabs of 32 rows a warp owns, lanes over rows (coalesced panel loads):
+// out[k] on lane l = sum_i U[i, cb + (l & 7)] x_i[k] over rows i = i0 + lane + 32 q < i1,
+// q < MAXSLAB; FMAs per row, one warp_reduce8 per right-hand side.
+template <int NRHS, int MAXSLAB>
+__device__ __forceinline__ void warp_colsum8(const double* U, int64_t ld, int cb, int ncols,
+                                             int i0, int i1, const double (&xr)[MAXSLAB][NRHS],
+                                             double (&out)[NRHS], int lane) {
+  double acc[NRHS][8];
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[k][c] = 0.0;
+#pragma unroll
+  for (int q = 0; q < MAXSLAB; ++q) {
+    const int i = i0 + lane + 32 * q;
+    if (i0 + 32 * q >= i1) break;
+    const bool act = i < i1;
+    const double* urow = U + i + (int64_t)cb * ld;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const double u = (act && c < ncols) ? __ldg(urow + (int64_t)c * ld) : 0.0;
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k][c] = fma(u, xr[q][k], acc[k][c]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NRHS; ++k) out[k] = warp_reduce8(acc[k], lane);
 }
 
 // one small supernode, backward, by one warp: xs = y_s - U12 x_R with lanes over the rows R
-// (16-column sums by warp_colsum16), then x_s = U11^-1 xs
+// (8-column sums by warp_colsum8), then x_s = U11^-1 xs
 template <int NRHS>
 __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*xs)[64]) {
   const DevicePlan& P = A.P;
@@ -201,26 +218,25 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) xs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
   __syncwarp();
-  // column sums, one 16-column block at a time over all row slabs
-  for (int cb = 0; cb < w; cb += 16) {
-    double tot[NRHS];
+  // column sums, 64 rows at a time (x of the rows in registers), 8 columns per block
+  for (int i0 = 0; i0 < r; i0 += 64) {
+    double xr[2][NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) tot[k] = 0.0;
-    for (int i0 = 0; i0 < r; i0 += 32) {
-      const int i = i0 + lane;
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + lane + 32 * q;
       const bool act = i < r;
-      double xr[NRHS];
       const int row = act ? __ldg(R + i) : 0;
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k) xr[k] = act ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
-      double v[NRHS];
-      warp_colsum16<NRHS>(Uo + i + (int64_t)cb * r, r, min(16, w - cb), act, xr, v, lane);
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) tot[k] += v[k];
+      for (int k = 0; k < NRHS; ++k) xr[q][k] = act ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
     }
-    if (lane < 16 && cb + lane < w)
+    for (int cb = 0; cb < w; cb += 8) {
+      double v[NRHS];
+      warp_colsum8<NRHS, 2>(Uo, r, cb, min(8, w - cb), i0, min(r, i0 + 64), xr, v, lane);
+      if (lane < 8 && cb + lane < w)
 #pragma unroll
-      for (int k = 0; k < NRHS; ++k) xs[k][cb + lane] -= tot[k];
+        for (int k = 0; k < NRHS; ++k) xs[k][cb + lane] -= v[k];
+      __syncwarp();
+    }
   }
   __syncwarp();
   double z[2][NRHS];
@@ -410,8 +426,10 @@ __device__ void fwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   __syncwarp();
 }
 
-// a far chunk, backward, one warp: y[c0 + j] -= sum_{i in chunk} Uo[i + j r] x[R[i]], lanes
-// over the chunk's rows (coalesced panel loads) and 16-column sums by warp_colsum16
+// a far chunk, backward, one warp: y[c0 + j] -= sum_{i in chunk} Uo[i + j r] x[R[i]] over up
+// to BCH rows, lanes over rows (coalesced panel loads), FMAs over the chunk's slabs and one
+// 8-column exchange per block (warp_colsum8)
+constexpr int BCH = 128;         // rows of a backward far chunk (SymbolicOptions::bwd_chunk)
 template <int NRHS>
 __device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, double* buf) {
   const DevicePlan& P = A.P;
@@ -422,22 +440,25 @@ __device__ void bwd_chunk(const SolveArgs& A, const SolveTask& T, int lane, doub
   const double* Uo = P.Uo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
   (void)buf;
-  const int i = T.r0 + lane;
-  const bool act = i < T.r1;
-  const int myrow = act ? __ldg(R + i) : 0;
   int ok = 1;
   if (lane == 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) return;
   __threadfence();
-  double xr[NRHS];
+  double xr[BCH / 32][NRHS];      // x at the chunk's rows: row T.r0 + lane + 32 q
 #pragma unroll
-  for (int k = 0; k < NRHS; ++k) xr[k] = act ? __ldcg(A.y + (int64_t)k * n + myrow) : 0.0;
+  for (int q = 0; q < BCH / 32; ++q) {
+    const int i = T.r0 + lane + 32 * q;
+    const bool act = i < T.r1;
+    const int row = act ? __ldg(R + i) : 0;
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) xr[q][k] = act ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
+  }
   double* dst = T.grp >= 0 ? A.Z : A.y;   // a merged piece accumulates in Z
-  for (int cb = 0; cb < w; cb += 16) {
+  for (int cb = 0; cb < w; cb += 8) {
     double v[NRHS];
-    warp_colsum16<NRHS>(Uo + i + (int64_t)cb * r, r, min(16, w - cb), act, xr, v, lane);
-    if (lane < 16 && cb + lane < w)
+    warp_colsum8<NRHS, BCH / 32>(Uo, r, cb, min(8, w - cb), T.r0, T.r1, xr, v, lane);
+    if (lane < 8 && cb + lane < w)
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) atomicAdd(dst + (int64_t)k * n + c0 + cb + lane, -v[k]);
   }

@@ -1035,17 +1035,21 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       first = (int)smalls.size();
     };
     const int WC = opt.warp_chunk;
-    // Forward entries by height (leaves first), backward entries by depth (roots first):
-    // entries of one level are independent, so the CTAs holding consecutive entries can
-    // all make progress and the critical path is the tree height, not the list length.
-    std::vector<int32_t> depth(nsn, 0);
-    for (int s = nsn - 1; s >= 0; --s)
-      depth[s] = S.sn_parent[s] >= 0 ? depth[S.sn_parent[s]] + 1 : 0;
+    const int BWC = opt.bwd_chunk;
+    // Forward entries by level (height: leaves first), backward entries by decreasing level
+    // (roots first): entries of one level are independent, so the CTAs holding consecutive
+    // entries can all make progress and the critical path is the tree height, not the list
+    // length.
     std::vector<int32_t> ford(nsn), bord(nsn);
     std::iota(ford.begin(), ford.end(), 0);
     std::iota(bord.begin(), bord.end(), 0);
     std::stable_sort(ford.begin(), ford.end(), [&](int a, int b) { return S.level[a] < S.level[b]; });
-    std::stable_sort(bord.begin(), bord.end(), [&](int a, int b) { return depth[a] < depth[b]; });
+    // backward: by decreasing level (height), the forward levels reversed -- a parent's level
+    // exceeds its children's, and the narrow leaves gather on the last levels, where lane
+    // tasks take them 32 per warp (ordered by depth they spread over many thin levels)
+    std::vector<int32_t> bkey(nsn);
+    for (int s = 0; s < nsn; ++s) bkey[s] = S.nlevels - 1 - S.level[s];
+    std::stable_sort(bord.begin(), bord.end(), [&](int a, int b) { return bkey[a] < bkey[b]; });
     // forward: per level, narrow supernodes (one per lane) and small ones (one per warp) in
     // GROUP entries, DIAG entries, then far chunks (BULK)
     for (size_t k0 = 0; k0 < ford.size();) {
@@ -1122,17 +1126,17 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
       flush(S.fwd, S.fwd_small, first, TASK_BULK);
       k0 = k1;
     }
-    // backward: per depth, far chunks (BULK; they wait for ancestors only), then small
+    // backward: per level (decreasing), far chunks (BULK; they wait for ancestors only), then small
     // supernodes (GROUP) and DIAG entries
     for (size_t k0 = 0; k0 < bord.size();) {
       size_t k1 = k0;
-      while (k1 < bord.size() && depth[bord[k1]] == depth[bord[k0]]) ++k1;
+      while (k1 < bord.size() && bkey[bord[k1]] == bkey[bord[k0]]) ++k1;
       int first = (int)S.bwd_small.size();
       auto far_chunks = [&](int s, int r_begin) {
         int r = (int)(S.rptr[s + 1] - S.rptr[s]);
-        for (int r0 = r_begin; r0 < r; r0 += WC) {
+        for (int r0 = r_begin; r0 < r; r0 += BWC) {
           int ws = S.sn_of[S.rows[S.rptr[s] + r0]];
-          S.bwd_small.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + WC), 0, 0, ws, 0});
+          S.bwd_small.push_back(SolveTask{TASK_OFF, s, r0, std::min(r, r0 + BWC), 0, 0, ws, 0});
           S.bwd_nchunk[s]++;
           if ((int)S.bwd_small.size() - first == 8) flush(S.bwd, S.bwd_small, first, TASK_BULK);
         }
@@ -1141,7 +1145,7 @@ std::string analyze(int n, const int32_t* ptr, const int32_t* idx, const Symboli
         int s = bord[k];
         if (large(s)) far_chunks(s, CH);
       }
-      // merged blocks whose last (top) piece is at this depth: their far chunks wait for
+      // merged blocks whose last (top) piece is on this level: their far chunks wait for
       // ancestors only, their MGEMV entries (below) for those chunks
       std::vector<int> done_grp;
       for (size_t k = k0; k < k1; ++k) {

@@ -20,7 +20,9 @@ struct SymbolicOptions {
   int relax_zeros = 20;      // relaxed amalgamation: max % explicit zeros (0 = fundamental only)
   int relax_width = 16;      // merged supernodes up to this width are accepted regardless
   int solve_chunk = 64;      // rows of the near chunk done by a large supernode's DIAG task
-  int warp_chunk = 32;       // rows of a far chunk (one warp; 8 chunks per BULK entry)
+  int warp_chunk = 32;       // rows of a forward far chunk (one warp; 8 chunks per BULK entry)
+  int bwd_chunk = 128;       // rows of a backward far chunk (one warp: FMAs over 4 row slabs
+                             // before one cross-lane exchange; matches the kernel's BCH)
   int fused_limit = 2048;    // w*(w+r) at or below which one warp does a supernode's solve
   int lane_rows = 32;        // supernodes of at most lane_width columns and lane_rows rows
   int lane_width = 4;        // are solved one per lane (32 per warp task); 0 rows disables

@@ -79,13 +79,16 @@ def test_solve_matches_sparse_lu(ers, name, circ):
     sim.set_state(0.0, x0)
     lin = O.linearize(circ, x0)
     rng = np.random.default_rng(0)
+    G = lin.Gk.tocsr()
+    g_inf = float(abs(G).sum(axis=1).max())
     for _ in range(3):
         b = rng.normal(size=circ.n)
         x = sim.solve(b)
         ref = lin.solve(b)
-        # backward-stable LU: compare residuals and solutions relative to cond-scaled bar
-        res = np.max(np.abs(lin.Gk @ x - b)) / np.max(np.abs(b))
-        assert res < 1e-11, res
+        # backward-stable LU: the normwise backward error (SuperLU and the oracle reach
+        # 3e-17 .. 7e-17 on these families), and solutions within a cond-scaled bar
+        eta = np.max(np.abs(G @ x - b)) / (g_inf * np.max(np.abs(x)) + np.max(np.abs(b)))
+        assert eta <= 1e-14, eta
         assert np.max(np.abs(x - ref)) <= 1e-8 * np.max(np.abs(ref))
     sim.close()
 
