@@ -32,11 +32,13 @@ METRIC = "ER-Euler steps/s & Krylov vectors/s at rel err 1e-6; plain vs batched+
 UNIT = "steps/s"
 FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32)
 # DRAM bytes / algorithmic bytes of one solve pair, from an ncu capture of the same kernels on
-# the 70^3 mesh (2.663 GB measured vs 2.553 GB algorithmic); the full-size traffic is this ratio
-# times the full-size algorithmic bytes (traffic grows with the factor).  Set to None whenever
-# k_trsv_fwd / k_trsv_bwd change until a new capture is taken.
-SOLVE_TRAFFIC_RATIO = None
-SOLVE_TRAFFIC_SOURCE = "ncu dram bytes of the 70^3 pair scaled by algorithmic bytes"
+# the 70^3 mesh; the full-size traffic is this ratio times the full-size algorithmic bytes
+# (traffic grows with the factor).  Set to None whenever k_trsv_fwd / k_trsv_bwd change until
+# a new capture is taken.
+SOLVE_TRAFFIC_RATIO = 2.692 / 2.562
+SOLVE_TRAFFIC_SOURCE = ("ncu dram bytes of the 70^3 pair (k_trsv_fwd<2,2> + k_trsv_bwd<2,2>: "
+                        "2.692 GB vs 2.562 GB algorithmic) scaled to the 100^3 pair by its "
+                        "algorithmic bytes")
 CLOCKS_DIR = os.environ.get("ERS_CLOCKS_DIR") or os.path.join(ROOT, ".bench")   # nvidia-smi samples
 L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
 FLUSH_BYTES = 256 * 2 ** 20
