@@ -10,6 +10,7 @@ phi_2 Krylov spaces, the update, the controller).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch      (batched Monte Carlo inverter chains, plain vs learned)
   python bench.py --workload solve --size 70   (the supernodal solves alone, for profiling)
+  python bench.py --workload mesh2d --steps 1000  (the 32x32 mesh at fixed h and m alone)
 
 Prints one JSON line (rank 0).  The value is accepted ER steps per second of the whole job;
 N > 1 runs independent replicas (a single circuit does not shard: every G^-1 couples all
@@ -58,7 +59,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="main line only (no accuracy run, config [0] / [2] / batch sub-lines)")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--workload", default="mesh", choices=["mesh", "chain", "batch", "solve"])
+    p.add_argument("--workload", default="mesh",
+                   choices=["mesh", "chain", "batch", "solve", "mesh2d"])
     p.add_argument("--ordering", type=int, default=0, help="ers_opts.ordering (0 or 1)")
     p.add_argument("--nrhs", type=int, default=2, help="solve: right-hand sides per pass")
     p.add_argument("--stages", type=int, default=2000, help="chain: inverter stages")
@@ -759,6 +761,12 @@ def main():
         run_batch_workload(a)
     elif a.workload == "solve":
         run_solve_workload(a)
+    elif a.workload == "mesh2d":
+        import torch
+        from paper_1511_04515_gb300 import build
+        build.build()
+        from paper_1511_04515_gb300 import ers
+        print(json.dumps(mesh2d_line(ers, torch.cuda.Stream(), steps=max(1, a.steps))), flush=True)
     else:
         run_ours(a)
 
