@@ -12,6 +12,8 @@
 //  * k_combine      : out = a*in + sum_b c_b beta_b V_b (y_b - e_1) + sum_q d_q u_q, the
 //                     ER update of Eq. 13, the error vector of Eq. 15 and ER-C (Eq. 20),
 //                     optionally with max |out|.
+#include <mutex>
+
 #include "ers_internal.h"
 #include "kcommon.cuh"
 #include "kdense.cuh"
@@ -29,9 +31,8 @@ struct CoopArgs {
   KrylovState* ks;
   const int32_t *Gp, *Gi;
   const double* Gv;
-  double* part;         // partial sums: NV * gridDim
-  double* out;          // reduced values
-  unsigned* bar;
+  double* part;         // grid-reduction partials: 2 * GRID_RED_NV * gridDim
+  unsigned* bar;        // arrival / exit counters of the grid reductions
   unsigned* status;
 };
 
@@ -46,38 +47,42 @@ __device__ __forceinline__ double gnorm_part(const CoopArgs& A, const double* u,
   return acc;
 }
 
+// NB: number of spaces in the group (compile-time, so that per-space values stay in registers)
+template <int NB>
 __global__ void __launch_bounds__(KB) k_arnoldi_init(CoopArgs A) {
-  __shared__ double sh[KB / 32];
+  __shared__ double sh[GRID_RED_NV * (KB / 32)];
+  GridRed gr{A.part, A.bar, A.status, 0u};
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int nb = A.g.nb;
-  double loc[MAX_RHS];
-  for (int b = 0; b < MAX_RHS; ++b) loc[b] = 0.0;
-  for (int b = 0; b < nb; ++b) {
+  double beta[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
     double acc = 0.0;
     for (int64_t i = tid; i < A.n; i += T) { double v = A.g.src[b][i]; acc += v * v; }
-    loc[b] = block_sum(acc, sh);
+    beta[b] = acc;
   }
-  grid_reduce<MAX_RHS>(loc, A.part, A.out, A.bar, A.status, sh);
-  double beta[MAX_RHS];
-  for (int b = 0; b < nb; ++b) beta[b] = sqrt(__ldcg(A.out + b));
-  for (int b = 0; b < nb; ++b) {
+  grid_sum_n<NB>(beta, gr, sh);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    beta[b] = sqrt(beta[b]);
     double inv = beta[b] > 0.0 ? 1.0 / beta[b] : 0.0;
     for (int64_t i = tid; i < A.n; i += T) A.g.V[b][i] = A.g.src[b][i] * inv;
   }
-  double gl[MAX_RHS];
-  for (int b = 0; b < MAX_RHS; ++b) gl[b] = 0.0;
+  double gl[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) gl[b] = 0.0;
   if (A.adaptive) {
-    const double zero1[1] = {0.0};
-    grid_reduce<1>(zero1, A.part, A.out + MAX_RHS, A.bar, A.status, sh);  // V_0 complete
-    for (int b = 0; b < nb; ++b) gl[b] = block_sum(gnorm_part(A, A.g.V[b], T), sh);
-    grid_reduce<MAX_RHS>(gl, A.part, A.out, A.bar, A.status, sh);
+    grid_sync(gr);                                   // V_0 complete
+#pragma unroll
+    for (int b = 0; b < NB; ++b) gl[b] = gnorm_part(A, A.g.V[b], T);
+    grid_sum_n<NB>(gl, gr, sh);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int b = 0; b < nb; ++b) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
       KrylovState& K = A.ks[A.g.slot[b]];
       K.beta = beta[b];
-      K.gv1 = A.adaptive ? sqrt(__ldcg(A.out + b)) : 0.0;
+      K.gv1 = A.adaptive ? sqrt(gl[b]) : 0.0;
       K.built = 0;
       K.m = 0;
       K.best_m = 0;
@@ -88,109 +93,144 @@ __global__ void __launch_bounds__(KB) k_arnoldi_init(CoopArgs A) {
       if (!isfinite(beta[b])) atomicOr(A.status, ST_NONFINITE);
     }
   }
+  grid_exit(gr);
 }
 
-template <int EPT>
-__global__ void __launch_bounds__(KB) k_mgs(CoopArgs A) {
-  __shared__ double sh[KB / 32];
+// One modified Gram-Schmidt step of Algorithm 1 for NB spaces: w = J^-1 v_j (the solve's
+// output, negated) is orthogonalised against v_0 .. v_j one vector at a time.  Each thread
+// owns EPT elements, at i = tid + q T: w stays in registers, and so does the basis vector of
+// the current projection, which is also the one of the next inner product.  With PF the
+// vector after it is loaded before the inner product's grid reduction, so the load is in
+// flight while the blocks wait for each other (used where the three register arrays fit).
+template <int NB, int EPT, bool PF>
+__global__ void __launch_bounds__(KB, 2) k_mgs(CoopArgs A) {
+  __shared__ double sh[GRID_RED_NV * (KB / 32)];
+  GridRed gr{A.part, A.bar, A.status, 0u};
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int nb = A.g.nb, j = A.j, n = A.n;
-  const int ldh = MAX_M + 1;
-  int active[MAX_RHS];
-  for (int b = 0; b < nb; ++b) active[b] = !A.ks[A.g.slot[b]].done;
-  double w[MAX_RHS][EPT];
-  for (int b = 0; b < nb; ++b)
+  const int j = A.j, n = A.n;
+  constexpr int ldh = MAX_M + 1;
+  bool active[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) active[b] = !A.ks[A.g.slot[b]].done;
+  // PF: cur = v_i and nxt = v_{i+1} in registers; otherwise both are read at their use
+  double w[NB][EPT], cur[NB][EPT], nxt[NB][EPT];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      int64_t i = tid + q * T;
+      const int64_t i = tid + q * T;
       w[b][q] = (active[b] && i < n) ? -A.g.src[b][i] : 0.0;
+      cur[b][q] = (PF && i < n) ? A.g.V[b][i] : 0.0;
+      nxt[b][q] = 0.0;
     }
+  if (PF && j >= 1)
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int64_t i = tid + q * T;
+        nxt[b][q] = i < n ? A.g.V[b][(int64_t)n + i] : 0.0;
+      }
   // pass 0: ||w||^2 and <w, v_0>
-  double loc[2 * MAX_RHS];
-  for (int b = 0; b < 2 * MAX_RHS; ++b) loc[b] = 0.0;
-  for (int b = 0; b < nb; ++b) {
+  double r0[2 * NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
     double nn = 0.0, dd = 0.0;
-    const double* v0 = A.g.V[b];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      int64_t i = tid + q * T;
-      if (i < n) { nn += w[b][q] * w[b][q]; dd += w[b][q] * v0[i]; }
+      const int64_t i = tid + q * T;
+      const double v0 = PF ? cur[b][q] : (i < n ? A.g.V[b][i] : 0.0);
+      nn += w[b][q] * w[b][q];
+      dd += w[b][q] * v0;
     }
-    loc[2 * b] = block_sum(nn, sh);
-    loc[2 * b + 1] = block_sum(dd, sh);
+    r0[2 * b] = nn;
+    r0[2 * b + 1] = dd;
   }
-  grid_reduce<2 * MAX_RHS>(loc, A.part, A.out, A.bar, A.status, sh);
-  double w0[MAX_RHS], hcur[MAX_RHS];
-  for (int b = 0; b < nb; ++b) {
-    w0[b] = sqrt(__ldcg(A.out + 2 * b));
-    hcur[b] = __ldcg(A.out + 2 * b + 1);
-  }
+  grid_sum_n<2 * NB>(r0, gr, sh);
+  double w0[NB], hcur[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) { w0[b] = sqrt(r0[2 * b]); hcur[b] = r0[2 * b + 1]; }
   if (blockIdx.x == 0 && threadIdx.x == 0)
-    for (int b = 0; b < nb; ++b)
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
       if (active[b]) A.g.H[b][0 + j * ldh] = hcur[b];
   for (int i = 0; i <= j; ++i) {
-    double lp[MAX_RHS];
-    for (int b = 0; b < MAX_RHS; ++b) lp[b] = 0.0;
-    for (int b = 0; b < nb; ++b) {
-      const double* vi = A.g.V[b] + (int64_t)i * n;
-      const double* vn = A.g.V[b] + (int64_t)(i + 1) * n;
+    double lp[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
       double acc = 0.0;
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
-        int64_t e = tid + q * T;
-        if (e < n) {
-          w[b][q] -= hcur[b] * vi[e];
-          acc += (i < j) ? w[b][q] * vn[e] : w[b][q] * w[b][q];
+        const int64_t e = tid + q * T;
+        const double vi = PF ? cur[b][q] : (e < n ? A.g.V[b][(int64_t)i * n + e] : 0.0);
+        w[b][q] -= hcur[b] * vi;
+        if (i < j) {
+          const double v = PF ? nxt[b][q] : (e < n ? A.g.V[b][(int64_t)(i + 1) * n + e] : 0.0);
+          acc += w[b][q] * v;
+          if (PF) cur[b][q] = v;
+        } else {
+          acc += w[b][q] * w[b][q];
         }
       }
-      lp[b] = block_sum(acc, sh);
+      lp[b] = acc;
     }
-    grid_reduce<MAX_RHS>(lp, A.part, A.out, A.bar, A.status, sh);
-    for (int b = 0; b < nb; ++b) hcur[b] = __ldcg(A.out + b);
+    if (PF && i + 1 < j)                 // v_{i+2}, in flight during the reduction
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int64_t e = tid + q * T;
+          nxt[b][q] = e < n ? A.g.V[b][(int64_t)(i + 2) * n + e] : 0.0;
+        }
+    grid_sum_n<NB>(lp, gr, sh);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) hcur[b] = lp[b];
     if (i < j && blockIdx.x == 0 && threadIdx.x == 0)
-      for (int b = 0; b < nb; ++b)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
         if (active[b]) A.g.H[b][(i + 1) + j * ldh] = hcur[b];
   }
   // hcur = ||w||^2 after orthogonalisation
-  double hn[MAX_RHS];
-  int bd[MAX_RHS];
-  for (int b = 0; b < nb; ++b) {
+  double hn[NB];
+  bool bd[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
     hn[b] = sqrt(hcur[b]);
     bd[b] = !(hn[b] > 1e-12 * w0[b]);
-  }
-  for (int b = 0; b < nb; ++b) {
     if (!active[b] || bd[b]) continue;
-    double inv = 1.0 / hn[b];
+    const double inv = 1.0 / hn[b];
     double* vn = A.g.V[b] + (int64_t)(j + 1) * n;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      int64_t e = tid + q * T;
+      const int64_t e = tid + q * T;
       if (e < n) vn[e] = w[b][q] * inv;
     }
   }
-  double gl[MAX_RHS];
-  for (int b = 0; b < MAX_RHS; ++b) gl[b] = 0.0;
+  double gl[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) gl[b] = 0.0;
   if (A.adaptive) {
-    const double zero1[1] = {0.0};
-    grid_reduce<1>(zero1, A.part, A.out + MAX_RHS, A.bar, A.status, sh);  // v_{j+1} complete
-    for (int b = 0; b < nb; ++b)
-      if (active[b] && !bd[b])
-        gl[b] = block_sum(gnorm_part(A, A.g.V[b] + (int64_t)(j + 1) * n, T), sh);
-    grid_reduce<MAX_RHS>(gl, A.part, A.out, A.bar, A.status, sh);
+    grid_sync(gr);                                   // v_{j+1} complete
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (active[b] && !bd[b]) gl[b] = gnorm_part(A, A.g.V[b] + (int64_t)(j + 1) * n, T);
+    grid_sum_n<NB>(gl, gr, sh);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int b = 0; b < nb; ++b) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
       if (!active[b]) continue;
       KrylovState& K = A.ks[A.g.slot[b]];
       A.g.H[b][(j + 1) + j * ldh] = hn[b];
       K.w0 = w0[b];
       K.built = j + 1;
-      K.gvnext[j] = A.adaptive && !bd[b] ? sqrt(__ldcg(A.out + b)) : 0.0;
+      K.gvnext[j] = A.adaptive && !bd[b] ? sqrt(gl[b]) : 0.0;
       if (!isfinite(hn[b])) atomicOr(A.status, ST_NONFINITE);
       if (bd[b]) { K.breakdown = 1; K.done = 1; K.m = j + 1; }
     }
   }
+  grid_exit(gr);
 }
 
 struct SmallArgs {
@@ -297,9 +337,9 @@ cudaError_t krylov_init_constants() {
 }
 
 // Grid of the cooperative vector kernels: every inner product of MGS is a grid-wide reduction
-// (arrival counter, one CTA sums the partials), whose cost grows with the CTA count, so the grid
-// is sized for at least 8 elements per thread; the memory traffic of an iteration stays far
-// below what the resulting CTAs can stream.
+// whose latency grows with the CTA count, so the grid is sized for about 8 elements per thread
+// (one CTA up to 2,048 nodes); the memory traffic of an iteration stays far below what the
+// resulting CTAs can stream.
 static int coop_blocks_for(ers_ctx* c, int n) {
   int want = (n + 8 * KB - 1) / (8 * KB);
   return std::max(1, std::min(want, c->coop_blocks));
@@ -316,33 +356,83 @@ static CoopArgs make_coop(ers_ctx* c, const VecGroup& g, int j, int adaptive) {
   A.Gi = c->G_idx;
   A.Gv = c->G_val;
   A.part = c->red;
-  A.out = c->red + 2 * MAX_RHS * 4096;
   A.bar = c->d_status + 4;
   A.status = c->d_status;
   return A;
 }
 
+typedef void (*CoopKernel)(CoopArgs);
+
+// Krylov groups hold one or two spaces (the solution bases of a ramp step, or one basis)
+constexpr int MGS_MAX_NB = 2;
+
+static CoopKernel init_kernel(int nb) { return nb == 1 ? k_arnoldi_init<1> : k_arnoldi_init<2>; }
+
+constexpr int EPT_LEVELS = 5;     // 1, 2, 4, 8, 16 elements per thread
+
+// the prefetching variant exists where its three register arrays (NB x EPT doubles each) fit
+static bool pf_exists(int nb, int lvl) { return nb * (1 << lvl) <= 16; }
+
+template <int NB, int EPT, bool PF>
+static CoopKernel mgs_instance() {
+  if constexpr (PF && NB * EPT > 16) return nullptr;
+  else return k_mgs<NB, EPT, PF>;
+}
+
+template <int NB, bool PF>
+static CoopKernel mgs_kernel_nb(int lvl) {
+  switch (lvl) {
+    case 0: return mgs_instance<NB, 1, PF>();
+    case 1: return mgs_instance<NB, 2, PF>();
+    case 2: return mgs_instance<NB, 4, PF>();
+    case 3: return mgs_instance<NB, 8, PF>();
+    default: return mgs_instance<NB, 16, PF>();
+  }
+}
+
+static CoopKernel mgs_kernel(int nb, int lvl, bool pf) {
+  if (pf) return nb == 1 ? mgs_kernel_nb<1, true>(lvl) : mgs_kernel_nb<2, true>(lvl);
+  return nb == 1 ? mgs_kernel_nb<1, false>(lvl) : mgs_kernel_nb<2, false>(lvl);
+}
+
+// resident CTAs per SM of the prefetching MGS variants (0 where a variant does not exist)
+static int g_pf_occ[MGS_MAX_NB][EPT_LEVELS];
+static std::once_flag g_pf_once;
+
+static void pf_occupancy() {
+  for (int nb = 1; nb <= MGS_MAX_NB; ++nb)
+    for (int l = 0; l < EPT_LEVELS; ++l) {
+      int occ = 0;
+      if (pf_exists(nb, l))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mgs_kernel(nb, l, true), KB, 0);
+      g_pf_occ[nb - 1][l] = occ;
+    }
+}
+
 cudaError_t launch_arnoldi_init(ers_ctx* c, const VecGroup& g, int adaptive) {
+  if (g.nb < 1 || g.nb > MGS_MAX_NB) return cudaErrorInvalidValue;
   CoopArgs A = make_coop(c, g, 0, adaptive);
   int blocks = coop_blocks_for(c, c->n);
   void* args[] = {&A};
   c->stats.kernel_launches++;
-  return cudaLaunchCooperativeKernel((void*)k_arnoldi_init, blocks, KB, args, 0, c->stream);
+  return cudaLaunchCooperativeKernel((void*)init_kernel(g.nb), blocks, KB, args, 0, c->stream);
 }
 
 cudaError_t launch_mgs(ers_ctx* c, const VecGroup& g, int j, int adaptive) {
+  if (g.nb < 1 || g.nb > MGS_MAX_NB) return cudaErrorInvalidValue;
   CoopArgs A = make_coop(c, g, j, adaptive);
-  int blocks = coop_blocks_for(c, c->n);
-  int64_t T = (int64_t)blocks * KB;
-  int ept = (int)((c->n + T - 1) / T);
+  const int blocks = coop_blocks_for(c, c->n);
+  const int64_t T = (int64_t)blocks * KB;
+  const int64_t ept = (c->n + T - 1) / T;
+  int lvl = 0;
+  while (lvl < EPT_LEVELS && ((int64_t)1 << lvl) < ept) ++lvl;
+  if (lvl >= EPT_LEVELS) return cudaErrorInvalidValue;
+  std::call_once(g_pf_once, pf_occupancy);
+  const bool pf = pf_exists(g.nb, lvl) && (int64_t)g_pf_occ[g.nb - 1][lvl] * c->sm_count >= blocks;
   void* args[] = {&A};
   c->stats.kernel_launches++;
-  if (ept <= 1) return cudaLaunchCooperativeKernel((void*)k_mgs<1>, blocks, KB, args, 0, c->stream);
-  if (ept <= 2) return cudaLaunchCooperativeKernel((void*)k_mgs<2>, blocks, KB, args, 0, c->stream);
-  if (ept <= 4) return cudaLaunchCooperativeKernel((void*)k_mgs<4>, blocks, KB, args, 0, c->stream);
-  if (ept <= 8) return cudaLaunchCooperativeKernel((void*)k_mgs<8>, blocks, KB, args, 0, c->stream);
-  if (ept <= 16) return cudaLaunchCooperativeKernel((void*)k_mgs<16>, blocks, KB, args, 0, c->stream);
-  return cudaErrorInvalidValue;
+  return cudaLaunchCooperativeKernel((void*)mgs_kernel(g.nb, lvl, pf), blocks, KB, args, 0,
+                                     c->stream);
 }
 
 cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int m_max) {
@@ -405,13 +495,18 @@ cudaError_t launch_absmax(ers_ctx* c, const double* x, unsigned long long* out) 
   return cudaGetLastError();
 }
 
+// Co-resident CTAs of the cooperative kernels: the smallest count over the Arnoldi start and
+// the non-prefetching MGS variants at 16 elements per thread (the launch falls back to those),
+// at most 4 per SM.
 int coop_max_blocks(int sm_count) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs<16>, KB, 0);
-  int per_sm2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_arnoldi_init, KB, 0);
-  per_sm = std::min(per_sm, per_sm2);
-  return std::max(1, std::min(per_sm, 4) * sm_count);
+  int per_sm = 4;
+  for (int nb = 1; nb <= MGS_MAX_NB; ++nb) {
+    int o1 = 0, o2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, mgs_kernel(nb, EPT_LEVELS - 1, false), KB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, init_kernel(nb), KB, 0);
+    per_sm = std::min(per_sm, std::min(o1, o2));
+  }
+  return std::max(1, per_sm * sm_count);
 }
 
 }  // namespace ers

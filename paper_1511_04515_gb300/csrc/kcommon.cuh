@@ -92,52 +92,111 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
-// Grid barrier for a cooperative (co-resident) launch with a deterministic reduction of
-// NV per-block partial values: every block writes part[v * gridDim.x + blockIdx.x]; the
-// last block to arrive sums them in block order into out[v] and releases the others.
-// bar[0] = arrival count, bar[1] = generation.  Bounded: gives up with ST_TIMEOUT.
+// Sums NV per-thread values over the block; every thread receives the NV totals.  Each warp
+// reduces with the xor butterfly (all lanes end with the same bits), then every thread adds
+// the warp totals in warp order: the result is fixed by the data, not by timing.
+// sh: NV * blockDim.x / 32 doubles.
 template <int NV>
-__device__ void grid_reduce(const double (&local)[NV], double* part, double* out,
-                            unsigned* bar, unsigned* status, double* sh) {
-  __shared__ int s_last;
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * nw + wid] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = 0.0;
+    for (int q = 0; q < nw; ++q) a += sh[k * nw + q];
+    v[k] = a;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void red_release_add_u(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin until *p >= target (one thread); bounded like wait_geq, with short first polls since
+// the grid reductions that use it wait for microseconds.
+__device__ __forceinline__ void wait_geq_u(const unsigned* p, unsigned target, unsigned* status) {
+  if (ld_acquire_u(p) >= target) return;
+  for (int it = 0; it < SPIN_LIMIT; ++it) {
+    if (it >= 16) __nanosleep(it < 256 ? 32 : 256);
+    if (ld_acquire_u(p) >= target) return;
+    if ((it & 255) == 255 && (ld_acquire_u(status) & ST_TIMEOUT)) return;
+  }
+  atomicOr(status, ST_TIMEOUT);
+}
+
+// Grid-wide reductions and barriers of a cooperative (co-resident) launch.  bar[0] counts the
+// blocks' arrivals over the whole launch (the r-th reduction completes when it reaches
+// (r + 1) * gridDim.x) and bar[1] their exits; both are zero at launch and reset by the last
+// block to leave (grid_exit).  A block publishes its partials and arrives with one release
+// add; after the acquire every block reads all partials and sums them in block order, so all
+// blocks hold the same total with no second hand-off.  The partial slots alternate between
+// two halves by round parity: a block can only write round r + 2's partials after every block
+// has arrived at round r + 1, i.e. finished reading round r's.  Bounded: ST_TIMEOUT.
+constexpr int GRID_RED_NV = 2 * MAX_RHS;   // most values reduced at once
+struct GridRed {
+  double* part;        // 2 * GRID_RED_NV * gridDim.x doubles
+  unsigned* bar;
+  unsigned* status;
+  unsigned round;
+};
+
+// v: per-thread values in, grid totals out (all threads of all blocks).
+// sh: NV * (blockDim.x / 32) doubles.
+template <int NV>
+__device__ __forceinline__ void grid_sum_n(double (&v)[NV], GridRed& g, double* sh) {
+  static_assert(NV <= GRID_RED_NV, "too many values");
+  block_sum_n<NV>(v, sh);
+  const unsigned G = gridDim.x;
+  if (G == 1) return;
+  double* slot = g.part + (size_t)(g.round & 1u) * (GRID_RED_NV * G);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) part[v * gridDim.x + blockIdx.x] = local[v];
+    for (int k = 0; k < NV; ++k) slot[k * G + blockIdx.x] = v[k];
+    red_release_add_u(g.bar, 1u);
+    wait_geq_u(g.bar, (g.round + 1u) * G, g.status);
+  }
+  g.round++;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < NV) {               // one warp per value: the block-order sum in lane-strided parts
+    double a = 0.0;
+    for (unsigned b = lane; b < G; b += 32) a += __ldcg(slot + wid * G + b);
+    a = warp_sum(a);
+    if (lane == 0) sh[wid] = a;
   }
   __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = sh[k];
+  __syncthreads();
+}
+
+// Every block's writes before the call are visible to every block after it.
+__device__ __forceinline__ void grid_sync(GridRed& g) {
+  __syncthreads();
+  const unsigned G = gridDim.x;
+  if (G == 1) return;
   if (threadIdx.x == 0) {
-    unsigned gen = ld_acquire_u(bar + 1);
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
-    s_last = arrived == gridDim.x - 1;
-    if (!s_last) {
-      int it = 0;
-      while (ld_acquire_u(bar + 1) == gen) {
-        __nanosleep(40);
-        if (++it > SPIN_LIMIT) { atomicOr(status, ST_TIMEOUT); break; }
-      }
-    }
+    red_release_add_u(g.bar, 1u);
+    wait_geq_u(g.bar, (g.round + 1u) * G, g.status);
   }
+  g.round++;
   __syncthreads();
-  if (s_last) {
-    __threadfence();
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        acc += __ldcg(part + v * gridDim.x + b);
-      acc = block_sum(acc, sh);
-      if (threadIdx.x == 0) out[v] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    }
+}
+
+// Last call of a kernel that used grid_sum_n / grid_sync: the last block out resets the
+// counters for the next launch (every other block is past its last wait by then).
+__device__ __forceinline__ void grid_exit(GridRed& g) {
+  if (gridDim.x == 1 || threadIdx.x != 0) return;
+  if (atomicAdd(g.bar + 1, 1u) == gridDim.x - 1) {
+    atomicExch(g.bar, 0u);
+    atomicExch(g.bar + 1, 0u);
   }
-  __syncthreads();
-  __threadfence();
 }
 
 }  // namespace ers
