@@ -56,8 +56,31 @@ constexpr int SM_V = MAX_RHS * 64;       // vectors
 constexpr int SM_PART = 4 * 64 * MAX_RHS;
 constexpr int SOLVE_SMEM = (SM_D + SM_P + 2 * SM_V + SM_PART) * 8;
 
+// A GROUP entry gives each warp an equal share of the CTA's shared memory: its vectors (SM_V
+// doubles) and a staging area for its supernode's factor values.
+constexpr int WARP_SM = SOLVE_SMEM / 8 / (SOLVE_THREADS / 32);
+constexpr int STAGE_CAP = WARP_SM - SM_V;
+
+// Asynchronous 8-byte global -> shared copies (they stay in flight through a dependency wait;
+// cp_async_wait_all makes them visible to the issuing lane, a __syncwarp to the warp).
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void warp_stage(double* dst, const double* src, int cnt, int lane) {
+  for (int e = lane; e < cnt; e += 32) cp_async8(dst + e, src + e);
+}
+
+// factor value at M + off: from shared memory (staged) or through the read-only path
+template <bool SMEM>
+__device__ __forceinline__ double fval(const double* M, int64_t off) {
+  if constexpr (SMEM) return M[off];
+  else return __ldg(M + off);
+}
+
 // z_q = sum_{j in tri(q)} M[q + j w] y_j for lanes q (lower: j <= q, upper: j >= q)
-template <int NRHS, bool LOWER>
+template <int NRHS, bool LOWER, bool SMEM = false>
 __device__ __forceinline__ void warp_tri_gemv(const double* M, int w, const double (*ys)[64],
                                               double (*z)[NRHS], int lane) {
 #pragma unroll
@@ -71,41 +94,85 @@ __device__ __forceinline__ void warp_tri_gemv(const double* M, int w, const doub
     for (; j + UNR <= j1; j += UNR) {
       double m[UNR];
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) m[u] = __ldg(M + q + (int64_t)(j + u) * w);
+      for (int u = 0; u < UNR; ++u) m[u] = fval<SMEM>(M, q + (int64_t)(j + u) * w);
 #pragma unroll
       for (int u = 0; u < UNR; ++u)
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) z[h][k] += m[u] * ys[k][j + u];
     }
     for (; j < j1; ++j) {
-      double m = __ldg(M + q + (int64_t)j * w);
+      double m = fval<SMEM>(M, q + (int64_t)j * w);
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) z[h][k] += m * ys[k][j];
     }
   }
 }
 
-// one small supernode, forward, by one warp
+// rows [0, r) of y_R -= L21 z, lanes over rows (L21 column-major r x w, from M)
+template <int NRHS, bool SMEM>
+__device__ __forceinline__ void fwd_panel(const SolveArgs& A, const double* M, const int32_t* R,
+                                          int w, int r, int row0, const double (*ys)[64],
+                                          int lane) {
+  const int n = A.n;
+  for (int i = lane; i < r; i += 32) {
+    double acc[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
+    int j = 0;
+    for (; j + UNR <= w; j += UNR) {
+      double l[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) l[u] = fval<SMEM>(M, i + (int64_t)(j + u) * r);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) acc[k] += l[u] * ys[k][j + u];
+    }
+    for (; j < w; ++j) {
+      const double l = fval<SMEM>(M, i + (int64_t)j * r);
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) acc[k] += l * ys[k][j];
+    }
+    const int row = i < 32 ? row0 : __ldg(R + i);
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
+  }
+}
+
+// one small supernode, forward, by one warp.  Its factor values (when they fit the warp's
+// staging area), first 32 row indices and first 32 targets are requested before the wait on
+// its children, so that only the y loads, the FMAs and the scatter follow the hand-off.
 template <int NRHS>
-__device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*ys)[64]) {
+__device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region) {
   const DevicePlan& P = A.P;
+  double (*ys)[64] = reinterpret_cast<double (*)[64]>(region);
+  double* stg = region + SM_V;
   int32_t* arrive = P.sync + 2;
   const int n = A.n;
   const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
   const double* Li = P.LDi + T.d_off;
   const double* Lo = P.Lo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
+  const bool staged = w * w + r * w <= STAGE_CAP;
+  if (staged) {
+    warp_stage(stg, Li, w * w, lane);
+    warp_stage(stg + w * w, Lo, r * w, lane);
+  }
+  const int row0 = lane < r ? __ldg(R + lane) : 0;
+  const int tgt0 = lane < T.ntgt ? __ldg(P.fwd_tgt + T.tgt0 + lane) : 0;
   int ok = 1;
   if (lane == 0) ok = wait_geq(arrive + s, T.wait_cnt, A.status);
   ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (!ok) return;
+  if (!ok) { cp_async_wait_all(); __syncwarp(); return; }
   __threadfence();
   for (int q = lane; q < w; q += 32)
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) ys[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+  cp_async_wait_all();
   __syncwarp();
   double z[2][NRHS];
-  warp_tri_gemv<NRHS, true>(Li, w, ys, z, lane);
+  if (staged) warp_tri_gemv<NRHS, true, true>(stg, w, ys, z, lane);
+  else warp_tri_gemv<NRHS, true, false>(Li, w, ys, z, lane);
   __syncwarp();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -118,34 +185,13 @@ __device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
       }
   }
   __syncwarp();
-  for (int i = lane; i < r; i += 32) {
-    double acc[NRHS];
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) acc[k] = 0.0;
-    const double* col = Lo + i;
-    int j = 0;
-    for (; j + UNR <= w; j += UNR) {
-      double l[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) l[u] = __ldg(col + (int64_t)(j + u) * r);
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) acc[k] += l[u] * ys[k][j + u];
-    }
-    for (; j < w; ++j) {
-      double l = __ldg(col + (int64_t)j * r);
-#pragma unroll
-      for (int k = 0; k < NRHS; ++k) acc[k] += l * ys[k][j];
-    }
-    int row = __ldg(R + i);
-#pragma unroll
-    for (int k = 0; k < NRHS; ++k) atomicAdd(A.y + (int64_t)k * n + row, -acc[k]);
-  }
+  if (staged) fwd_panel<NRHS, true>(A, stg + w * w, R, w, r, row0, ys, lane);
+  else fwd_panel<NRHS, false>(A, Lo, R, w, r, row0, ys, lane);
   __threadfence();
   __syncwarp();
-  if (lane == 0)
-    for (int q = 0; q < T.ntgt; ++q) red_release_add(arrive + P.fwd_tgt[T.tgt0 + q], 1);
+  // one lane per target: every lane's scatter is ordered before the barrier above
+  for (int q = lane; q < T.ntgt; q += 32)
+    red_release_add(arrive + (q < 32 ? tgt0 : __ldg(P.fwd_tgt + T.tgt0 + q)), 1);
   __syncwarp();
 }
 
@@ -172,7 +218,7 @@ __device__ __forceinline__ double warp_reduce8(double (&p)[8], int lane) {
 // Column sums over the slabs of 32 rows a warp owns, lanes over rows (coalesced panel loads):
 // out[k] on lane l = sum_i U[i, cb + (l & 7)] x_i[k] over rows i = i0 + lane + 32 q < i1,
 // q < MAXSLAB; FMAs per row, one warp_reduce8 per right-hand side.
-template <int NRHS, int MAXSLAB>
+template <int NRHS, int MAXSLAB, bool SMEM = false>
 __device__ __forceinline__ void warp_colsum8(const double* U, int64_t ld, int cb, int ncols,
                                              int i0, int i1, const double (&xr)[MAXSLAB][NRHS],
                                              double (&out)[NRHS], int lane) {
@@ -189,7 +235,7 @@ __device__ __forceinline__ void warp_colsum8(const double* U, int64_t ld, int cb
     const double* urow = U + i + (int64_t)cb * ld;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const double u = (act && c < ncols) ? __ldg(urow + (int64_t)c * ld) : 0.0;
+      const double u = (act && c < ncols) ? fval<SMEM>(urow, (int64_t)c * ld) : 0.0;
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) acc[k][c] = fma(u, xr[q][k], acc[k][c]);
     }
@@ -199,25 +245,42 @@ __device__ __forceinline__ void warp_colsum8(const double* U, int64_t ld, int cb
 }
 
 // one small supernode, backward, by one warp: xs = y_s - U12 x_R with lanes over the rows R
-// (8-column sums by warp_colsum8), then x_s = U11^-1 xs
+// (8-column sums by warp_colsum8), then x_s = U11^-1 xs.  Before the wait on the parent it
+// requests what the parent does not write: the factor values (staged when they fit), the
+// first 64 row indices and y_s (only this task writes y_s in the backward pass).
 template <int NRHS>
-__device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double (*xs)[64]) {
+__device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region) {
   const DevicePlan& P = A.P;
+  double (*xs)[64] = reinterpret_cast<double (*)[64]>(region);
+  double* stg = region + SM_V;
   int32_t* done = P.sync + 2 + P.nsn;
   const int n = A.n;
   const int s = T.sn, c0 = T.c0, w = T.w, r = T.r;
   const double* Ui = P.UDi + T.d_off;
   const double* Uo = P.Uo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
-  int ok = 1;
-  if (lane == 0 && T.wait_sn >= 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (!ok) return;
-  __threadfence();
+  const bool staged = w * w + r * w <= STAGE_CAP;
+  if (staged) {
+    warp_stage(stg, Ui, w * w, lane);
+    warp_stage(stg + w * w, Uo, r * w, lane);
+  }
+  int rowq[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int i = lane + 32 * q;
+    rowq[q] = i < r ? __ldg(R + i) : 0;
+  }
   for (int q = lane; q < w; q += 32)
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) xs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
+  int ok = 1;
+  if (lane == 0 && T.wait_sn >= 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) { cp_async_wait_all(); __syncwarp(); return; }
+  __threadfence();
+  cp_async_wait_all();
   __syncwarp();
+  const double* U = staged ? stg + w * w : Uo;
   // column sums, 64 rows at a time (x of the rows in registers), 8 columns per block
   for (int i0 = 0; i0 < r; i0 += 64) {
     double xr[2][NRHS];
@@ -225,13 +288,16 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
     for (int q = 0; q < 2; ++q) {
       const int i = i0 + lane + 32 * q;
       const bool act = i < r;
-      const int row = act ? __ldg(R + i) : 0;
+      const int row = i0 == 0 ? rowq[q] : (act ? __ldg(R + i) : 0);
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) xr[q][k] = act ? __ldcg(A.y + (int64_t)k * n + row) : 0.0;
     }
     for (int cb = 0; cb < w; cb += 8) {
       double v[NRHS];
-      warp_colsum8<NRHS, 2>(Uo, r, cb, min(8, w - cb), i0, min(r, i0 + 64), xr, v, lane);
+      if (staged)
+        warp_colsum8<NRHS, 2, true>(U, r, cb, min(8, w - cb), i0, min(r, i0 + 64), xr, v, lane);
+      else
+        warp_colsum8<NRHS, 2, false>(U, r, cb, min(8, w - cb), i0, min(r, i0 + 64), xr, v, lane);
       if (lane < 8 && cb + lane < w)
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) xs[k][cb + lane] -= v[k];
@@ -240,7 +306,8 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   }
   __syncwarp();
   double z[2][NRHS];
-  warp_tri_gemv<NRHS, false>(Ui, w, xs, z, lane);
+  if (staged) warp_tri_gemv<NRHS, false, true>(stg, w, xs, z, lane);
+  else warp_tri_gemv<NRHS, false, false>(Ui, w, xs, z, lane);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     int q = lane + 32 * h;
@@ -638,9 +705,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
     if (T.kind == TASK_GROUP) {
       if (wq < T.r0) {
         const SolveTask& U = P.fwd_small[T.sn + wq];
-        double (*buf)[64] = reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64);
         if (U.kind == TASK_LANES) fwd_lanes<NRHS>(A, U, lane);
-        else fwd_small<NRHS>(A, U, lane, buf);
+        else fwd_small<NRHS>(A, U, lane, sm + wq * WARP_SM);
       }
       continue;
     }
@@ -758,9 +824,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
     if (T.kind == TASK_GROUP) {
       if (wq < T.r0) {
         const SolveTask& U = P.bwd_small[T.sn + wq];
-        double (*buf)[64] = reinterpret_cast<double (*)[64]>(sm + wq * MAX_RHS * 64);
         if (U.kind == TASK_LANES) bwd_lanes<NRHS>(A, U, lane);
-        else bwd_small<NRHS>(A, U, lane, buf);
+        else bwd_small<NRHS>(A, U, lane, sm + wq * WARP_SM);
       }
       continue;
     }
