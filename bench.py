@@ -272,6 +272,8 @@ def chain_line(ers, stream, steps=10, warmup=3):
            "krylov_vectors_per_s": (st1["krylov_vectors"] - st0["krylov_vectors"]) / (ms * 1e-3),
            "refactors": st1["refactors"] - st0["refactors"],
            "gpu_launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / max(ns, 1),
+           "host_syncs_per_step": (st1["host_syncs"] - st0["host_syncs"]) / max(ns, 1),
+           "host_polls_per_step": (st1["host_polls"] - st0["host_polls"]) / max(ns, 1),
            "solve_ctas_per_sm": tuned, "l2_flush": note}
     sim.close()
     return out
@@ -308,6 +310,7 @@ def mesh2d_line(ers, stream, steps=1000):
            "steps": steps, "ms_per_step": ms / steps, "steps_per_s": steps / (ms * 1e-3),
            "krylov_vectors_per_s": (st1["krylov_vectors"] - st0["krylov_vectors"]) / (ms * 1e-3),
            "gpu_launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / steps,
+           "host_syncs_per_step": (st1["host_syncs"] - st0["host_syncs"]) / steps,
            "l2_flush": ("one 256 MB write before the run; the 1024-node factor stays in L2 "
                         "across the 1000 steps of the run, as in any use of this size")}
     sim.close()
@@ -445,6 +448,8 @@ def run_ours(a):
             "krylov_vectors_per_s": kvec_all / (ms_max * 1e-3),
             "rejects": int(nr),
             "gpu_launches": int(launches),
+            "host_syncs_per_step": (st1["host_syncs"] - st0["host_syncs"]) / max(steps, 1),
+            "host_polls_per_step": (st1["host_polls"] - st0["host_polls"]) / max(steps, 1),
             "roofline": roof,
             "clocks": clocks,
             "e2e": {"value": k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,

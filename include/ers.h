@@ -112,6 +112,11 @@ typedef struct {
   int64_t merged_columns;      /* columns in those blocks                               */
   int64_t merged_inverse_doubles; /* doubles of the two inverses (M_L and M_U)          */
   double merged_inverse_flops; /* flops of computing the inverses after each refactor   */
+  int64_t host_syncs;          /* stream synchronisations of the stepping calls (the host
+                                  waits for the device queue to drain)                   */
+  int64_t host_polls;          /* lagged reads of the Krylov spaces' done flags: the host
+                                  waits for an event two iterations back while the
+                                  device runs the iteration queued after it             */
 } ers_stats_t;
 
 /* One circuit of a batch (ers_create_batch): the same data ers_create takes. */

@@ -23,6 +23,7 @@ cudaError_t launch_minv(ers_ctx* c);
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done);
 cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag);
 cudaError_t solve_kernel_attributes();
 // k_krylov.cu
@@ -41,7 +42,11 @@ int coop_max_blocks(int sm_count);
 // ---------------------------------------------------------------------------------------
 // small kernels local to the host-side step orchestration
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np, double x) {
+// Piecewise-linear source value at x.  The host evaluates the same function to decide
+// whether a step sees a ramp, so the product and the sum are rounded separately on both
+// sides (no fused multiply-add): the two agree bit for bit.
+__host__ __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np,
+                                                    double x) {
   if (x <= t[0]) return v[0];
   if (x >= t[np - 1]) return v[np - 1];
   int lo = 0, hi = np - 1;
@@ -49,8 +54,13 @@ __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int
     int mid = (lo + hi) >> 1;
     if (t[mid] <= x) lo = mid; else hi = mid;
   }
-  double f = (x - t[lo]) / (t[hi] - t[lo]);
-  return v[lo] + f * (v[hi] - v[lo]);
+  const double f = (x - t[lo]) / (t[hi] - t[lo]);
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(v[lo], __dmul_rn(f, v[hi] - v[lo]));
+#else
+  volatile double prod = f * (v[hi] - v[lo]);
+  return v[lo] + prod;
+#endif
 }
 
 // u = u(t); slope = (u(t+h) - u(t)) / h
@@ -116,11 +126,13 @@ struct RhsArgs {
   int n, nv;
   const double* x[MAX_RHS];
   double* y;
+  const int* done[MAX_RHS];   // a space's done flag (nullptr: always computed)
 };
 __global__ void k_rhs_C(RhsArgs A, const int32_t* ptr, const int32_t* idx, const double* val) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   for (int v = 0; v < A.nv; ++v) {
+    if (A.done[v] && __ldcg(A.done[v])) continue;   // finished space: its output is not read
     double acc = 0.0;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) acc += val[e] * A.x[v][idx[e]];
     A.y[(int64_t)v * A.n + i] = acc;
@@ -206,6 +218,7 @@ std::string check_csr(const ers_csr* a, int rows, int cols, const char* name) {
 ers_status sync_status(ers_ctx* c) {
   CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  c->stats.host_syncs++;
   unsigned st = c->h_status[0];
   if (st & ST_TIMEOUT) return fail(c, ERS_ERR_TIMEOUT, "device wait timed out");
   if (st & ST_SINGULAR) return fail(c, ERS_ERR_SINGULAR, "zero or non-finite pivot in LU of G_k");
@@ -251,43 +264,76 @@ ers_status do_refactor(ers_ctx* c) {
 
 // Build invert-Krylov bases for the vectors of group g (Algorithm 1 up to the MEVP) and
 // leave y = exp(h H_m^-1) e_1 in the Krylov states.  mfixed > 0: fixed dimension.
+//
+// Adaptive dimension: the spaces' done flags (set by the Eq.-16 test) are read back with a
+// lag.  Every iteration ends with an asynchronous copy of the flags into a pinned ring slot
+// and an event; before iteration j the host waits only for iteration j - POLL_LAG's event,
+// so the next iteration is already queued on the device while the host reads.  A space that
+// finished in between is skipped by the kernels themselves (k_rhs_C, the solves, k_mgs and
+// k_small read its flag), so the results do not depend on the lag.
+constexpr int POLL_LAG = 2, POLL_RING = 4;
+
+ers_status ensure_poll_events(ers_ctx* c) {
+  for (int s = 0; s < POLL_RING; ++s)
+    if (!c->poll_ev[s]) CU(cudaEventCreateWithFlags(&c->poll_ev[s], cudaEventDisableTiming));
+  return ERS_OK;
+}
+
 ers_status build_bases(ers_ctx* c, VecGroup g, double h, int mfixed) {
   const int adaptive = mfixed == 0;
   const int mc = adaptive ? c->opts.m_max : mfixed;
   CU(launch_arnoldi_init(c, g, adaptive));
+  if (adaptive) {
+    ers_status st = ensure_poll_events(c);
+    if (st != ERS_OK) return st;
+  }
+  int32_t* ring = reinterpret_cast<int32_t*>(c->h_scalars + 32);   // POLL_RING x MAX_RHS
   VecGroup act = g;
   for (int j = 0; j < mc; ++j) {
-    if (adaptive && j > 0) {
-      // host reads which spaces are still running
-      for (int b = 0; b < g.nb; ++b)
-        CU(cudaMemcpyAsync(c->h_scalars + b, &c->ks[g.slot[b]].done, sizeof(int),
-                           cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaStreamSynchronize(c->stream));
+    if (adaptive && j >= POLL_LAG) {
+      const int slot = (j - POLL_LAG) % POLL_RING;
+      CU(cudaEventSynchronize(c->poll_ev[slot]));
+      c->stats.host_polls++;
+      const VecGroup was = act;
       act.nb = 0;
       for (int b = 0; b < g.nb; ++b) {
-        int done;
-        std::memcpy(&done, c->h_scalars + b, sizeof(int));
-        if (!done) {
-          act.slot[act.nb] = g.slot[b];
-          act.V[act.nb] = g.V[b];
-          act.H[act.nb] = g.H[b];
-          act.nb++;
+        if (ring[slot * MAX_RHS + b]) {
+          // finished by iteration j - POLL_LAG: the POLL_LAG - 1 iterations since then were
+          // counted for it but built nothing
+          for (int a = 0; a < was.nb; ++a)
+            if (was.slot[a] == g.slot[b]) c->stats.krylov_vectors -= POLL_LAG - 1;
+          continue;
         }
+        act.slot[act.nb] = g.slot[b];
+        act.V[act.nb] = g.V[b];
+        act.H[act.nb] = g.H[b];
+        act.nb++;
       }
       if (act.nb == 0) break;
     }
     RhsArgs R{};
     R.n = c->n;
     R.nv = act.nb;
-    for (int b = 0; b < act.nb; ++b) R.x[b] = act.V[b] + (size_t)j * c->n;
+    const int* done[MAX_RHS] = {};
+    for (int b = 0; b < act.nb; ++b) {
+      R.x[b] = act.V[b] + (size_t)j * c->n;
+      done[b] = R.done[b] = adaptive ? &c->ks[act.slot[b]].done : nullptr;
+    }
     R.y = c->solve_buf;
     k_rhs_C<<<nblk(c->n), 256, 0, c->stream>>>(R, c->C_ptr, c->C_idx, c->C_val);
     c->stats.kernel_launches++;
-    CU(launch_solve(c, c->solve_buf, act.nb));
+    CU(launch_solve_skip(c, c->solve_buf, act.nb, adaptive ? done : nullptr));
     for (int b = 0; b < act.nb; ++b) act.src[b] = c->solve_buf + (size_t)b * c->n;
     CU(launch_mgs(c, act, j, adaptive));
     c->stats.krylov_vectors += act.nb;
-    if (adaptive) CU(launch_small(c, SMALL_RESID, act, h, mc));
+    if (adaptive) {
+      CU(launch_small(c, SMALL_RESID, act, h, mc));
+      const int slot = j % POLL_RING;
+      for (int b = 0; b < g.nb; ++b)
+        CU(cudaMemcpyAsync(ring + slot * MAX_RHS + b, &c->ks[g.slot[b]].done, sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaEventRecord(c->poll_ev[slot], c->stream));
+    }
   }
   if (!adaptive) CU(launch_small(c, SMALL_FIXED_END, g, h, mc));
   return ERS_OK;
@@ -305,19 +351,33 @@ struct StepWork {
   VecGroup sol{};
 };
 
+// Whether some source's slope (u(t + h) - u(t)) / h is non-zero, i.e. whether the device's
+// k_pwl gives a non-zero slope (same pwl_eval, same t + h): no device round trip needed.
+// Steps whose [t, t + h] meets no range in which a source changes are decided at once.
+bool host_ramp(const ers_ctx* c, double t, double h) {
+  if (!(h > 0.0)) return false;
+  const double t1 = t + h;
+  auto it = std::lower_bound(c->pwl_active.begin(), c->pwl_active.end(), t,
+                             [](const std::pair<double, double>& a, double x) { return a.second < x; });
+  if (it == c->pwl_active.end() || it->first > t1) return false;
+  for (int q = 0; q < c->p; ++q) {
+    const int o = c->h_pwl_ptr[q], np = c->h_pwl_ptr[q + 1] - o;
+    const double* tt = c->h_pwl_t.data() + o;
+    const double* vv = c->h_pwl_v.data() + o;
+    if (pwl_eval(tt, vv, np, t1) != pwl_eval(tt, vv, np, t)) return true;
+  }
+  return false;
+}
+
 // Setup vectors of Eq. 12-13 at (t, x_k) for a step of h, and the solution bases.
 ers_status step_setup(ers_ctx* c, double t, double h, int mfixed, StepWork& W) {
   k_pwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, t, h, c->u,
                                              c->slope);
-  // host needs to know whether the slope vanishes (v2 and w1 skipped)
-  std::vector<double> hs(c->p);
-  CU(cudaMemcpyAsync(hs.data(), c->slope, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream));
   // v1 = x_k - G^-1 (F_k + B u(t_k))
   k_bu<<<nblk(c->n), 256, 0, c->stream>>>(c->n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F, c->rhs);
-  c->stats.kernel_launches++;
-  CU(cudaStreamSynchronize(c->stream));
-  bool ramp = false;
-  for (double s : hs) ramp = ramp || s != 0.0;
+  c->stats.kernel_launches += 2;
+  // v2 and w1 are skipped when every slope vanishes
+  const bool ramp = host_ramp(c, t, h);
   if (ramp) {
     // two right-hand sides in one pass: F + B u and B s
     CU(cudaMemcpyAsync(c->solve_buf, c->rhs, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
@@ -359,10 +419,31 @@ ers_status step_update(ers_ctx* c, const StepWork& W, double h) {
   return ERS_OK;
 }
 
-// e_rr = -(e^{hJ} - I) G^-1 dF (Eq. 15/19), its max-norm in *err_inf; leaves
-// v_e = G^-1 dF in c->ve for the ER-C correction.
-ers_status step_error(ers_ctx* c, double h, int mfixed, double* err_inf) {
-  *err_inf = 0.0;
+// Pinned host words that the stepping calls fill with asynchronous copies and read after
+// their one stream synchronisation per try (sync_status).
+double* host_err_bits(ers_ctx* c) { return c->h_scalars + 8; }    // ||e_rr||_inf
+double* host_xmax_bits(ers_ctx* c) { return c->h_scalars + 9; }   // max |x_k|
+int32_t* host_m_word(ers_ctx* c) { return reinterpret_cast<int32_t*>(c->h_scalars + 10); }
+
+double read_host_double(const double* p) {
+  double v;
+  std::memcpy(&v, p, sizeof(v));
+  return v;
+}
+
+// max |x| into the pinned word dst, asynchronously (read after the next sync_status)
+ers_status enqueue_absmax(ers_ctx* c, const double* x, double* dst) {
+  unsigned long long* mx = (unsigned long long*)(c->red + 2 * MAX_RHS * 4096 + 72);
+  CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
+  CU(launch_absmax(c, x, mx));
+  CU(cudaMemcpyAsync(dst, mx, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  return ERS_OK;
+}
+
+// e_rr = -(e^{hJ} - I) G^-1 dF (Eq. 15/19); its max-norm goes to host_err_bits(c) with the
+// next sync_status (0 for a linear circuit); leaves v_e = G^-1 dF in c->ve for ER-C.
+ers_status step_error(ers_ctx* c, double h, int mfixed) {
+  *host_err_bits(c) = 0.0;
   if (!c->ndev) return ERS_OK;
   launch_dev_eval(c, c->xnew, c->dev_I + c->ndev, 0);
   launch_node_F(c, 1, c->dev_I + c->ndev, c->xnew, c->solve_buf);
@@ -377,12 +458,8 @@ ers_status step_error(ers_ctx* c, double h, int mfixed, double* err_inf) {
   CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream));
   double cb[1] = {-1.0};
   CU(launch_combine(c, c->tmp, nullptr, 0.0, &ge, cb, nullptr, 0.0, nullptr, 0.0, mx));
-  unsigned long long bits;
-  CU(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  double e;
-  std::memcpy(&e, &bits, sizeof(e));
-  *err_inf = e;
+  CU(cudaMemcpyAsync(host_err_bits(c), mx, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->stream));
   return ERS_OK;
 }
 
@@ -409,10 +486,10 @@ double next_breakpoint(const ers_ctx* c, double t) {
   return it == c->bp.end() ? INFINITY : *it;
 }
 
-ers_status read_m(ers_ctx* c, int slot, int* m) {
-  CU(cudaMemcpyAsync(c->h_scalars, &c->ks[slot].m, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  std::memcpy(m, c->h_scalars, sizeof(int));
+// the dimension of Krylov space slot into host_m_word(c) with the next sync_status
+ers_status enqueue_m(ers_ctx* c, int slot) {
+  CU(cudaMemcpyAsync(host_m_word(c), &c->ks[slot].m, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                     c->stream));
   return ERS_OK;
 }
 
@@ -681,6 +758,24 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   }
   std::sort(c->bp.begin(), c->bp.end());
   c->bp.erase(std::unique(c->bp.begin(), c->bp.end()), c->bp.end());
+  c->h_pwl_ptr = pptr;
+  c->h_pwl_t = pt;
+  c->h_pwl_v = pv;
+  // the time ranges in which some source changes: [t_k, t_k+1] of every segment whose end
+  // values differ (a zero-width jump included), merged
+  {
+    std::vector<std::pair<double, double>> act;
+    for (int q = 0; q < p; ++q)
+      for (int k = pptr[q]; k + 1 < pptr[q + 1]; ++k)
+        if (pv[k] != pv[k + 1]) act.push_back({pt[k], pt[k + 1]});
+    std::sort(act.begin(), act.end());
+    for (auto& a : act) {
+      if (!c->pwl_active.empty() && a.first <= c->pwl_active.back().second)
+        c->pwl_active.back().second = std::max(c->pwl_active.back().second, a.second);
+      else
+        c->pwl_active.push_back(a);
+    }
+  }
   // devices
   std::vector<int32_t> dtype(ndev), dterm(3 * std::max(ndev, 0));
   std::vector<double> dpar(3 * std::max(ndev, 0));
@@ -929,18 +1024,18 @@ static ers_status step_core(ers_ctx* c, double h, int32_t m, int32_t* m_used, do
   if (st != ERS_OK) return st;
   st = step_update(c, W, h);
   if (st != ERS_OK) return st;
-  double err = 0.0;
-  st = step_error(c, h, m, &err);
+  st = step_error(c, h, m);
   if (st != ERS_OK) return st;
   st = step_correct(c, h, m);
   if (st != ERS_OK) return st;
-  st = sync_status(c);
-  if (st != ERS_OK) return st;
   if (m_used) {
-    st = read_m(c, 0, m_used);
+    st = enqueue_m(c, 0);
     if (st != ERS_OK) return st;
   }
-  if (err_inf) *err_inf = err;
+  st = sync_status(c);     // the step's one synchronisation: status, e_rr and m together
+  if (st != ERS_OK) return st;
+  if (m_used) *m_used = *host_m_word(c);
+  if (err_inf) *err_inf = read_host_double(host_err_bits(c));
   return ERS_OK;
 }
 
@@ -955,7 +1050,6 @@ ers_status ers_step(ers_ctx* c, double h, int32_t m, int32_t* m_used, double* er
   c->t += h;
   if (!c->linear) c->factored = false;
   c->stats.steps++;
-  CU(cudaStreamSynchronize(c->stream));
   return ERS_OK;
 }
 
@@ -976,11 +1070,11 @@ ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int3
   while (c->t < t_end * (1 - 1e-12) && (max_steps <= 0 || steps < max_steps)) {
     double nb = std::min(next_breakpoint(c, c->t), t_end);
     double h = std::min(std::min(h_prop, h_max), nb - c->t);
-    double E_rr = o.E_rr;
-    if (!(E_rr > 0)) {
-      double xm = host_absmax(c, c->x, &st);
+    // Alg. 2's error bound: E_rr, or tol * max(1, ||x_k||_inf) read with the try's sync
+    const bool relative = !(o.E_rr > 0);
+    if (relative) {
+      st = enqueue_absmax(c, c->x, host_xmax_bits(c));
       if (st != ERS_OK) return st;
-      E_rr = tol * std::max(1.0, xm);
     }
     if (!c->factored) {
       st = do_refactor(c);
@@ -999,20 +1093,21 @@ ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int3
       first = false;
       st = step_update(c, W, h);
       if (st != ERS_OK) return st;
-      double err = 0.0;
-      st = step_error(c, h, 0, &err);
+      st = step_error(c, h, 0);
       if (st != ERS_OK) return st;
-      st = sync_status(c);
+      st = sync_status(c);     // the try's one synchronisation: status, e_rr, ||x_k||
       if (st != ERS_OK) return st;
+      const double err = read_host_double(host_err_bits(c));
+      const double E_rr = relative ? tol * std::max(1.0, read_host_double(host_xmax_bits(c)))
+                                   : o.E_rr;
       if (err <= E_rr) break;
       ++i;
       ++rejects;
       h *= o.alpha;
       if (h < o.h_min) return fail(c, ERS_ERR_STEP_UNDERFLOW, "step size underflow");
     }
-    if (c->opts.correction && c->ndev) {
+    if (c->opts.correction && c->ndev) {   // its status is read with the next try's
       st = step_correct(c, h, 0);
-      if (st == ERS_OK) st = sync_status(c);
       if (st != ERS_OK) return st;
     }
     bool landed = h == nb - c->t;
@@ -1027,8 +1122,7 @@ ers_status ers_run(ers_ctx* c, double t_end, double tol, int32_t max_steps, int3
   c->stats.rejects += rejects;
   if (nsteps) *nsteps = steps;
   if (nreject) *nreject = rejects;
-  CU(cudaStreamSynchronize(c->stream));
-  return ERS_OK;
+  return sync_status(c);
 }
 
 ers_status ers_get_state(const ers_ctx* cc, double* t, double* x, double* h) {
@@ -1166,12 +1260,13 @@ ers_status ers_mevp(ers_ctx* c, const double* v, double h, int32_t m, double* ou
   // out = beta V y = v + beta V (y - e_1)
   double cb[1] = {1.0};
   CU(launch_combine(c, c->tmp, c->ve, 1.0, &g, cb, nullptr, 0.0, nullptr, 0.0, nullptr));
-  st = sync_status(c);
-  if (st != ERS_OK) return st;
   if (m_used) {
-    st = read_m(c, 2, m_used);
+    st = enqueue_m(c, 2);
     if (st != ERS_OK) return st;
   }
+  st = sync_status(c);
+  if (st != ERS_OK) return st;
+  if (m_used) *m_used = *host_m_word(c);
   return from_dev_perm(c, c->tmp, out);
 }
 
@@ -1461,6 +1556,8 @@ void ers_destroy(ers_ctx* c) {
   for (auto& ev : c->ev_used) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  for (cudaEvent_t e : c->poll_ev)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

@@ -19,6 +19,7 @@ namespace ers {
 void launch_dev_eval(ers_ctx* c, const double* x, double* dev_I, int with_jac);
 void launch_node_F(ers_ctx* c, int mode, const double* dev_In, const double* xn, double* out);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done);
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 
@@ -312,6 +313,8 @@ __global__ void k_bmused(int ninst, int nb, const KrylovState* ks, int32_t* out)
 }
 
 // how many (instance, space) pairs of the group are still iterating
+// out[0] = spaces still running, out[1] = 1 when none is (the solves of later iterations
+// that were already queued read it and do nothing)
 __global__ void k_bcount(BArgs A, int32_t* out) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -321,7 +324,10 @@ __global__ void k_bcount(BArgs A, int32_t* out) {
     if (A.mask[i] && !A.ks[A.slot[b] * A.ninst + i].done) atomicAdd(&cnt, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) *out = cnt;
+  if (threadIdx.x == 0) {
+    out[0] = cnt;
+    out[1] = cnt == 0;
+  }
 }
 
 // out[e] = a in[e] + sum_b c_b beta_{b,i} V_b (y_{b,i} - e_1)[e] + hfac * h_i * u0[e]
@@ -472,15 +478,17 @@ ScanBuf scan_buf(ers_ctx* c) {
 }
 
 // One Arnoldi iteration of the spaces of A: C v_j, the solves, Gram-Schmidt, the dimension
-// test.  With use_jdev the iteration index is read from (and advanced in) device memory, which
-// makes the sequence replayable as a graph.
+// test, and the count of spaces still running (c->bcount).  With use_jdev the iteration
+// index is read from (and advanced in) device memory, which makes the sequence replayable as
+// a graph.  The solve pass is skipped on the device once no space runs (c->bcount[1]).
 cudaError_t enqueue_iteration(ers_ctx* c, const BArgs& A, int nb, int j, bool use_jdev) {
   const int32_t* jd = use_jdev ? c->bj : nullptr;
   k_brhs_C<<<nblk(c->n), 256, 0, c->stream>>>(c->n, nb, c->C_ptr, c->C_idx, c->C_val, A.V[0],
                                                nb > 1 ? A.V[1] : nullptr,
                                                nb > 2 ? A.V[2] : nullptr, jd, j, c->solve_buf);
   c->stats.kernel_launches++;
-  cudaError_t e = launch_solve(c, c->solve_buf, nb);
+  const int* none_running[1] = {c->bcount + 1};
+  cudaError_t e = launch_solve_skip(c, c->solve_buf, nb, none_running);
   if (e != cudaSuccess) return e;
   BArgs M = A;
   M.j = j;
@@ -492,6 +500,8 @@ cudaError_t enqueue_iteration(ers_ctx* c, const BArgs& A, int nb, int j, bool us
   S.mode = SMALL_RESID;
   size_t mm = (size_t)c->opts.m_max;
   k_bsmall<<<c->ninst * nb, 256, small_smem_doubles(mm) * 8, c->stream>>>(S);
+  c->stats.kernel_launches++;
+  k_bcount<<<1, 256, 0, c->stream>>>(A, c->bcount);
   c->stats.kernel_launches++;
   if (use_jdev) {
     k_binc<<<1, 1, 0, c->stream>>>(c->bj);
@@ -554,7 +564,13 @@ ers_ctx::IterGraph* iteration_graph(ers_ctx* c, const BArgs& A, int nb, const in
 // Algorithm 1 up to the MEVP for the spaces `slots` of every instance set in `mask` (the host
 // copy of the device mask; adaptive m).  No space can finish before its first decision (at
 // m_min, or at the proposed dimension) unless it breaks down, and a broken-down space only
-// skips work, so the host polls for completion from the smallest first decision on.
+// skips work, so the host polls for completion from the smallest first decision on.  The
+// poll is lagged: every iteration ends with an asynchronous copy of the running count into a
+// pinned ring slot and an event, and before iteration j the host reads iteration
+// j - BPOLL_LAG's count, so the device always has the next iteration queued; the kernels of a
+// finished space, and the solve pass once none runs, do nothing.
+constexpr int BPOLL_LAG = 2, BPOLL_RING = 4;
+
 ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
                        const std::vector<int32_t>& mask) {
   const int mc = c->opts.m_max;
@@ -569,14 +585,18 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
   c->stats.kernel_launches++;
   ers_ctx::IterGraph* G = iteration_graph(c, A, nb, slots);
   if (G) BCU(cudaMemsetAsync(c->bj, 0, sizeof(int32_t), c->stream));
+  BCU(cudaMemsetAsync(c->bcount, 0, 2 * sizeof(int32_t), c->stream));
+  for (int s = 0; s < BPOLL_RING; ++s)
+    if (!c->poll_ev[s]) BCU(cudaEventCreateWithFlags(&c->poll_ev[s], cudaEventDisableTiming));
+  int32_t* ring = reinterpret_cast<int32_t*>(c->h_scalars + 32);   // BPOLL_RING counts
   for (int j = 0; j < mc; ++j) {
-    if (j > 0 && j >= first_test) {
-      k_bcount<<<1, 256, 0, c->stream>>>(A, c->bcount);
-      int32_t cnt = 0;
-      BCU(cudaMemcpyAsync(&cnt, c->bcount, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-      BCU(cudaStreamSynchronize(c->stream));
-      c->stats.kernel_launches++;
-      if (cnt == 0) break;
+    // the count after iteration j - BPOLL_LAG reflects the tests up to dimension
+    // j - BPOLL_LAG + 1; the first space can finish at dimension first_test
+    if (j >= BPOLL_LAG && j - BPOLL_LAG + 1 >= first_test) {
+      const int slot = (j - BPOLL_LAG) % BPOLL_RING;
+      BCU(cudaEventSynchronize(c->poll_ev[slot]));
+      c->stats.host_polls++;
+      if (ring[slot] == 0) break;
     }
     if (G) {
       BCU(cudaGraphLaunch(G->exec, c->stream));
@@ -587,6 +607,12 @@ ers_status batch_bases(ers_ctx* c, int nb, const int* slots, double* const* src,
       c->stats.solve_rhs += G->rhs;
     } else {
       BCU(enqueue_iteration(c, A, nb, j, false));
+    }
+    {
+      const int slot = j % BPOLL_RING;
+      BCU(cudaMemcpyAsync(ring + slot, c->bcount, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+      BCU(cudaEventRecord(c->poll_ev[slot], c->stream));
     }
     // instances whose proposed first decision is at dimension j + 1: test [m_min, j + 1]
     if (c->ctrl && j + 1 > c->opts.m_min) {
@@ -743,7 +769,7 @@ ers_status ers::create_batch_here(ers_ctx** out, const ers_instance* inst, int32
   BCU(cudaMalloc((void**)&c->bt, sizeof(double) * ninst));
   BCU(cudaMalloc((void**)&c->bred, sizeof(double) * ninst));
   BCU(cudaMalloc((void**)&c->bmask, sizeof(int32_t) * ninst));
-  BCU(cudaMalloc((void**)&c->bcount, sizeof(int32_t)));
+  BCU(cudaMalloc((void**)&c->bcount, 2 * sizeof(int32_t)));
   BCU(cudaMalloc((void**)&c->d_mstart, sizeof(int32_t) * ninst));
   BCU(cudaMalloc((void**)&c->d_kv, sizeof(unsigned long long)));
   BCU(cudaMalloc((void**)&c->bj, sizeof(int32_t)));

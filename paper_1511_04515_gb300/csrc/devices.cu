@@ -334,6 +334,8 @@ ers_status group_stats(ers_ctx* g, ers_stats_t* out) {
     acc.merged_columns += x.merged_columns;
     acc.merged_inverse_doubles += x.merged_inverse_doubles;
     acc.merged_inverse_flops += x.merged_inverse_flops;
+    acc.host_syncs += x.host_syncs;
+    acc.host_polls += x.host_polls;
     return ERS_OK;
   });
   if (st == ERS_OK) *out = acc;

@@ -155,6 +155,9 @@ struct ers_ctx {
   int solve_ctas_per_sm = 3;           // resident CTAs per SM of the persistent solves (tunable)
   // host copies (permuted) needed by the host-side step orchestration
   std::vector<double> bp;              // sorted unique PWL corner times
+  std::vector<int32_t> h_pwl_ptr;      // PWL tables (the device's copy is pwl_*)
+  std::vector<double> h_pwl_t, h_pwl_v;
+  std::vector<std::pair<double, double>> pwl_active;   // merged ranges where a source changes
   // device arrays (permuted node order)
   int32_t* d_perm = nullptr;                    // new -> old node index
   int32_t *G_ptr = nullptr, *G_idx = nullptr;   // union pattern of G_k
@@ -190,6 +193,7 @@ struct ers_ctx {
   unsigned* d_status = nullptr;      // [0] status bits, [1..] barrier words
   unsigned* h_status = nullptr;      // pinned mirror
   double* h_scalars = nullptr;       // pinned scalars for host decisions
+  cudaEvent_t poll_ev[4] = {};       // lagged done-flag reads of adaptive Arnoldi builds
   int coop_blocks = 0;
   // state
   double t = 0.0, h = 0.0;

@@ -110,9 +110,15 @@ __global__ void __launch_bounds__(KB, 2) k_mgs(CoopArgs A) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int j = A.j, n = A.n;
   constexpr int ldh = MAX_M + 1;
-  bool active[NB];
+  bool active[NB], any = false;
 #pragma unroll
-  for (int b = 0; b < NB; ++b) active[b] = !A.ks[A.g.slot[b]].done;
+  for (int b = 0; b < NB; ++b) {
+    active[b] = !A.ks[A.g.slot[b]].done;
+    any = any || active[b];
+  }
+  // every space finished (a launch the host queued before it knew): nothing to do.  The
+  // flags come from earlier launches, so every block returns here, before any reduction.
+  if (!any) return;
   // PF: cur = v_i and nxt = v_{i+1} in registers; otherwise both are read at their use
   double w[NB][EPT], cur[NB][EPT], nxt[NB][EPT];
 #pragma unroll

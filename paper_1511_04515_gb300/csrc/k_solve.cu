@@ -47,7 +47,24 @@ struct SolveArgs {
   unsigned* status;
   double* Z;        // merged blocks: z = M_L y (forward result), accumulates y - U12 x_R
   double* part;     // partial sums of MGEMV tasks: slot x 64 x MAX_RHS
+  const int* done[MAX_RHS];   // Arnoldi solves: the spaces' done flags (ndone of them)
+  int ndone;
 };
+
+// An Arnoldi solve whose spaces have all finished does nothing (the host learns of it with
+// a lag and may have launched it already).  Uniform over the grid: the flags were written by
+// earlier launches.
+__device__ __forceinline__ bool solve_skipped(const SolveArgs& A) {
+  if (A.ndone == 0) return false;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int b = 0; b < A.ndone; ++b) all &= __ldcg(A.done[b]) != 0;
+    s_skip = all;
+  }
+  __syncthreads();
+  return s_skip != 0;
+}
 
 // shared-memory layout of a CTA (doubles)
 constexpr int SM_D = 64 * 64;            // diagonal block
@@ -695,6 +712,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
   int32_t* arrive = sync + 2;
   int32_t* ready = sync + 2 + P.nsn;
   const int n = A.n;
+  if (solve_skipped(A)) return;
   while (true) {
     __syncthreads();
     if (tid == 0) s_cur = atomicAdd(sync, 1);
@@ -814,6 +832,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
   int32_t* done = sync + 2 + P.nsn;
   int32_t* arriveb = sync + 2 + 2 * P.nsn;
   const int n = A.n;
+  if (solve_skipped(A)) return;
   while (true) {
     __syncthreads();
     if (tid == 0) s_cur = atomicAdd(sync + 1, 1);
@@ -968,13 +987,18 @@ cudaError_t solve_kernel_attributes() {
   return cudaSuccess;
 }
 
-// Solve G_k X = Y in place for nrhs vectors (stride n).
-cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
+// Solve G_k X = Y in place for nrhs vectors (stride n).  done (nrhs flags, or nullptr): the
+// whole pass is skipped on the device when every flag is set.
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done) {
   DevicePlan& P = c->plan;
   if (nrhs < 1 || nrhs > MAX_RHS) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * solve_sync_words(P.nsn), c->stream);
   if (e != cudaSuccess) return e;
-  SolveArgs A{P, y, c->n, c->d_status, c->solve_z, c->solve_part};
+  SolveArgs A{P, y, c->n, c->d_status, c->solve_z, c->solve_part, {}, 0};
+  if (done) {
+    for (int b = 0; b < nrhs; ++b) A.done[b] = done[b];
+    A.ndone = nrhs;
+  }
   int blocks = c->sm_count * c->solve_ctas_per_sm;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profile) {
@@ -1000,6 +1024,8 @@ cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) {
   c->stats.kernel_launches += 2;
   return cudaGetLastError();
 }
+
+cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) { return launch_solve_skip(c, y, nrhs, nullptr); }
 
 }  // namespace ers
 

@@ -79,7 +79,8 @@ class Stats(C.Structure):
                 ("solve_bytes_per_pass", C.c_double), ("solve_fma_per_rhs", C.c_double),
                 ("graph_launches", C.c_int64), ("merged_blocks", C.c_int64),
                 ("merged_columns", C.c_int64), ("merged_inverse_doubles", C.c_int64),
-                ("merged_inverse_flops", C.c_double)]
+                ("merged_inverse_flops", C.c_double), ("host_syncs", C.c_int64),
+                ("host_polls", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
