@@ -47,6 +47,11 @@ SAMPLE_SIZE = 24                   # oracle sample: 24^3 mesh of the same genera
 SAMPLE_STEPS = 40
 
 
+def ordering_kw(a):
+    """--ordering for ers.make_opts: nothing when the library default is meant."""
+    return {} if a.ordering is None else {"ordering": a.ordering}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -61,7 +66,8 @@ def parse():
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--workload", default="mesh",
                    choices=["mesh", "chain", "batch", "solve", "mesh2d"])
-    p.add_argument("--ordering", type=int, default=0, help="ers_opts.ordering (0 or 1)")
+    p.add_argument("--ordering", type=int, default=None,
+                   help="ers_opts.ordering (0 or 1; default: the library's)")
     p.add_argument("--nrhs", type=int, default=2, help="solve: right-hand sides per pass")
     p.add_argument("--stages", type=int, default=2000, help="chain: inverter stages")
     p.add_argument("--batch-n", type=int, default=64, help="batch: instances")
@@ -335,7 +341,7 @@ def run_ours(a):
     kind = "chain" if a.workload == "chain" else "mesh"
     circ = workload(a.size, kind, a.stages)
     t_end = workload_t_end(kind)
-    opts = ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100, ordering=a.ordering)
+    opts = ers.make_opts(eps_krylov=1e-7, h_max=t_end / 100, **ordering_kw(a))
     tc = time.perf_counter()
     sim = ers.Simulator.from_circuit(circ, opts=opts)
     create_s = time.perf_counter() - tc
@@ -443,6 +449,7 @@ def run_ours(a):
                        "l2_flush": l2_note,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "create_s": create_s, "factor_and_dc_s": factor_s,
+                       "ordering": int(opts.ordering),
                        "solve_ctas_per_sm": tuned,
                        "autotune_ms_per_pass_at_1_2_3": tune_ms},
             "krylov_vectors_per_s": kvec_all / (ms_max * 1e-3),
@@ -461,7 +468,7 @@ def run_ours(a):
     sim.close()
     if world == 1 and not a.no_extras:
         ref = ers.Simulator.from_circuit(
-            circ, opts=ers.make_opts(eps_krylov=1e-10, h_max=t_end / 100, ordering=a.ordering))
+            circ, opts=ers.make_opts(eps_krylov=1e-10, h_max=t_end / 100, **ordering_kw(a)))
         ref.set_stream(stream)
         ref.set_state(t_start, x_start, h_start)
         ref.run(t_stop, a.tol / 10)
@@ -501,7 +508,7 @@ def run_solve_workload(a):
     from paper_1511_04515_gb300 import ers
     circ = workload(a.size, "mesh")
     tc = time.perf_counter()
-    sim = ers.Simulator.from_circuit(circ, opts=ers.make_opts(ordering=a.ordering))
+    sim = ers.Simulator.from_circuit(circ, opts=ers.make_opts(**ordering_kw(a)))
     create_s = time.perf_counter() - tc
     sim.set_state(0.0, np.zeros(circ.n))
     tf = time.perf_counter()
@@ -519,7 +526,7 @@ def run_solve_workload(a):
     best = min(ms)
     fma = st["solve_fma_per_rhs"] * a.nrhs
     line = {"workload": f"solve passes, rc3d_{a.size}^3 mesh ({circ.n} nodes), "
-                        f"ordering {a.ordering}, {a.nrhs} right-hand sides",
+                        f"ordering {ers.make_opts(**ordering_kw(a)).ordering}, {a.nrhs} right-hand sides",
             "ms_per_pass_at_1_2_3_ctas_per_sm": ms, "chosen_ctas_per_sm": chosen,
             "fp64_tflops": 2 * fma / (best * 1e-3) / 1e12,
             "hbm_GBps": (st["solve_bytes_per_pass"] + 16.0 * circ.n * a.nrhs) / (best * 1e-3) / 1e9,

@@ -85,7 +85,7 @@ typedef struct {
   int32_t m_max;       /* Algorithm 1's m_c (default 40, at most 64)                              */
   int32_t combined_vector; /* 1: one Krylov space on v1 + v2 instead of two (default 0)           */
   int32_t correction;  /* 1: ER-C (Eq. 20), 0: ER (default 0)                                      */
-  int32_t ordering;    /* fill-reducing ordering of G_k's pattern (default 0):
+  int32_t ordering;    /* fill-reducing ordering of G_k's pattern (default 1):
                           0: nested dissection, separator = the BFS level at the median;
                           1: the smallest BFS level leaving >= 35% of the part on each side,
                              from either end of the pseudo-diameter (less fill on meshes) */

@@ -23,7 +23,7 @@ cudaError_t launch_minv(ers_ctx* c);
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
-cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done);
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done, int ndone);
 cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag);
 cudaError_t solve_kernel_attributes();
 // k_krylov.cu
@@ -42,27 +42,6 @@ int coop_max_blocks(int sm_count);
 // ---------------------------------------------------------------------------------------
 // small kernels local to the host-side step orchestration
 // ---------------------------------------------------------------------------------------
-// Piecewise-linear source value at x.  The host evaluates the same function to decide
-// whether a step sees a ramp, so the product and the sum are rounded separately on both
-// sides (no fused multiply-add): the two agree bit for bit.
-__host__ __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np,
-                                                    double x) {
-  if (x <= t[0]) return v[0];
-  if (x >= t[np - 1]) return v[np - 1];
-  int lo = 0, hi = np - 1;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (t[mid] <= x) lo = mid; else hi = mid;
-  }
-  const double f = (x - t[lo]) / (t[hi] - t[lo]);
-#ifdef __CUDA_ARCH__
-  return __dadd_rn(v[lo], __dmul_rn(f, v[hi] - v[lo]));
-#else
-  volatile double prod = f * (v[hi] - v[lo]);
-  return v[lo] + prod;
-#endif
-}
-
 // u = u(t); slope = (u(t+h) - u(t)) / h
 __global__ void k_pwl(int p, const int32_t* ptr, const double* tt, const double* vv, double t,
                       double h, double* u, double* slope) {
@@ -322,7 +301,7 @@ ers_status build_bases(ers_ctx* c, VecGroup g, double h, int mfixed) {
     R.y = c->solve_buf;
     k_rhs_C<<<nblk(c->n), 256, 0, c->stream>>>(R, c->C_ptr, c->C_idx, c->C_val);
     c->stats.kernel_launches++;
-    CU(launch_solve_skip(c, c->solve_buf, act.nb, adaptive ? done : nullptr));
+    CU(launch_solve_skip(c, c->solve_buf, act.nb, adaptive ? done : nullptr, act.nb));
     for (int b = 0; b < act.nb; ++b) act.src[b] = c->solve_buf + (size_t)b * c->n;
     CU(launch_mgs(c, act, j, adaptive));
     c->stats.krylov_vectors += act.nb;
@@ -550,7 +529,7 @@ ers_status ers_default_opts(ers_opts* o) {
   o->m_max = 40;
   o->combined_vector = 0;
   o->correction = 0;
-  o->ordering = 0;
+  o->ordering = 1;
   return ERS_OK;
 }
 
@@ -1558,6 +1537,7 @@ void ers_destroy(ers_ctx* c) {
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   for (cudaEvent_t e : c->poll_ev)
     if (e) cudaEventDestroy(e);
+  if (c->h_bpin) cudaFreeHost(c->h_bpin);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

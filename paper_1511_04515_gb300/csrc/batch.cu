@@ -19,22 +19,11 @@ namespace ers {
 void launch_dev_eval(ers_ctx* c, const double* x, double* dev_I, int with_jac);
 void launch_node_F(ers_ctx* c, int mode, const double* dev_In, const double* xn, double* out);
 cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs);
-cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done);
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done, int ndone);
 void launch_spmv(ers_ctx* c, const int32_t* ptr, const int32_t* idx, const double* val,
                  const double* x, double* y, double alpha);
 
 constexpr int BT = 512;   // threads of the per-instance kernels
-
-__device__ __forceinline__ double pwl_at(const double* t, const double* v, int np, double x) {
-  if (x <= t[0]) return v[0];
-  if (x >= t[np - 1]) return v[np - 1];
-  int lo = 0, hi = np - 1;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (t[mid] <= x) lo = mid; else hi = mid;
-  }
-  return v[lo] + (x - t[lo]) / (t[hi] - t[lo]) * (v[hi] - v[lo]);
-}
 
 // per source: u = u(t_inst), slope = (u(t_inst + h_inst) - u) / h_inst (0 for idle instances)
 __global__ void k_bpwl(int p, const int32_t* ptr, const double* tt, const double* vv,
@@ -45,9 +34,9 @@ __global__ void k_bpwl(int p, const int32_t* ptr, const double* tt, const double
   int i = src_inst[q];
   int o = ptr[q], np = ptr[q + 1] - ptr[q];
   double t = t_arr[i], h = h_arr[i];
-  double u0 = pwl_at(tt + o, vv + o, np, t);
+  double u0 = pwl_eval(tt + o, vv + o, np, t);
   u[q] = u0;
-  slope[q] = (mask[i] && h > 0.0) ? (pwl_at(tt + o, vv + o, np, t + h) - u0) / h : 0.0;
+  slope[q] = (mask[i] && h > 0.0) ? (pwl_eval(tt + o, vv + o, np, t + h) - u0) / h : 0.0;
 }
 
 struct BArgs {
@@ -488,7 +477,7 @@ cudaError_t enqueue_iteration(ers_ctx* c, const BArgs& A, int nb, int j, bool us
                                                nb > 2 ? A.V[2] : nullptr, jd, j, c->solve_buf);
   c->stats.kernel_launches++;
   const int* none_running[1] = {c->bcount + 1};
-  cudaError_t e = launch_solve_skip(c, c->solve_buf, nb, none_running);
+  cudaError_t e = launch_solve_skip(c, c->solve_buf, nb, none_running, 1);
   if (e != cudaSuccess) return e;
   BArgs M = A;
   M.j = j;
@@ -770,6 +759,8 @@ ers_status ers::create_batch_here(ers_ctx** out, const ers_instance* inst, int32
   BCU(cudaMalloc((void**)&c->bred, sizeof(double) * ninst));
   BCU(cudaMalloc((void**)&c->bmask, sizeof(int32_t) * ninst));
   BCU(cudaMalloc((void**)&c->bcount, 2 * sizeof(int32_t)));
+  BCU(cudaMallocHost((void**)&c->h_bpin, sizeof(double) * 4 * (size_t)ninst));
+  c->h_src_inst = src_inst;
   BCU(cudaMalloc((void**)&c->d_mstart, sizeof(int32_t) * ninst));
   BCU(cudaMalloc((void**)&c->d_kv, sizeof(unsigned long long)));
   BCU(cudaMalloc((void**)&c->bj, sizeof(int32_t)));
@@ -828,7 +819,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   const int ninst = c->ninst, n = c->n;
   const ers_opts& o = c->opts;
   const double h_max = o.h_max > 0 ? o.h_max : t_end / 100.0;
-  std::vector<double> h(ninst), E(ninst), err(ninst), xmax(ninst), dF(ninst), dF_acc(ninst);
+  std::vector<double> h(ninst), E(ninst), err(ninst), dF(ninst), dF_acc(ninst);
   std::vector<double> err_acc(ninst);
   std::vector<int32_t> active(ninst), trying(ninst), retries(ninst), mused(ninst);
   std::vector<int> landed(ninst);
@@ -837,6 +828,11 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
   if (st != ERS_OK) return st;
   BCU(cudaMemsetAsync(c->d_where, 0, 4 * sizeof(unsigned), c->stream));
   const std::vector<int64_t> steps0 = c->steps_inst, rejects0 = c->rejects_inst;
+  // pinned per-instance words filled by asynchronous copies and read after a try's sync
+  double* pin_xmax = c->h_bpin;
+  double* pin_dF = c->h_bpin + ninst;
+  double* pin_err = c->h_bpin + 2 * (size_t)ninst;
+  int32_t* pin_mused = reinterpret_cast<int32_t*>(c->h_bpin + 3 * (size_t)ninst);
   int round = 0;
   std::vector<int32_t> ones(ninst, 1);
   while (max_steps <= 0 || round < max_steps) {
@@ -853,18 +849,18 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       if (!c->ctrl) c->mstart_inst[i] = o.m_min;
     }
     if (nact == 0) break;
-    // error budgets from ||x_i||_inf
+    // error budgets from ||x_i||_inf, read with the first try's synchronisation (pinned);
+    // the uploads below are stream-ordered and need no synchronisation
     BCU(cudaMemcpyAsync(c->bmask, ones.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
     k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->x, c->bred);
-    BCU(cudaMemcpyAsync(xmax.data(), c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
+    BCU(cudaMemcpyAsync(pin_xmax, c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
     BCU(cudaMemcpyAsync(c->bh, h.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
     BCU(cudaMemcpyAsync(c->bt, c->t_inst.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice, c->stream));
     BCU(cudaMemcpyAsync(c->bmask, active.data(), sizeof(int32_t) * ninst, cudaMemcpyHostToDevice, c->stream));
     if (c->ctrl)
       BCU(cudaMemcpyAsync(c->d_mstart, c->mstart_inst.data(), sizeof(int32_t) * ninst,
                           cudaMemcpyHostToDevice, c->stream));
-    BCU(cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < ninst; ++i) E[i] = o.E_rr > 0 ? o.E_rr : tol * std::max(1.0, xmax[i]);
+    bool have_E = false;
     if (!c->factored) {
       st = ctx_refactor(c);
       if (st != ERS_OK) return st;
@@ -872,14 +868,20 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     // setup vectors (Eq. 12-13): v1 = x - G^-1 (F + B u), w1 = G^-1 B s, v2 = G^-1 C w1
     k_bpwl<<<nblk(c->p), 256, 0, c->stream>>>(c->p, c->pwl_ptr, c->pwl_t, c->pwl_v, c->d_src_inst,
                                               c->bt, c->bh, c->bmask, c->u, c->slope);
-    std::vector<double> hs(c->p);
-    BCU(cudaMemcpyAsync(hs.data(), c->slope, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream));
     k_bbu<<<nblk(n), 256, 0, c->stream>>>(n, c->B_ptr, c->B_idx, c->B_val, c->u, c->F, c->solve_buf);
     k_bbu<<<nblk(n), 256, 0, c->stream>>>(n, c->B_ptr, c->B_idx, c->B_val, c->slope, nullptr,
                                           c->solve_buf + n);
-    BCU(cudaStreamSynchronize(c->stream));
+    // whether some active instance's source has a non-zero slope: decided on the host with
+    // the kernel's own arithmetic (pwl_eval at t_i and t_i + h_i), no read-back
     bool ramp = false;
-    for (double s : hs) ramp = ramp || s != 0.0;
+    for (int q = 0; q < c->p && !ramp; ++q) {
+      const int i = c->h_src_inst[q];
+      if (!active[i] || !(h[i] > 0.0)) continue;
+      const int o = c->h_pwl_ptr[q], np = c->h_pwl_ptr[q + 1] - o;
+      const double* tt = c->h_pwl_t.data() + o;
+      const double* vv = c->h_pwl_v.data() + o;
+      ramp = pwl_eval(tt, vv, np, c->t_inst[i] + h[i]) != pwl_eval(tt, vv, np, c->t_inst[i]);
+    }
     BCU(launch_solve(c, c->solve_buf, ramp ? 2 : 1));
     k_bsub<<<nblk(n), 256, 0, c->stream>>>(n, c->v1, c->x, c->solve_buf);
     if (ramp) {
@@ -895,7 +897,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
     st = batch_bases(c, nsol, slots, src, active);
     if (st != ERS_OK) return st;
     k_bmused<<<nblk(ninst), 256, 0, c->stream>>>(ninst, nsol, c->bks, c->d_mused);
-    BCU(cudaMemcpyAsync(mused.data(), c->d_mused, sizeof(int32_t) * ninst, cudaMemcpyDeviceToHost, c->stream));
+    BCU(cudaMemcpyAsync(pin_mused, c->d_mused, sizeof(int32_t) * ninst, cudaMemcpyDeviceToHost, c->stream));
     c->stats.kernel_launches++;
     trying = active;
     while (true) {
@@ -912,14 +914,14 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       U.inst_of = c->d_inst_of; U.mask = c->bmask;
       k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(U);
       c->stats.kernel_launches++;
-      std::fill(err.begin(), err.end(), 0.0);
-      std::fill(dF.begin(), dF.end(), 0.0);
+      std::fill(pin_err, pin_err + ninst, 0.0);
+      std::fill(pin_dF, pin_dF + ninst, 0.0);
       if (c->ndev) {
         // e_rr = -(e^{hJ} - I) G^-1 dF per instance (Eq. 15)
         launch_dev_eval(c, c->xnew, c->dev_I + c->ndev, 0);
         launch_node_F(c, 1, c->dev_I + c->ndev, c->xnew, c->solve_buf);
         k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->solve_buf, c->bdf);
-        BCU(cudaMemcpyAsync(dF.data(), c->bdf, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
+        BCU(cudaMemcpyAsync(pin_dF, c->bdf, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
         BCU(launch_solve(c, c->solve_buf, 1));
         BCU(cudaMemcpyAsync(c->ve, c->solve_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
         int es = 2;
@@ -932,11 +934,19 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
         Er.ks = c->bks; Er.u0 = nullptr; Er.h = c->bh; Er.inst_of = c->d_inst_of; Er.mask = c->bmask;
         k_bcombine<<<std::min(c->sm_count * 8, nblk(n)), 256, 0, c->stream>>>(Er);
         k_bmax<<<ninst, 256, 0, c->stream>>>(ninst, c->d_seg_off, c->bmask, c->tmp, c->bred);
-        BCU(cudaMemcpyAsync(err.data(), c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
+        BCU(cudaMemcpyAsync(pin_err, c->bred, sizeof(double) * ninst, cudaMemcpyDeviceToHost, c->stream));
         c->stats.kernel_launches += 3;
       }
-      st = ctx_sync_status(c);
+      st = ctx_sync_status(c);    // the try's one synchronisation
       if (st != ERS_OK) return batch_fail_where(c, st);
+      std::copy(pin_err, pin_err + ninst, err.begin());
+      std::copy(pin_dF, pin_dF + ninst, dF.begin());
+      if (!have_E) {
+        for (int i = 0; i < ninst; ++i)
+          E[i] = o.E_rr > 0 ? o.E_rr : tol * std::max(1.0, pin_xmax[i]);
+        std::copy(pin_mused, pin_mused + ninst, mused.begin());
+        have_E = true;
+      }
       int left = 0;
       for (int i = 0; i < ninst; ++i) {
         if (!trying[i]) continue;
@@ -1004,6 +1014,7 @@ ers_status ers_run_batch(ers_ctx* c, double t_end, double tol, int32_t max_steps
       if (st != ERS_OK) return ctx_fail(c, st, std::string("controller network: ") + ers_mlp_last_error(c->ctrl));
       BCU(cudaMemcpyAsync(pred.data(), c->d_pred, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, c->stream));
       BCU(cudaStreamSynchronize(c->stream));
+      c->stats.host_syncs++;
       c->stats.kernel_launches++;
       for (int q = 0; q < na; ++q) {
         int i = ask[q];

@@ -12,6 +12,28 @@
 
 namespace ers {
 
+// Piecewise-linear source value at x (constant beyond the table's ends).  The host evaluates
+// the same function to decide whether a step sees a ramp, so the product and the sum are
+// rounded separately on both sides (no fused multiply-add): the two agree bit for bit.
+__host__ __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np,
+                                                    double x) {
+  if (x <= t[0]) return v[0];
+  if (x >= t[np - 1]) return v[np - 1];
+  int lo = 0, hi = np - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (t[mid] <= x) lo = mid; else hi = mid;
+  }
+  const double f = (x - t[lo]) / (t[hi] - t[lo]);
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(v[lo], __dmul_rn(f, v[hi] - v[lo]));
+#else
+  volatile double prod = f * (v[hi] - v[lo]);
+  return v[lo] + prod;
+#endif
+}
+
+
 // device status bits (OR-ed into ctx->d_status[0])
 enum : unsigned {
   ST_SINGULAR = 1u,     // zero or tiny pivot in the refactor
@@ -194,6 +216,8 @@ struct ers_ctx {
   unsigned* h_status = nullptr;      // pinned mirror
   double* h_scalars = nullptr;       // pinned scalars for host decisions
   cudaEvent_t poll_ev[4] = {};       // lagged done-flag reads of adaptive Arnoldi builds
+  double* h_bpin = nullptr;          // batched: pinned per-instance reads (4 ninst doubles)
+  std::vector<int32_t> h_src_inst;   // batched: instance of each PWL source
   int coop_blocks = 0;
   // state
   double t = 0.0, h = 0.0;

@@ -987,17 +987,18 @@ cudaError_t solve_kernel_attributes() {
   return cudaSuccess;
 }
 
-// Solve G_k X = Y in place for nrhs vectors (stride n).  done (nrhs flags, or nullptr): the
-// whole pass is skipped on the device when every flag is set.
-cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done) {
+// Solve G_k X = Y in place for nrhs vectors (stride n).  done (ndone device flags, or
+// nullptr): the whole pass is skipped on the device when every flag is set.
+cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const* done, int ndone) {
   DevicePlan& P = c->plan;
   if (nrhs < 1 || nrhs > MAX_RHS) return cudaErrorInvalidValue;
+  if (done && (ndone < 1 || ndone > MAX_RHS)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(P.sync, 0, sizeof(int32_t) * solve_sync_words(P.nsn), c->stream);
   if (e != cudaSuccess) return e;
   SolveArgs A{P, y, c->n, c->d_status, c->solve_z, c->solve_part, {}, 0};
   if (done) {
-    for (int b = 0; b < nrhs; ++b) A.done[b] = done[b];
-    A.ndone = nrhs;
+    for (int b = 0; b < ndone; ++b) A.done[b] = done[b];
+    A.ndone = ndone;
   }
   int blocks = c->sm_count * c->solve_ctas_per_sm;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -1025,7 +1026,7 @@ cudaError_t launch_solve_skip(ers_ctx* c, double* y, int nrhs, const int* const*
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) { return launch_solve_skip(c, y, nrhs, nullptr); }
+cudaError_t launch_solve(ers_ctx* c, double* y, int nrhs) { return launch_solve_skip(c, y, nrhs, nullptr, 0); }
 
 }  // namespace ers
 

@@ -374,14 +374,14 @@ def make_opts(**kw) -> Opts:
     return o
 
 
-def analyze(pattern, ordering: int = 0) -> dict:
+def analyze(pattern, ordering: Optional[int] = None) -> dict:
     """Host-only symbolic analysis of a square CSR pattern (no GPU needed); ordering as the
     field of ers_opts."""
     h = _CsrHold(pattern)
     st = Stats()
     n = pattern.shape[0]
     perm = np.zeros(n, np.int32)
-    o = make_opts(ordering=ordering)
+    o = make_opts() if ordering is None else make_opts(ordering=ordering)
     rc = lib().ers_analyze(C.byref(h.c), C.byref(o), C.byref(st), _iptr(perm))
     if rc != 0:
         raise ErsError(rc, "symbolic analysis failed")
@@ -390,12 +390,12 @@ def analyze(pattern, ordering: int = 0) -> dict:
     return d
 
 
-def solve_plan_check(pattern, ordering: int = 0) -> dict:
+def solve_plan_check(pattern, ordering: Optional[int] = None) -> dict:
     """Host-only check of the solve work lists of a square CSR pattern (see ers.h); raises
     ErsError when a property is violated."""
     h = _CsrHold(pattern)
     counts = np.zeros(8, np.int64)
-    o = make_opts(ordering=ordering)
+    o = make_opts() if ordering is None else make_opts(ordering=ordering)
     rc = lib().ers_solve_plan_check(C.byref(h.c), C.byref(o),
                                     counts.ctypes.data_as(C.POINTER(C.c_int64)))
     if rc != 0:
@@ -413,11 +413,11 @@ PLAN_ARRAYS = [("perm", np.int32), ("sn_start", np.int32), ("sn_parent", np.int3
                ("arena", np.int64)]
 
 
-def plan_arrays(pattern, ordering: int = 0) -> dict:
+def plan_arrays(pattern, ordering: Optional[int] = None) -> dict:
     """Host-only export of the symbolic plan of a square CSR pattern (see ers_plan_array in
     ers.h): every array by name, in the plan's (new) node order."""
     h = _CsrHold(pattern)
-    o = make_opts(ordering=ordering)
+    o = make_opts() if ordering is None else make_opts(ordering=ordering)
     out = {}
     for which, (name, dt) in enumerate(PLAN_ARRAYS):
         ln = C.c_int64(0)
