@@ -837,6 +837,24 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   CUB(upload(&P.bwd_lane, S.bwd_lane));
   P.nfwd = (int)S.fwd.size();
   P.nbwd = (int)S.bwd.size();
+  // all-GROUP passes run warp-scheduled over their tasks flattened in entry order
+  auto flatten = [](const std::vector<SolveTask>& list, const std::vector<SolveTask>& small,
+                    std::vector<SolveTask>& out) {
+    out.clear();
+    for (const SolveTask& T : list) {
+      if (T.kind != TASK_GROUP) { out.clear(); return; }
+      for (int q = 0; q < T.r0; ++q) out.push_back(small[T.sn + q]);
+    }
+  };
+  {
+    std::vector<SolveTask> fw, bw;
+    flatten(S.fwd, S.fwd_small, fw);
+    flatten(S.bwd, S.bwd_small, bw);
+    if (!fw.empty()) CUB(upload(&P.fwd_warp, fw));
+    if (!bw.empty()) CUB(upload(&P.bwd_warp, bw));
+    P.nfwd_warp = (int)fw.size();
+    P.nbwd_warp = (int)bw.size();
+  }
   CUB(dalloc(&P.LDi, S.d_total));
   CUB(dalloc(&P.UDi, S.d_total));
   CUB(dalloc(&P.Lo, S.o_total));
@@ -1506,6 +1524,7 @@ void ers_destroy(ers_ctx* c) {
                   (void*)P.d_off, (void*)P.o_off, (void*)P.front_off, (void*)P.lvl_sn,
                   (void*)P.lvl_slot, (void*)P.ea_child, (void*)P.ch_ptr, (void*)P.ch_list, (void*)P.asm_dst, (void*)P.tile_sn,
                   (void*)P.tile_ij, (void*)P.ptask_sn, (void*)P.ptask_r0, (void*)P.fwd, (void*)P.bwd, (void*)P.fwd_small, (void*)P.bwd_small,
+                  (void*)P.fwd_warp, (void*)P.bwd_warp,
                   (void*)P.fwd_tgt, (void*)P.fwd_expect, (void*)P.bwd_nchunk, (void*)P.fwd_lane,
                   (void*)P.bwd_lane, (void*)P.LDi,
                   (void*)P.UDi, (void*)P.Lo, (void*)P.Uo, (void*)P.arena, (void*)P.sync})

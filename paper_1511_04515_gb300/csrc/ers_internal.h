@@ -90,6 +90,10 @@ struct DevicePlan {
   int32_t *fwd_tgt = nullptr, *fwd_expect = nullptr, *bwd_nchunk = nullptr;
   int32_t *fwd_lane = nullptr, *bwd_lane = nullptr;   // 4 ints per lane item
   int nfwd = 0, nbwd = 0;
+  // a pass whose entries are all GROUP entries: its warp tasks flattened in entry order, run
+  // by self-scheduling warps (n = 0: the CTA list above is used)
+  SolveTask *fwd_warp = nullptr, *bwd_warp = nullptr;
+  int nfwd_warp = 0, nbwd_warp = 0;
   // factor values
   double *LDi = nullptr, *UDi = nullptr, *Lo = nullptr, *Uo = nullptr;
   double* arena = nullptr;

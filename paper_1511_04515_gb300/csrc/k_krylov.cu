@@ -253,20 +253,39 @@ struct SmallArgs {
   const double* Htest; int ldh_test; int m_test; double* y_out; double* last_out;
 };
 
-__global__ void k_small(SmallArgs A) {
+// One space per cluster of SMALL_CS CTAs (kdense.cuh: every CTA computes a column slab of
+// each product and holds the whole result).  The CTA of rank 0 works on the space's state in
+// global memory; the others on a shared-memory copy that they update identically, so every
+// CTA takes the same branches and only rank 0 writes results.
+constexpr int SMALL_CS = 8;
+
+__global__ void __cluster_dims__(SMALL_CS, 1, 1) k_small(SmallArgs A) {
   extern __shared__ double smem[];
   __shared__ int ipiv[MAX_M];
   __shared__ double ybuf[MAX_M];
   __shared__ double s_last;
+  __shared__ KrylovState kcopy;
+  const unsigned rank = cl_rank();
   if (A.mode == SMALL_TEST) {
-    phi_small(A.Htest, A.ldh_test, A.m_test, A.h, ybuf, &s_last, smem, ipiv, A.pade);
-    for (int k = threadIdx.x; k < A.m_test; k += blockDim.x) A.y_out[k] = ybuf[k];
-    if (threadIdx.x == 0) *A.last_out = s_last;
+    phi_small<SMALL_CS>(A.Htest, A.ldh_test, A.m_test, A.h, ybuf, &s_last, smem, ipiv, A.pade);
+    if (rank == 0) {
+      for (int k = threadIdx.x; k < A.m_test; k += blockDim.x) A.y_out[k] = ybuf[k];
+      if (threadIdx.x == 0) *A.last_out = s_last;
+    }
     return;
   }
-  int b = blockIdx.x;
-  small_decide(A.mode, A.H[b], A.ks[A.slot[b]], A.h, A.eps, A.m_min, A.m_max, A.m_min, smem, ipiv, ybuf,
-               &s_last, A.status, A.pade);
+  const int b = blockIdx.x / SMALL_CS;
+  KrylovState* K = A.ks + A.slot[b];
+  if (rank != 0) {
+    const int* src = reinterpret_cast<const int*>(K);
+    int* dst = reinterpret_cast<int*>(&kcopy);
+    for (int e = threadIdx.x; e < (int)(sizeof(KrylovState) / sizeof(int)); e += blockDim.x)
+      dst[e] = src[e];
+    __syncthreads();
+    K = &kcopy;
+  }
+  small_decide<SMALL_CS>(A.mode, A.H[b], *K, A.h, A.eps, A.m_min, A.m_max, A.m_min, smem, ipiv,
+                         ybuf, &s_last, A.status, A.pade);
 }
 
 // out = a*in + sum_b c_b beta_b V_b (y_b - e_1) + d0 u0 + d1 u1; optional max|out| into
@@ -454,7 +473,7 @@ cudaError_t launch_small(ers_ctx* c, int mode, const VecGroup& g, double h, int 
   A.m_max = m_max;
   A.status = c->d_status;
   size_t sm = small_smem_doubles((size_t)c->opts.m_max) * 8;
-  k_small<<<g.nb, KB, sm, c->stream>>>(A);
+  k_small<<<g.nb * SMALL_CS, KB, sm, c->stream>>>(A);
   c->stats.kernel_launches++;
   return cudaGetLastError();
 }
@@ -471,7 +490,7 @@ cudaError_t launch_small_test(ers_ctx* c, const double* H, int ldh, int m, doubl
   A.y_out = y;
   A.last_out = last;
   size_t sm = small_smem_doubles((size_t)m) * 8;
-  k_small<<<1, KB, sm, c->stream>>>(A);
+  k_small<<<SMALL_CS, KB, sm, c->stream>>>(A);
   return cudaGetLastError();
 }
 

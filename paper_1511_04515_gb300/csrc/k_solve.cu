@@ -73,10 +73,12 @@ constexpr int SM_V = MAX_RHS * 64;       // vectors
 constexpr int SM_PART = 4 * 64 * MAX_RHS;
 constexpr int SOLVE_SMEM = (SM_D + SM_P + 2 * SM_V + SM_PART) * 8;
 
-// A GROUP entry gives each warp an equal share of the CTA's shared memory: its vectors (SM_V
-// doubles) and a staging area for its supernode's factor values.
-constexpr int WARP_SM = SOLVE_SMEM / 8 / (SOLVE_THREADS / 32);
-constexpr int STAGE_CAP = WARP_SM - SM_V;
+// A GROUP entry of k warp tasks gives each of them 1/k of the CTA's shared memory: its vectors
+// (SM_V doubles) and a staging area for its supernode's factor values; a self-scheduling warp
+// has 1/8 (WARP_SM).
+constexpr int CTA_SM = SOLVE_SMEM / 8;
+constexpr int WARP_SM = CTA_SM / (SOLVE_THREADS / 32);
+__device__ __forceinline__ int group_share(int ntasks) { return (CTA_SM / max(ntasks, 1)) & ~1; }
 
 // Asynchronous 8-byte global -> shared copies (they stay in flight through a dependency wait;
 // cp_async_wait_all makes them visible to the issuing lane, a __syncwarp to the warp).
@@ -160,7 +162,8 @@ __device__ __forceinline__ void fwd_panel(const SolveArgs& A, const double* M, c
 // staging area), first 32 row indices and first 32 targets are requested before the wait on
 // its children, so that only the y loads, the FMAs and the scatter follow the hand-off.
 template <int NRHS>
-__device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region) {
+__device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region,
+                          int cap) {
   const DevicePlan& P = A.P;
   double (*ys)[64] = reinterpret_cast<double (*)[64]>(region);
   double* stg = region + SM_V;
@@ -170,7 +173,12 @@ __device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   const double* Li = P.LDi + T.d_off;
   const double* Lo = P.Lo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
-  const bool staged = w * w + r * w <= STAGE_CAP;
+  // staging pays only while the children are still running: a task whose arrivals are all
+  // in streams its factor values directly (cap: the region's doubles after the vectors)
+  int pending = 0;
+  if (lane == 0) pending = ld_acquire(arrive + s) < T.wait_cnt;
+  pending = __shfl_sync(0xffffffffu, pending, 0);
+  const bool staged = pending && w * w + r * w <= cap;
   if (staged) {
     warp_stage(stg, Li, w * w, lane);
     warp_stage(stg + w * w, Lo, r * w, lane);
@@ -178,7 +186,7 @@ __device__ void fwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   const int row0 = lane < r ? __ldg(R + lane) : 0;
   const int tgt0 = lane < T.ntgt ? __ldg(P.fwd_tgt + T.tgt0 + lane) : 0;
   int ok = 1;
-  if (lane == 0) ok = wait_geq(arrive + s, T.wait_cnt, A.status);
+  if (lane == 0 && pending) ok = wait_geq(arrive + s, T.wait_cnt, A.status);   // else seen
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) { cp_async_wait_all(); __syncwarp(); return; }
   __threadfence();
@@ -266,7 +274,8 @@ __device__ __forceinline__ void warp_colsum8(const double* U, int64_t ld, int cb
 // requests what the parent does not write: the factor values (staged when they fit), the
 // first 64 row indices and y_s (only this task writes y_s in the backward pass).
 template <int NRHS>
-__device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region) {
+__device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, double* region,
+                          int cap) {
   const DevicePlan& P = A.P;
   double (*xs)[64] = reinterpret_cast<double (*)[64]>(region);
   double* stg = region + SM_V;
@@ -276,7 +285,12 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
   const double* Ui = P.UDi + T.d_off;
   const double* Uo = P.Uo + T.o_off;
   const int32_t* R = P.rows + T.row_off;
-  const bool staged = w * w + r * w <= STAGE_CAP;
+  // staging pays only while the parent is still running (cap: the region's doubles after
+  // the vectors)
+  int pending = 0;
+  if (lane == 0) pending = T.wait_sn >= 0 && ld_acquire(done + T.wait_sn) < 2;
+  pending = __shfl_sync(0xffffffffu, pending, 0);
+  const bool staged = pending && w * w + r * w <= cap;
   if (staged) {
     warp_stage(stg, Ui, w * w, lane);
     warp_stage(stg + w * w, Uo, r * w, lane);
@@ -291,7 +305,7 @@ __device__ void bwd_small(const SolveArgs& A, const SolveTask& T, int lane, doub
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) xs[k][q] = __ldcg(A.y + (int64_t)k * n + c0 + q);
   int ok = 1;
-  if (lane == 0 && T.wait_sn >= 0) ok = wait_geq(done + T.wait_sn, 2, A.status);
+  if (lane == 0 && pending) ok = wait_geq(done + T.wait_sn, 2, A.status);   // else seen
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) { cp_async_wait_all(); __syncwarp(); return; }
   __threadfence();
@@ -695,6 +709,36 @@ __device__ void mgemv(const SolveArgs& A, const SolveTask& T, double* sm, bool f
   }
 }
 
+// Work lists made of warp tasks only (tree-structured factors: chains, batches of chains):
+// every warp schedules itself over the flattened list (entries in order, each entry's tasks
+// in order, so still topological), with the next index fetched while the current task runs.
+// No CTA barrier is involved, so a warp whose task is done does not wait for the slowest warp
+// of its CTA.  Deadlock-free like the CTA list: a warp holds at most its current task and
+// the next one, and the smallest unfinished task is always being run.
+template <int NRHS, bool FWD>
+__device__ __forceinline__ void warp_scheduled(const SolveArgs& A, double* sm, int wq, int lane) {
+  const DevicePlan& P = A.P;
+  int32_t* ctr = P.sync + (FWD ? 0 : 1);
+  const SolveTask* list = FWD ? P.fwd_warp : P.bwd_warp;
+  const int N = FWD ? P.nfwd_warp : P.nbwd_warp;
+  double* region = sm + wq * WARP_SM;
+  int k = 0, nk = 0;
+  if (lane == 0) k = atomicAdd(ctr, 1);
+  k = __shfl_sync(0xffffffffu, k, 0);
+  while (k < N) {
+    if (lane == 0) nk = atomicAdd(ctr, 1);
+    const SolveTask& U = list[k];
+    if (FWD) {
+      if (U.kind == TASK_LANES) fwd_lanes<NRHS>(A, U, lane);
+      else fwd_small<NRHS>(A, U, lane, region, WARP_SM - SM_V);
+    } else {
+      if (U.kind == TASK_LANES) bwd_lanes<NRHS>(A, U, lane);
+      else bwd_small<NRHS>(A, U, lane, region, WARP_SM - SM_V);
+    }
+    k = __shfl_sync(0xffffffffu, nk, 0);
+  }
+}
+
 // MINB: resident CTAs per SM the kernel is compiled for (register cap 65536 / (256 MINB)); the
 // launch uses the instance matching the autotuned count, so no count pays the tighter cap.
 template <int NRHS, int MINB>
@@ -724,7 +768,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
       if (wq < T.r0) {
         const SolveTask& U = P.fwd_small[T.sn + wq];
         if (U.kind == TASK_LANES) fwd_lanes<NRHS>(A, U, lane);
-        else fwd_small<NRHS>(A, U, lane, sm + wq * WARP_SM);
+        else {
+          const int share = group_share(T.r0);
+          fwd_small<NRHS>(A, U, lane, sm + wq * share, share - SM_V);
+        }
       }
       continue;
     }
@@ -844,7 +891,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
       if (wq < T.r0) {
         const SolveTask& U = P.bwd_small[T.sn + wq];
         if (U.kind == TASK_LANES) bwd_lanes<NRHS>(A, U, lane);
-        else bwd_small<NRHS>(A, U, lane, sm + wq * WARP_SM);
+        else {
+          const int share = group_share(T.r0);
+          bwd_small<NRHS>(A, U, lane, sm + wq * share, share - SM_V);
+        }
       }
       continue;
     }
@@ -962,29 +1012,53 @@ cudaError_t launch_wait_probe(ers_ctx* c, const int32_t* flag) {
   return cudaGetLastError();
 }
 
-template <int NRHS>
-static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
-  if (c->solve_ctas_per_sm >= 3) {
-    k_trsv_fwd<NRHS, 3><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-    k_trsv_bwd<NRHS, 3><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-  } else {
-    k_trsv_fwd<NRHS, 2><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-    k_trsv_bwd<NRHS, 2><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-  }
+// The warp-scheduled passes (a work list of warp tasks only) as kernels of their own, so that
+// the CTA-list kernels keep their register allocation.
+template <int NRHS, int MINB, bool FWD>
+__global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_warp(SolveArgs A) {
+  extern __shared__ double sm[];
+  if (solve_skipped(A)) return;
+  warp_scheduled<NRHS, FWD>(A, sm, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
-cudaError_t solve_kernel_attributes() {
-  const void* fns[] = {(const void*)k_trsv_fwd<1, 2>, (const void*)k_trsv_fwd<2, 2>,
-                       (const void*)k_trsv_fwd<3, 2>, (const void*)k_trsv_bwd<1, 2>,
-                       (const void*)k_trsv_bwd<2, 2>, (const void*)k_trsv_bwd<3, 2>,
-                       (const void*)k_trsv_fwd<1, 3>, (const void*)k_trsv_fwd<2, 3>,
-                       (const void*)k_trsv_fwd<3, 3>, (const void*)k_trsv_bwd<1, 3>,
-                       (const void*)k_trsv_bwd<2, 3>, (const void*)k_trsv_bwd<3, 3>};
+template <int NRHS, int MINB>
+static void launch_pair_minb(ers_ctx* c, const SolveArgs& A, int blocks) {
+  if (A.P.nfwd_warp > 0)
+    k_trsv_warp<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  else
+    k_trsv_fwd<NRHS, MINB><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  if (A.P.nbwd_warp > 0)
+    k_trsv_warp<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  else
+    k_trsv_bwd<NRHS, MINB><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+}
+
+template <int NRHS>
+static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
+  if (c->solve_ctas_per_sm >= 3) launch_pair_minb<NRHS, 3>(c, A, blocks);
+  else launch_pair_minb<NRHS, 2>(c, A, blocks);
+}
+
+template <int NRHS, int MINB>
+static cudaError_t set_smem_attributes() {
+  const void* fns[] = {(const void*)k_trsv_fwd<NRHS, MINB>, (const void*)k_trsv_bwd<NRHS, MINB>,
+                       (const void*)k_trsv_warp<NRHS, MINB, true>,
+                       (const void*)k_trsv_warp<NRHS, MINB, false>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t solve_kernel_attributes() {
+  cudaError_t e = set_smem_attributes<1, 2>();
+  if (e == cudaSuccess) e = set_smem_attributes<2, 2>();
+  if (e == cudaSuccess) e = set_smem_attributes<3, 2>();
+  if (e == cudaSuccess) e = set_smem_attributes<1, 3>();
+  if (e == cudaSuccess) e = set_smem_attributes<2, 3>();
+  if (e == cudaSuccess) e = set_smem_attributes<3, 3>();
+  return e;
 }
 
 // Solve G_k X = Y in place for nrhs vectors (stride n).  done (ndone device flags, or

@@ -34,14 +34,62 @@ inline PadeCoef pade_coefficients(int deflate = 0) {
   return P;
 }
 
+// ---- a cluster of CS CTAs on one small dense problem ------------------------------------
+// GB300 issues FP64 at 2 FMA/clk/SM, so the m^3 products of the scaling and squaring take
+// tens of microseconds on one SM.  With CS > 1 each CTA of a thread-block cluster computes a
+// slab of columns of every product (and of the two multi-column LU solves) and stores it
+// into every CTA's copy through distributed shared memory; everything else (the LU
+// factorisations, the elementwise steps, the decisions) runs redundantly in every CTA on
+// identical data, so all CTAs hold the same bits and take the same branches.  Each element is
+// computed with the same operations in the same order as with CS = 1: the results are the
+// single-CTA results bit for bit.
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders the distributed stores before it
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_store(double* p, unsigned rank, double v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+// the columns [j0, j1) of an m-column result this CTA computes
+template <int CS>
+__device__ __forceinline__ void cl_slab(int m, int& j0, int& j1) {
+  if constexpr (CS == 1) {
+    j0 = 0;
+    j1 = m;
+  } else {
+    const int w = (m + CS - 1) / CS;
+    j0 = min(m, (int)cl_rank() * w);
+    j1 = min(m, j0 + w);
+  }
+}
+
+// C = A B (m x m, column-major).  CS > 1: C's slab goes to every CTA.  No CTA may read C
+// between the previous cluster barrier and this call (the callers below keep that rule).
+template <int CS = 1>
 __device__ inline void sm_matmul(double* C, const double* A, const double* B, int m) {
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e % m, jj = e / m;
+  int j0, j1;
+  cl_slab<CS>(m, j0, j1);
+  const int ne = (j1 - j0) * m;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int i = e % m, jj = j0 + e / m;
     double acc = 0.0;
     for (int k = 0; k < m; ++k) acc += A[i + k * m] * B[k + jj * m];
-    C[e] = acc;
+    C[i + jj * m] = acc;
+    if constexpr (CS > 1) {
+      const unsigned r = cl_rank();
+      for (int q = 1; q < CS; ++q) cl_store(C + i + jj * m, (r + q) % CS, acc);
+    }
   }
-  __syncthreads();
+  if constexpr (CS > 1) cl_sync();
+  else __syncthreads();
 }
 
 // LU with partial pivoting of M (m x m, column-major, in place); piv[k] = row swapped with k.
@@ -97,8 +145,16 @@ __device__ inline void sm_lu(double* M, int* piv, int m, double floor = 0.0) {
 // Solve (LU) X = B in place (B: m x m, column-major) with the CTA: the row permutation, then
 // forward and backward substitution row by row, each row's update of the rows below (above)
 // spread over all m columns.
+//
+// CS > 1: each CTA solves its slab of B's columns and sends it to every other CTA; a cluster
+// barrier first makes sure that no CTA still writes B locally.
+template <int CS = 1>
 __device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, int m) {
-  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+  int j0, j1;
+  cl_slab<CS>(m, j0, j1);
+  const int nc = j1 - j0;
+  if constexpr (CS > 1) cl_sync();
+  for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x) {
     double* b = B + jj * m;
     for (int k = 0; k < m; ++k)
       if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
@@ -106,21 +162,31 @@ __device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, 
   __syncthreads();
   for (int k = 0; k < m - 1; ++k) {          // L (unit diagonal): B[i,:] -= L[i,k] B[k,:]
     const int rem = m - k - 1;
-    for (int e = threadIdx.x; e < rem * m; e += blockDim.x) {
-      int i = k + 1 + e % rem, jj = e / rem;
+    for (int e = threadIdx.x; e < rem * nc; e += blockDim.x) {
+      int i = k + 1 + e % rem, jj = j0 + e / rem;
       B[i + jj * m] -= LU[i + k * m] * B[k + jj * m];
     }
     __syncthreads();
   }
   for (int k = m - 1; k >= 0; --k) {         // U: B[k,:] /= U[k,k]; B[i,:] -= U[i,k] B[k,:]
     const double d = LU[k + k * m];
-    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) B[k + jj * m] /= d;
+    for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x) B[k + jj * m] /= d;
     __syncthreads();
-    for (int e = threadIdx.x; e < k * m; e += blockDim.x) {
-      int i = e % k, jj = e / k;
+    for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+      int i = e % k, jj = j0 + e / k;
       B[i + jj * m] -= LU[i + k * m] * B[k + jj * m];
     }
     __syncthreads();
+  }
+  if constexpr (CS > 1) {
+    const unsigned r = cl_rank();
+    const int ne = nc * m;
+    for (int e = threadIdx.x; e < ne * (CS - 1); e += blockDim.x) {
+      const int q = 1 + e / ne, el = e % ne;
+      double* pe = B + (size_t)j0 * m + el;
+      cl_store(pe, (r + q) % CS, *pe);
+    }
+    cl_sync();
   }
 }
 
@@ -263,6 +329,7 @@ __device__ inline void sm_deflate(double* A, int m, double h, double* W, double*
 // Scaling and squaring of the diagonal [13/13] Pade approximant (theta_13 = 5.37), after the
 // deflation of near-null eigenvalues when pade.deflate is set (C with capacitor-free nodes).
 // Returns true when y and last are finite.  smem: small_smem_doubles(m) doubles.
+template <int CS = 1>
 __device__ inline bool phi_small(const double* H, int ldh, int m, double h, double* y,
                                  double* last, double* smem, int* ipiv, const PadeCoef& pade) {
   const double* c_pade = pade.c;
@@ -284,7 +351,7 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
   __syncthreads();
   if (pade.deflate) sm_deflate(M0, m, h, M2, M3, M4, vec + m, ipiv);
   sm_lu(M0, ipiv, m);
-  sm_lu_solve(M0, ipiv, M1, m);          // M1 = X = h H^-1
+  sm_lu_solve<CS>(M0, ipiv, M1, m);          // M1 = X = h H^-1
   for (int k = threadIdx.x; k < m; k += blockDim.x) lastrow[k] = M1[(m - 1) + k * m] / h;
   if (threadIdx.x == 0) {
     double nrm = 0.0;
@@ -310,23 +377,23 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
   double sc = ldexp(1.0, -s);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) M1[e] *= sc;
   __syncthreads();
-  sm_matmul(M2, M1, M1, m);   // A2
-  sm_matmul(M3, M2, M2, m);   // A4
-  sm_matmul(M4, M3, M2, m);   // A6
+  sm_matmul<CS>(M2, M1, M1, m);   // A2
+  sm_matmul<CS>(M3, M2, M2, m);   // A4
+  sm_matmul<CS>(M4, M3, M2, m);   // A6
   for (int e = threadIdx.x; e < m * m; e += blockDim.x)
     M0[e] = c_pade[13] * M4[e] + c_pade[11] * M3[e] + c_pade[9] * M2[e];
   __syncthreads();
-  sm_matmul(M5, M4, M0, m);
+  sm_matmul<CS>(M5, M4, M0, m);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int i = e % m, jj = e / m;
     M5[e] += c_pade[7] * M4[e] + c_pade[5] * M3[e] + c_pade[3] * M2[e] + (i == jj ? c_pade[1] : 0.0);
   }
   __syncthreads();
-  sm_matmul(M0, M1, M5, m);   // U
+  sm_matmul<CS>(M0, M1, M5, m);   // U
   for (int e = threadIdx.x; e < m * m; e += blockDim.x)
     M5[e] = c_pade[12] * M4[e] + c_pade[10] * M3[e] + c_pade[8] * M2[e];
   __syncthreads();
-  sm_matmul(M1, M4, M5, m);
+  sm_matmul<CS>(M1, M4, M5, m);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int i = e % m, jj = e / m;
     double V = M1[e] + c_pade[6] * M4[e] + c_pade[4] * M3[e] + c_pade[2] * M2[e] +
@@ -336,11 +403,11 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
   }
   __syncthreads();
   sm_lu(M2, ipiv, m);
-  sm_lu_solve(M2, ipiv, M3, m);   // R = (V - U)^-1 (V + U)
+  sm_lu_solve<CS>(M2, ipiv, M3, m);   // R = (V - U)^-1 (V + U)
   double* R = M3;
   double* Tm = M4;
   for (int q = 0; q + 1 < s; ++q) {
-    sm_matmul(Tm, R, R, m);
+    sm_matmul<CS>(Tm, R, R, m);
     double* t = R; R = Tm; Tm = t;
   }
   // y = R (R e_1) when s >= 1, else R e_1
@@ -385,6 +452,7 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
 // the chosen dimension is the one the plain rule picks, and never a larger one: past its
 // converged dimension a basis gathers rounding-noise directions whose spurious Ritz values
 // can pass the residual test with a wrong exp(h H^-1) e_1.
+template <int CS = 1>
 __device__ inline void small_decide(int mode, const double* H, KrylovState& K, double h,
                                     double eps, int m_min, int m_max, int m_first, double* smem,
                                     int* ipiv, double* ybuf, double* s_last, unsigned* status,
@@ -404,7 +472,7 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
   // residual test (Eq. 16) at dimension jj <= built; true (and y written, space done) if it
   // passes.  Tracks the smallest finite residual.
   auto test_dim = [&](int jj) -> bool {
-    bool fin = phi_small(H, ldh, jj, h, ybuf, s_last, smem, ipiv, pade);
+    bool fin = phi_small<CS>(H, ldh, jj, h, ybuf, s_last, smem, ipiv, pade);
     if (threadIdx.x == 0) {
       double res = H[jj + (jj - 1) * ldh] * K.gvnext[jj - 1] * fabs(*s_last) / K.gv1;
       if (!fin) res = INFINITY;
@@ -429,23 +497,23 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
   // dimension at a breakdown: built, or built-1 when the last direction was noise
   auto finalize_breakdown = [&]() {
     int m = s_built;
-    bool fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    bool fin = phi_small<CS>(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
     if (!fin && m > 1) {
       m -= 1;
-      fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+      fin = phi_small<CS>(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
     }
     if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
     write_y(m);
   };
   if (mode == SMALL_FINAL) {
-    bool fin = phi_small(H, ldh, s_m, h, ybuf, s_last, smem, ipiv, pade);
+    bool fin = phi_small<CS>(H, ldh, s_m, h, ybuf, s_last, smem, ipiv, pade);
     if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
     write_y(s_m);
     return;
   }
   if (mode == SMALL_FIXED_END) {
     if (s_bd) { finalize_breakdown(); return; }
-    bool fin = phi_small(H, ldh, s_built, h, ybuf, s_last, smem, ipiv, pade);
+    bool fin = phi_small<CS>(H, ldh, s_built, h, ybuf, s_last, smem, ipiv, pade);
     if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
     write_y(s_built);
     if (threadIdx.x == 0) K.done = 1;
@@ -476,10 +544,10 @@ __device__ inline void small_decide(int mode, const double* H, KrylovState& K, d
     // dimension had one, the largest dimension whose exp(h H^-1) e_1 is finite
     int m = K.best_m > 0 ? K.best_m : jj;
     __syncthreads();
-    bool fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+    bool fin = phi_small<CS>(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
     while (!fin && m > 1) {
       --m;
-      fin = phi_small(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
+      fin = phi_small<CS>(H, ldh, m, h, ybuf, s_last, smem, ipiv, pade);
     }
     if (!fin && threadIdx.x == 0) atomicOr(status, ST_KRYLOV);
     write_y(m);
