@@ -71,12 +71,17 @@ __device__ __forceinline__ void cl_slab(int m, int& j0, int& j1) {
   }
 }
 
-// C = A B (m x m, column-major).  CS > 1: C's slab goes to every CTA.  No CTA may read C
-// between the previous cluster barrier and this call (the callers below keep that rule).
+// Small dense products and solves run across the cluster from this dimension on; below it
+// every CTA computes them whole (the exchange would cost more than the FMAs it splits).
+constexpr int CL_MIN_M = 20;
+
+// C = A B (m x m, column-major).  CS > 1 and m >= CL_MIN_M: C's slab goes to every CTA; no
+// CTA may read C between the previous cluster barrier and this call (phi_small keeps that).
 template <int CS = 1>
 __device__ inline void sm_matmul(double* C, const double* A, const double* B, int m) {
-  int j0, j1;
-  cl_slab<CS>(m, j0, j1);
+  const bool split = CS > 1 && m >= CL_MIN_M;
+  int j0 = 0, j1 = m;
+  if (split) cl_slab<CS>(m, j0, j1);
   const int ne = (j1 - j0) * m;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int i = e % m, jj = j0 + e / m;
@@ -84,78 +89,105 @@ __device__ inline void sm_matmul(double* C, const double* A, const double* B, in
     for (int k = 0; k < m; ++k) acc += A[i + k * m] * B[k + jj * m];
     C[i + jj * m] = acc;
     if constexpr (CS > 1) {
-      const unsigned r = cl_rank();
-      for (int q = 1; q < CS; ++q) cl_store(C + i + jj * m, (r + q) % CS, acc);
+      if (split) {
+        const unsigned r = cl_rank();
+        for (int q = 1; q < CS; ++q) cl_store(C + i + jj * m, (r + q) % CS, acc);
+      }
     }
   }
-  if constexpr (CS > 1) cl_sync();
-  else __syncthreads();
+  if (split) {
+    if constexpr (CS > 1) cl_sync();
+  } else {
+    __syncthreads();
+  }
 }
 
-// LU with partial pivoting of M (m x m, column-major, in place); piv[k] = row swapped with k.
-// The pivot search is a warp arg-max (ties to the lowest row), the row swap, the scaling of
-// column k and the trailing update are spread over the CTA: two barriers per column.
-__device__ inline void sm_lu(double* M, int* piv, int m, double floor = 0.0) {
+// LU with partial pivoting of M (m x m, column-major, in place); piv[k] = row swapped with k;
+// rdiag (m doubles, may be nullptr) receives 1 / U[k,k].
+// GB300 runs FP64 at 2 FMA/clk/SM, so every FP64 instruction of a warp costs tens of
+// cycles; the per-column critical path is kept short: warp 0 finds the pivot comparing the
+// bit patterns of |M[i,k]| as integers (same order as the values for finite entries; ties to
+// the lowest row) and its lane 0 forms the one reciprocal inv = 1 / pivot; then the CTA swaps
+// rows k and p and forms the multipliers l_i = M[i,k] * inv; then the trailing update
+// M[i,j] -= l_i M[k,j] and column k = l.  Three barriers per column.  floor > 0: a pivot
+// below it is raised to it (sign kept).
+__device__ inline void sm_lu(double* M, int* piv, int m, double floor = 0.0,
+                             double* rdiag = nullptr) {
   __shared__ int s_p;
+  __shared__ double s_inv, s_pv;
+  __shared__ double s_l[MAX_M];
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < m; ++k) {
     if (threadIdx.x < 32) {
-      double best = -1.0;
-      int p = k;
+      unsigned long long best = 0ull;
+      int p = 0x7fffffff;                      // a lane without rows loses every tie
       for (int i = k + lane; i < m; i += 32) {
-        double v = fabs(M[i + k * m]);
-        if (v > best) { best = v; p = i; }
+        const unsigned long long v =
+            (unsigned long long)__double_as_longlong(M[i + k * m]) & 0x7fffffffffffffffull;
+        if (p == 0x7fffffff || v > best) { best = v; p = i; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int op = __shfl_xor_sync(0xffffffffu, p, o);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
         if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
       }
-      if (lane == 0) { s_p = p; piv[k] = p; }
+      if (lane == 0) {
+        s_p = p;
+        piv[k] = p;
+        double v = M[p + k * m];
+        if (floor > 0.0 && fabs(v) < floor) v = v < 0.0 ? -floor : floor;
+        s_pv = v;
+        s_inv = 1.0 / v;
+        if (rdiag) rdiag[k] = s_inv;
+      }
     }
     __syncthreads();
     const int p = s_p;
-    // swap rows k and p (all columns), then scale column k below the diagonal
+    const double inv = s_inv;
+    // rows k and p swap in every column but k; column k below the diagonal becomes the
+    // multipliers (its row p holds the old M[k,k] after the swap)
     if (p != k)
-      for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
-        double t = M[k + jj * m];
-        M[k + jj * m] = M[p + jj * m];
-        M[p + jj * m] = t;
-      }
+      for (int jj = threadIdx.x; jj < m; jj += blockDim.x)
+        if (jj != k) {
+          double t = M[k + jj * m];
+          M[k + jj * m] = M[p + jj * m];
+          M[p + jj * m] = t;
+        }
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x)
+      s_l[i] = (i == p ? M[k + k * m] : M[i + k * m]) * inv;
     __syncthreads();
-    if (floor > 0.0) {          // a pivot below the floor is raised to it (sign kept)
-      if (threadIdx.x == 0 && fabs(M[k + k * m]) < floor)
-        M[k + k * m] = M[k + k * m] < 0.0 ? -floor : floor;
-      __syncthreads();
-    }
-    const double inv = 1.0 / M[k + k * m];
+    if (threadIdx.x == 0) M[k + k * m] = s_pv;
     const int rem = m - k - 1;
-    // trailing update with the multipliers l_i = M[i,k] / M[k,k] formed on the fly (column k
-    // and row k are only read here), then column k is scaled
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
       int i = k + 1 + e % rem, jj = k + 1 + e / rem;
-      M[i + jj * m] -= (M[i + k * m] * inv) * M[k + jj * m];
+      M[i + jj * m] -= s_l[i] * M[k + jj * m];
     }
-    __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] *= inv;
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i + k * m] = s_l[i];
     __syncthreads();
   }
 }
 
-// Solve (LU) X = B in place (B: m x m, column-major) with the CTA: the row permutation, then
-// forward and backward substitution row by row, each row's update of the rows below (above)
-// spread over all m columns.
+// Solve (LU) X = B in place (B: m x m, column-major) with rdiag = 1 / U[k,k] from sm_lu: the
+// row permutation, then forward and backward substitution row by row, each step's update
+// spread over the CTA's threads one element each (lane-dense: on GB300 an FP64 warp
+// instruction costs the same with idle lanes).  Backward step k scales row k by rdiag[k] and
+// updates the rows above with the scaled value, which every thread forms itself; the scaled
+// row k is stored one step later, when no thread reads it any more: one barrier per step.
 //
-// CS > 1: each CTA solves its slab of B's columns and sends it to every other CTA; a cluster
-// barrier first makes sure that no CTA still writes B locally.
+// CS > 1 and m >= CL_MIN_M: each CTA solves its slab of B's columns and sends it to every
+// other CTA; a cluster barrier first makes sure that no CTA still writes B locally.
 template <int CS = 1>
-__device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, int m) {
-  int j0, j1;
-  cl_slab<CS>(m, j0, j1);
+__device__ inline void sm_lu_solve(const double* LU, const int* piv, const double* rdiag,
+                                   double* B, int m) {
+  const bool split = CS > 1 && m >= CL_MIN_M;
+  int j0 = 0, j1 = m;
+  if (split) cl_slab<CS>(m, j0, j1);
   const int nc = j1 - j0;
-  if constexpr (CS > 1) cl_sync();
+  if constexpr (CS > 1) {
+    if (split) cl_sync();
+  }
   for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x) {
-    double* b = B + jj * m;
+    double* b = B + (size_t)jj * m;
     for (int k = 0; k < m; ++k)
       if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
   }
@@ -168,25 +200,30 @@ __device__ inline void sm_lu_solve(const double* LU, const int* piv, double* B, 
     }
     __syncthreads();
   }
-  for (int k = m - 1; k >= 0; --k) {         // U: B[k,:] /= U[k,k]; B[i,:] -= U[i,k] B[k,:]
-    const double d = LU[k + k * m];
-    for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x) B[k + jj * m] /= d;
-    __syncthreads();
+  for (int k = m - 1; k >= 0; --k) {         // U: x_k = B[k,:] rdiag[k]; B[i,:] -= U[i,k] x_k
+    const double rd = rdiag[k];
     for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
       int i = e % k, jj = j0 + e / k;
-      B[i + jj * m] -= LU[i + k * m] * B[k + jj * m];
+      B[i + jj * m] -= LU[i + k * m] * (B[k + jj * m] * rd);
     }
+    if (k + 1 < m)                           // row k + 1 is final now: store it scaled
+      for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x)
+        B[k + 1 + jj * m] *= rdiag[k + 1];
     __syncthreads();
   }
+  for (int jj = j0 + threadIdx.x; jj < j1; jj += blockDim.x) B[jj * m] *= rdiag[0];
+  __syncthreads();
   if constexpr (CS > 1) {
-    const unsigned r = cl_rank();
-    const int ne = nc * m;
-    for (int e = threadIdx.x; e < ne * (CS - 1); e += blockDim.x) {
-      const int q = 1 + e / ne, el = e % ne;
-      double* pe = B + (size_t)j0 * m + el;
-      cl_store(pe, (r + q) % CS, *pe);
+    if (split) {
+      const unsigned r = cl_rank();
+      const int ne = nc * m;
+      for (int e = threadIdx.x; e < ne * (CS - 1); e += blockDim.x) {
+        const int q = 1 + e / ne, el = e % ne;
+        double* pe = B + (size_t)j0 * m + el;
+        cl_store(pe, (r + q) % CS, *pe);
+      }
+      cl_sync();
     }
-    cl_sync();
   }
 }
 
@@ -350,16 +387,20 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
   }
   __syncthreads();
   if (pade.deflate) sm_deflate(M0, m, h, M2, M3, M4, vec + m, ipiv);
-  sm_lu(M0, ipiv, m);
-  sm_lu_solve<CS>(M0, ipiv, M1, m);          // M1 = X = h H^-1
+  __shared__ double s_rd[MAX_M];
+  sm_lu(M0, ipiv, m, 0.0, s_rd);
+  sm_lu_solve<CS>(M0, ipiv, s_rd, M1, m);    // M1 = X = h H^-1
   for (int k = threadIdx.x; k < m; k += blockDim.x) lastrow[k] = M1[(m - 1) + k * m] / h;
+  __shared__ double s_cs[MAX_M];
+  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {   // column sums of |X|, rows in order
+    double cs = 0.0;
+    for (int i = 0; i < m; ++i) cs += fabs(M1[i + jj * m]);
+    s_cs[jj] = cs;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double nrm = 0.0;
-    for (int jj = 0; jj < m; ++jj) {
-      double cs = 0.0;
-      for (int i = 0; i < m; ++i) cs += fabs(M1[i + jj * m]);
-      nrm = fmax(nrm, cs);
-    }
+    for (int jj = 0; jj < m; ++jj) nrm = fmax(nrm, s_cs[jj]);
     s_norm = nrm;
     int s = 0;
     if (nrm > 5.371920351148152) s = (int)ceil(log2(nrm / 5.371920351148152));
@@ -402,8 +443,8 @@ __device__ inline bool phi_small(const double* H, int ldh, int m, double h, doub
     M3[e] = V + M0[e];
   }
   __syncthreads();
-  sm_lu(M2, ipiv, m);
-  sm_lu_solve<CS>(M2, ipiv, M3, m);   // R = (V - U)^-1 (V + U)
+  sm_lu(M2, ipiv, m, 0.0, s_rd);
+  sm_lu_solve<CS>(M2, ipiv, s_rd, M3, m);   // R = (V - U)^-1 (V + U)
   double* R = M3;
   double* Tm = M4;
   for (int q = 0; q + 1 < s; ++q) {
