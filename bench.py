@@ -296,6 +296,7 @@ def mesh2d_line(ers, stream, steps=1000):
     sim.set_stream(stream)
     sim.set_state(0.0, np.zeros(circ.n))
     sim.step(1e-12, 20)                       # factor G once, warm the kernels
+    tuned, tune_ms = sim.autotune(nrhs=1, passes=5)   # resident CTAs per SM of the solves
     sim.set_state(0.0, np.zeros(circ.n))
     torch.cuda.synchronize()
     st0 = sim.stats()
@@ -317,6 +318,7 @@ def mesh2d_line(ers, stream, steps=1000):
            "krylov_vectors_per_s": (st1["krylov_vectors"] - st0["krylov_vectors"]) / (ms * 1e-3),
            "gpu_launches_per_step": (st1["kernel_launches"] - st0["kernel_launches"]) / steps,
            "host_syncs_per_step": (st1["host_syncs"] - st0["host_syncs"]) / steps,
+           "solve_ctas_per_sm": tuned, "autotune_ms_per_pass_at_1_2_3": tune_ms,
            "l2_flush": ("one 256 MB write before the run; the 1024-node factor stays in L2 "
                         "across the 1000 steps of the run, as in any use of this size")}
     sim.close()

@@ -1343,23 +1343,31 @@ ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, in
   const bool prof = c->profile;
   c->profile = false;
   double best = INFINITY;
-  int keep = c->solve_ctas_per_sm;
+  int keep = c->solve_ctas_per_sm, keep_v = c->solve_variant;
   cudaError_t err = cudaSuccess;
+  // a variant only matters where a pass uses the CTA-list kernels
+  const int nvar = (c->plan.nfwd_warp > 0 && c->plan.nbwd_warp > 0) ? 1 : 2;
   for (int k = 1; k <= 3 && err == cudaSuccess; ++k) {
-    c->solve_ctas_per_sm = k;
-    err = launch_solve(c, c->solve_buf, nrhs);   // warm-up pass
-    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-    for (int q = 0; q < passes && err == cudaSuccess; ++q) err = launch_solve(c, c->solve_buf, nrhs);
-    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    float t = 0.f;
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
-    double avg = (double)t / passes;
-    if (ms) ms[k - 1] = avg;
-    if (err == cudaSuccess && avg < best) { best = avg; keep = k; }
+    double best_k = INFINITY;
+    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+      c->solve_ctas_per_sm = k;
+      c->solve_variant = v;
+      err = launch_solve(c, c->solve_buf, nrhs);   // warm-up pass
+      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+      for (int q = 0; q < passes && err == cudaSuccess; ++q) err = launch_solve(c, c->solve_buf, nrhs);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+      const double avg = (double)t / passes;
+      best_k = std::min(best_k, avg);
+      if (err == cudaSuccess && avg < best) { best = avg; keep = k; keep_v = v; }
+    }
+    if (ms) ms[k - 1] = best_k;
   }
   c->profile = prof;
   c->solve_ctas_per_sm = keep;
+  c->solve_variant = keep_v;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(c, ERS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));

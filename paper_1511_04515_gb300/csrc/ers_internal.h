@@ -179,6 +179,7 @@ struct ers_ctx {
   int device = 0;
   int sm_count = 0;
   int solve_ctas_per_sm = 3;           // resident CTAs per SM of the persistent solves (tunable)
+  int solve_variant = 0;               // code variant of the CTA-list solve kernels (tunable)
   // host copies (permuted) needed by the host-side step orchestration
   std::vector<double> bp;              // sorted unique PWL corner times
   std::vector<int32_t> h_pwl_ptr;      // PWL tables (the device's copy is pwl_*)

@@ -739,9 +739,19 @@ __device__ __forceinline__ void warp_scheduled(const SolveArgs& A, double* sm, i
   }
 }
 
+// The same loop out of line.  The CTA-list kernels come in two variants, without (OOL =
+// false) and with a call of it on their entry path (never taken for their lists): ptxas
+// allocates their registers differently, and which variant is faster depends on the work
+// list (one is 30 % faster on the 32 x 32 mesh, the other 7 % faster on the 100^3 mesh), so
+// the autotuner times both.
+template <int NRHS, bool FWD>
+__device__ __noinline__ void warp_scheduled_ool(const SolveArgs& A, double* sm, int wq, int lane) {
+  warp_scheduled<NRHS, FWD>(A, sm, wq, lane);
+}
+
 // MINB: resident CTAs per SM the kernel is compiled for (register cap 65536 / (256 MINB)); the
 // launch uses the instance matching the autotuned count, so no count pays the tighter cap.
-template <int NRHS, int MINB>
+template <int NRHS, int MINB, bool OOL>
 __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
   extern __shared__ double sm[];
   double* sD = sm;
@@ -757,6 +767,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
   int32_t* ready = sync + 2 + P.nsn;
   const int n = A.n;
   if (solve_skipped(A)) return;
+  if constexpr (OOL) {
+    if (P.nfwd_warp > 0) {
+      warp_scheduled_ool<NRHS, true>(A, sm, threadIdx.x >> 5, threadIdx.x & 31);
+      return;
+    }
+  }
   while (true) {
     __syncthreads();
     if (tid == 0) s_cur = atomicAdd(sync, 1);
@@ -864,7 +880,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_fwd(SolveArgs A) {
   }
 }
 
-template <int NRHS, int MINB>
+template <int NRHS, int MINB, bool OOL>
 __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
   extern __shared__ double sm[];
   double* sD = sm;
@@ -880,6 +896,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_bwd(SolveArgs A) {
   int32_t* arriveb = sync + 2 + 2 * P.nsn;
   const int n = A.n;
   if (solve_skipped(A)) return;
+  if constexpr (OOL) {
+    if (P.nbwd_warp > 0) {
+      warp_scheduled_ool<NRHS, false>(A, sm, threadIdx.x >> 5, threadIdx.x & 31);
+      return;
+    }
+  }
   while (true) {
     __syncthreads();
     if (tid == 0) s_cur = atomicAdd(sync + 1, 1);
@@ -1023,14 +1045,19 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_warp(SolveArgs A) 
 
 template <int NRHS, int MINB>
 static void launch_pair_minb(ers_ctx* c, const SolveArgs& A, int blocks) {
+  const bool ool = c->solve_variant != 0;
   if (A.P.nfwd_warp > 0)
     k_trsv_warp<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  else if (ool)
+    k_trsv_fwd<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   else
-    k_trsv_fwd<NRHS, MINB><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+    k_trsv_fwd<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   if (A.P.nbwd_warp > 0)
     k_trsv_warp<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+  else if (ool)
+    k_trsv_bwd<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   else
-    k_trsv_bwd<NRHS, MINB><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
+    k_trsv_bwd<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
 }
 
 template <int NRHS>
@@ -1041,7 +1068,10 @@ static void launch_pair(ers_ctx* c, const SolveArgs& A, int blocks) {
 
 template <int NRHS, int MINB>
 static cudaError_t set_smem_attributes() {
-  const void* fns[] = {(const void*)k_trsv_fwd<NRHS, MINB>, (const void*)k_trsv_bwd<NRHS, MINB>,
+  const void* fns[] = {(const void*)k_trsv_fwd<NRHS, MINB, false>,
+                       (const void*)k_trsv_bwd<NRHS, MINB, false>,
+                       (const void*)k_trsv_fwd<NRHS, MINB, true>,
+                       (const void*)k_trsv_bwd<NRHS, MINB, true>,
                        (const void*)k_trsv_warp<NRHS, MINB, true>,
                        (const void*)k_trsv_warp<NRHS, MINB, false>};
   for (const void* f : fns) {
