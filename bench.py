@@ -36,10 +36,10 @@ FP64_FMA_PER_CLK_PER_SM = 2        # GB300: FP64 issue rate per SM (1/64 of FP32
 # the 70^3 mesh; the full-size traffic is this ratio times the full-size algorithmic bytes
 # (traffic grows with the factor).  Set to None whenever k_trsv_fwd / k_trsv_bwd change until
 # a new capture is taken.
-SOLVE_TRAFFIC_RATIO = 2.692 / 2.562
-SOLVE_TRAFFIC_SOURCE = ("ncu dram bytes of the 70^3 pair (k_trsv_fwd<2,2> + k_trsv_bwd<2,2>: "
-                        "2.692 GB vs 2.562 GB algorithmic) scaled to the 100^3 pair by its "
-                        "algorithmic bytes")
+SOLVE_TRAFFIC_RATIO = 2.156 / 2.023
+SOLVE_TRAFFIC_SOURCE = ("ncu dram bytes of the 70^3 pair (k_trsv_fwd<2,3,0> + k_trsv_bwd<2,3,0>, "
+                        "ordering 1: 2.156 GB vs 2.023 GB algorithmic) scaled to the 100^3 pair "
+                        "by its algorithmic bytes")
 CLOCKS_DIR = os.environ.get("ERS_CLOCKS_DIR") or os.path.join(ROOT, ".bench")   # nvidia-smi samples
 L2_BYTES = 129 * 2 ** 20              # GB300 L2; smaller factors get an L2 flush before each step
 FLUSH_BYTES = 256 * 2 ** 20
