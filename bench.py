@@ -577,8 +577,8 @@ def batch_oracle_baseline(circs, idx, t_end, tol):
     steps = sum(r[0] for r in res)
     return {"value": steps / wall, "unit": "instance-steps/s", "cores": cores, "kind": "oracle",
             "sample": (f"{len(idx)} instances of the batch to t_end, one per worker process "
-                       f"(spawn, 1 BLAS thread each), the oracle's own sparse LU + numpy; {steps} steps in "
-                       f"{wall:.1f} s wall; per-instance seconds "
+                       f"(spawn, 1 BLAS thread each), the oracle's own sparse LU + numpy; "
+                       f"{steps} steps in {wall:.1f} s wall; per-instance seconds "
                        f"{[round(r[1], 1) for r in res]}")}
 
 
