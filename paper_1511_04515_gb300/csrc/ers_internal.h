@@ -105,7 +105,7 @@ struct DevicePlan {
   // solve sync words: [0], [1] task counters of the two passes, then per supernode: arrivals,
   // ready / done flags, backward arrivals, forward and backward row-tile counters of merged
   // pieces, and the completed row tiles of each merged block (at its first piece)
-  int32_t* sync = nullptr;   // SOLVE_SYNC_WORDS(nsn) ints
+  int32_t* sync = nullptr;   // solve_sync_words(nsn) ints
 };
 
 constexpr size_t solve_sync_words(size_t nsn) { return 2 + 6 * nsn; }
