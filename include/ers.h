@@ -395,8 +395,9 @@ ers_status ers_wait_selftest(ers_ctx* ctx);
  * context refactors first if needed) time `passes` solve passes of `nrhs` (1-3) right-hand
  * sides for 1, 2 and 3 resident CTAs per SM (any count is deadlock-free: a task only waits on
  * earlier tasks of the ordered work list), each in both code variants of the CTA-list solve
- * kernels (their register allocations differ; which is faster depends on the factor), and
- * keep the fastest combination for the context's later solves.  ms (3 doubles, may be NULL)
+ * kernels (their register allocations differ; which is faster depends on the factor) and,
+ * where a pass's work list holds only small-supernode groups, with that pass run from the CTA
+ * list or warp-scheduled; keep the fastest combination for the context's later solves.  ms (3 doubles, may be NULL)
  * receives the average pass time of each count (its faster variant); *chosen (may be NULL)
  * the count kept.  Changes no result: the same tasks run with the same dependencies. */
 ers_status ers_autotune(ers_ctx* ctx, int32_t nrhs, int32_t passes, double* ms, int32_t* chosen);

@@ -1344,14 +1344,26 @@ ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, in
   c->profile = false;
   double best = INFINITY;
   int keep = c->solve_ctas_per_sm, keep_v = c->solve_variant;
+  bool keep_wf = c->solve_warp_fwd, keep_wb = c->solve_warp_bwd;
   cudaError_t err = cudaSuccess;
-  // a variant only matters where a pass uses the CTA-list kernels
-  const int nvar = (c->plan.nfwd_warp > 0 && c->plan.nbwd_warp > 0) ? 1 : 2;
+  // configurations: the code variant of the CTA-list kernels and, for passes whose lists are
+  // all GROUP entries, CTA-list or warp-scheduled execution of each direction
+  struct Cfg { int v; bool wf, wb; };
+  std::vector<Cfg> cfgs;
+  const bool can_wf = c->plan.nfwd_warp > 0, can_wb = c->plan.nbwd_warp > 0;
+  for (int v = 0; v < 2; ++v)
+    for (int wf = 0; wf <= (can_wf ? 1 : 0); ++wf)
+      for (int wb = 0; wb <= (can_wb ? 1 : 0); ++wb)
+        if (!(v == 1 && wf && wb)) cfgs.push_back({v, wf != 0, wb != 0});
   for (int k = 1; k <= 3 && err == cudaSuccess; ++k) {
     double best_k = INFINITY;
-    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+    for (size_t ci = 0; ci < cfgs.size() && err == cudaSuccess; ++ci) {
+      const Cfg& cf = cfgs[ci];
+      const int v = cf.v;
       c->solve_ctas_per_sm = k;
       c->solve_variant = v;
+      c->solve_warp_fwd = cf.wf;
+      c->solve_warp_bwd = cf.wb;
       err = launch_solve(c, c->solve_buf, nrhs);   // warm-up pass
       if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
       for (int q = 0; q < passes && err == cudaSuccess; ++q) err = launch_solve(c, c->solve_buf, nrhs);
@@ -1361,13 +1373,21 @@ ers_status ers_autotune(ers_ctx* c, int32_t nrhs, int32_t passes, double* ms, in
       if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
       const double avg = (double)t / passes;
       best_k = std::min(best_k, avg);
-      if (err == cudaSuccess && avg < best) { best = avg; keep = k; keep_v = v; }
+      if (err == cudaSuccess && avg < best) {
+        best = avg;
+        keep = k;
+        keep_v = v;
+        keep_wf = cf.wf;
+        keep_wb = cf.wb;
+      }
     }
     if (ms) ms[k - 1] = best_k;
   }
   c->profile = prof;
   c->solve_ctas_per_sm = keep;
   c->solve_variant = keep_v;
+  c->solve_warp_fwd = keep_wf;
+  c->solve_warp_bwd = keep_wb;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(c, ERS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));

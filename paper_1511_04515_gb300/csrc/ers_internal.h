@@ -180,6 +180,9 @@ struct ers_ctx {
   int sm_count = 0;
   int solve_ctas_per_sm = 3;           // resident CTAs per SM of the persistent solves (tunable)
   int solve_variant = 0;               // code variant of the CTA-list solve kernels (tunable)
+  // all-GROUP passes: run warp-scheduled (else as the CTA list); tunable.  The defaults are
+  // the faster choices on the 2000-stage chain: CTA list forward, warp-scheduled backward
+  bool solve_warp_fwd = false, solve_warp_bwd = true;
   // host copies (permuted) needed by the host-side step orchestration
   std::vector<double> bp;              // sorted unique PWL corner times
   std::vector<int32_t> h_pwl_ptr;      // PWL tables (the device's copy is pwl_*)

@@ -1046,13 +1046,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS, MINB) k_trsv_warp(SolveArgs A) 
 template <int NRHS, int MINB>
 static void launch_pair_minb(ers_ctx* c, const SolveArgs& A, int blocks) {
   const bool ool = c->solve_variant != 0;
-  if (A.P.nfwd_warp > 0)
+  if (A.P.nfwd_warp > 0 && c->solve_warp_fwd)
     k_trsv_warp<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   else if (ool)
     k_trsv_fwd<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   else
     k_trsv_fwd<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
-  if (A.P.nbwd_warp > 0)
+  if (A.P.nbwd_warp > 0 && c->solve_warp_bwd)
     k_trsv_warp<NRHS, MINB, false><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
   else if (ool)
     k_trsv_bwd<NRHS, MINB, true><<<blocks, SOLVE_THREADS, SOLVE_SMEM, c->stream>>>(A);
