@@ -531,7 +531,8 @@ int coop_max_blocks(int sm_count) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, init_kernel(nb), KB, 0);
     per_sm = std::min(per_sm, std::min(o1, o2));
   }
-  return std::max(1, per_sm * sm_count);
+  // the reduction scratch holds 2 * GRID_RED_NV partials per block in 2 * MAX_RHS * 4096 doubles
+  return std::max(1, std::min(per_sm * sm_count, MAX_RHS * 4096 / GRID_RED_NV));
 }
 
 }  // namespace ers
