@@ -10,6 +10,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 PROGRAM = r"""
+#include <stddef.h>
 #include <stdio.h>
 #include "ers.h"
 
@@ -28,6 +29,10 @@ int main(void) {
   if (ers_solve_plan_check(&G, &o, counts) != ERS_OK) return 3;
   printf("%d %lld %lld %g %d\n", (int)st.n, (long long)st.nnz_L, (long long)counts[0],
          o.eps_krylov, (int)o.m_max);
+  /* struct layouts, for the binding's mirror of them */
+  printf("%zu %zu %zu %zu %zu %d\n", sizeof(ers_opts), offsetof(ers_opts, ordering),
+         sizeof(ers_stats_t), offsetof(ers_stats_t, host_syncs), offsetof(ers_stats_t, host_polls),
+         (int)o.ordering);
   return 0;
 }
 """
@@ -57,6 +62,15 @@ def test_c_program_uses_the_library(lib_dir):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stderr)
-    n, nnz_l, entries, eps, m_max = r.stdout.split()
+    line1, line2 = r.stdout.strip().splitlines()
+    n, nnz_l, entries, eps, m_max = line1.split()
     assert int(n) == 4 and int(nnz_l) == 7          # a path has no fill: 4 + 3 entries
     assert int(entries) >= 1 and float(eps) == 1e-7 and int(m_max) == 40
+    # the ctypes mirrors in the binding have the header's layout
+    import ctypes
+    from paper_1511_04515_gb300 import ers
+    so, off_ord, ss, off_sync, off_poll, ordering = (int(v) for v in line2.split())
+    assert so == ctypes.sizeof(ers.Opts) and off_ord == ers.Opts.ordering.offset
+    assert ss == ctypes.sizeof(ers.Stats)
+    assert off_sync == ers.Stats.host_syncs.offset and off_poll == ers.Stats.host_polls.offset
+    assert ordering == ers.default_opts().ordering == 1
