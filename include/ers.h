@@ -438,6 +438,14 @@ enum { ERS_PLAN_PERM = 0, ERS_PLAN_SN_START, ERS_PLAN_SN_PARENT, ERS_PLAN_LEVEL,
 ers_status ers_plan_array(const ers_csr* pattern, const ers_opts* opts, int32_t which, void* out,
                           int64_t* len);
 
+/* Host-only: the ramp test of a step's set-up (Eq. 12-13: the v2 and w1 terms exist only when
+ * some input has a non-zero slope (u(t + h) - u(t)) / h over the step).  *ramp = 1 when some
+ * of the p PWL inputs gives pwl(t + h) != pwl(t), evaluated with the device kernel's
+ * arithmetic (product and sum rounded separately, so the two decisions agree bit for bit);
+ * ers_step and ers_run take this decision on the host instead of reading the slopes back.
+ * ERS_ERR_INVALID for a NULL pointer or corner times that do not increase. */
+ers_status ers_pwl_ramp(const ers_pwl* u, int32_t p, double t, double h, int32_t* ramp);
+
 /* Host-only: longest-processing-time-first partition of n jobs with costs cost[i] >= 0 over
  * nparts >= 1 parts (the device split of ers_create_batch): jobs by decreasing cost (ties:
  * lower index first) each onto the least-loaded part (ties: lower part), which keeps the

@@ -333,19 +333,40 @@ struct StepWork {
 // Whether some source's slope (u(t + h) - u(t)) / h is non-zero, i.e. whether the device's
 // k_pwl gives a non-zero slope (same pwl_eval, same t + h): no device round trip needed.
 // Steps whose [t, t + h] meets no range in which a source changes are decided at once.
-bool host_ramp(const ers_ctx* c, double t, double h) {
+// ptr / tt / vv: the concatenated PWL tables; active: the merged ranges [t_k, t_k+1] of the
+// segments whose end values differ.
+bool pwl_ramp(const std::vector<int32_t>& ptr, const std::vector<double>& tt,
+              const std::vector<double>& vv, const std::vector<std::pair<double, double>>& active,
+              double t, double h) {
   if (!(h > 0.0)) return false;
   const double t1 = t + h;
-  auto it = std::lower_bound(c->pwl_active.begin(), c->pwl_active.end(), t,
+  auto it = std::lower_bound(active.begin(), active.end(), t,
                              [](const std::pair<double, double>& a, double x) { return a.second < x; });
-  if (it == c->pwl_active.end() || it->first > t1) return false;
-  for (int q = 0; q < c->p; ++q) {
-    const int o = c->h_pwl_ptr[q], np = c->h_pwl_ptr[q + 1] - o;
-    const double* tt = c->h_pwl_t.data() + o;
-    const double* vv = c->h_pwl_v.data() + o;
-    if (pwl_eval(tt, vv, np, t1) != pwl_eval(tt, vv, np, t)) return true;
+  if (it == active.end() || it->first > t1) return false;
+  for (size_t q = 0; q + 1 < ptr.size(); ++q) {
+    const int o = ptr[q], np = ptr[q + 1] - o;
+    if (pwl_eval(tt.data() + o, vv.data() + o, np, t1) != pwl_eval(tt.data() + o, vv.data() + o, np, t))
+      return true;
   }
   return false;
+}
+
+void pwl_active_ranges(const std::vector<int32_t>& ptr, const std::vector<double>& tt,
+                       const std::vector<double>& vv, std::vector<std::pair<double, double>>& out) {
+  std::vector<std::pair<double, double>> act;
+  for (size_t q = 0; q + 1 < ptr.size(); ++q)
+    for (int k = ptr[q]; k + 1 < ptr[q + 1]; ++k)
+      if (vv[k] != vv[k + 1]) act.push_back({tt[k], tt[k + 1]});
+  std::sort(act.begin(), act.end());
+  out.clear();
+  for (auto& a : act) {
+    if (!out.empty() && a.first <= out.back().second) out.back().second = std::max(out.back().second, a.second);
+    else out.push_back(a);
+  }
+}
+
+bool host_ramp(const ers_ctx* c, double t, double h) {
+  return pwl_ramp(c->h_pwl_ptr, c->h_pwl_t, c->h_pwl_v, c->pwl_active, t, h);
 }
 
 // Setup vectors of Eq. 12-13 at (t, x_k) for a step of h, and the solution bases.
@@ -742,19 +763,7 @@ ers_status ers::create_context(ers_ctx* c, const ers_csr* G, const ers_csr* C, c
   c->h_pwl_v = pv;
   // the time ranges in which some source changes: [t_k, t_k+1] of every segment whose end
   // values differ (a zero-width jump included), merged
-  {
-    std::vector<std::pair<double, double>> act;
-    for (int q = 0; q < p; ++q)
-      for (int k = pptr[q]; k + 1 < pptr[q + 1]; ++k)
-        if (pv[k] != pv[k + 1]) act.push_back({pt[k], pt[k + 1]});
-    std::sort(act.begin(), act.end());
-    for (auto& a : act) {
-      if (!c->pwl_active.empty() && a.first <= c->pwl_active.back().second)
-        c->pwl_active.back().second = std::max(c->pwl_active.back().second, a.second);
-      else
-        c->pwl_active.push_back(a);
-    }
-  }
+  pwl_active_ranges(pptr, pt, pv, c->pwl_active);
   // devices
   std::vector<int32_t> dtype(ndev), dterm(3 * std::max(ndev, 0));
   std::vector<double> dpar(3 * std::max(ndev, 0));
@@ -1523,6 +1532,25 @@ ers_status ers_plan_array(const ers_csr* pat, const ers_opts* opts, int32_t whic
     if (v32) std::memcpy(out, v32->data(), sizeof(int32_t) * v32->size());
     else std::memcpy(out, v64->data(), sizeof(int64_t) * v64->size());
   }
+  return ERS_OK;
+}
+
+ers_status ers_pwl_ramp(const ers_pwl* u, int32_t p, double t, double h, int32_t* ramp) {
+  if (!ramp || p < 0 || (p > 0 && !u)) return ERS_ERR_INVALID;
+  std::vector<int32_t> ptr(1, 0);
+  std::vector<double> tt, vv;
+  for (int q = 0; q < p; ++q) {
+    if (u[q].npts < 1 || !u[q].t || !u[q].v) return ERS_ERR_INVALID;
+    for (int k = 0; k < u[q].npts; ++k) {
+      if (k > 0 && !(u[q].t[k] > u[q].t[k - 1])) return ERS_ERR_INVALID;
+      tt.push_back(u[q].t[k]);
+      vv.push_back(u[q].v[k]);
+    }
+    ptr.push_back((int32_t)tt.size());
+  }
+  std::vector<std::pair<double, double>> active;
+  pwl_active_ranges(ptr, tt, vv, active);
+  *ramp = pwl_ramp(ptr, tt, vv, active, t, h) ? 1 : 0;
   return ERS_OK;
 }
 

@@ -97,7 +97,8 @@ EXPORTS = ["ers_default_opts", "ers_create", "ers_set_stream", "ers_dc", "ers_re
            "ers_mlp_destroy", "ers_batch_set_controller", "ers_batch_trace", "ers_batch_records",
            "ers_batch_samples", "ers_batch_ctrl_stats", "ers_ctrl_propose",
            "ers_batch_set_graphs", "ers_autotune", "ers_solve_plan_check",
-           "ers_wait_selftest", "ers_plan_array", "ers_partition_lpt", "ers_fp64_fma_peak"]
+           "ers_wait_selftest", "ers_plan_array", "ers_partition_lpt", "ers_fp64_fma_peak",
+           "ers_pwl_ramp"]
 
 _lib = None
 
@@ -140,6 +141,7 @@ def lib():
         "ers_create_batch": ([C.POINTER(P), C.POINTER(Instance), I32, pi, I32, C.POINTER(Opts)],
                              C.c_int),
         "ers_partition_lpt": ([pd, I32, I32, pi], C.c_int),
+        "ers_pwl_ramp": ([C.POINTER(Pwl), I32, D, D, pi], C.c_int),
         "ers_fp64_fma_peak": ([I32, pd], C.c_int),
         "ers_run_batch": ([P, D, D, I32, pi, pi], C.c_int),
         "ers_get_state_inst": ([P, I32, pd, pd, pd], C.c_int),
@@ -209,6 +211,21 @@ def partition_lpt(costs, nparts: int) -> np.ndarray:
     if rc != 0:
         raise ErsError(rc, "partition: costs must be finite and >= 0, nparts >= 1")
     return out
+
+
+def pwl_ramp(pwl: Sequence, t: float, h: float) -> bool:
+    """The set-up step's ramp test on the host (see ers.h): True when some of the PWL inputs
+    (a sequence of (times, values)) has pwl(t + h) != pwl(t)."""
+    hold = [(np.ascontiguousarray(tt, np.float64), np.ascontiguousarray(vv, np.float64))
+            for tt, vv in pwl]
+    pw = (Pwl * max(1, len(hold)))()
+    for q, (tt, vv) in enumerate(hold):
+        pw[q] = Pwl(int(tt.size), _dptr(tt), _dptr(vv))
+    out = np.zeros(1, np.int32)
+    rc = lib().ers_pwl_ramp(pw, len(hold), float(t), float(h), _iptr(out))
+    if rc != 0:
+        raise ErsError(rc, "pwl_ramp: corner times must increase")
+    return bool(out[0])
 
 
 def _dptr(a: np.ndarray):

@@ -235,3 +235,57 @@ def test_device_list_refusals_without_a_gpu(E):
     with pytest.raises(E.ErsError) as ei:
         E.BatchSimulator([c, c], devices=[0, 10 ** 6])
     assert ei.value.status == 1
+
+
+def _py_pwl(tt, vv, x):
+    """PWL value at x: the last corner at or before x, linear to the next (separate roundings)."""
+    if x <= tt[0]:
+        return vv[0]
+    if x >= tt[-1]:
+        return vv[-1]
+    lo, hi = 0, len(tt) - 1
+    while hi - lo > 1:
+        mid = (lo + hi) >> 1
+        if tt[mid] <= x:
+            lo = mid
+        else:
+            hi = mid
+    f = (x - tt[lo]) / (tt[hi] - tt[lo])
+    prod = f * (vv[hi] - vv[lo])
+    return vv[lo] + prod
+
+
+def test_pwl_ramp_matches_brute_force(E):
+    """The host ramp test of a step's set-up (Eq. 12-13: the v2 / w1 terms exist only when an
+    input has a non-zero slope over the step) equals the brute-force evaluation of every input
+    at t and t + h, including its shortcut over the ranges where some input changes: pulses
+    with flat tops, steep edges, steps that start or end exactly on a corner, h = 0."""
+    rng = np.random.default_rng(11)
+    for trial in range(60):
+        pwl = []
+        corners = []
+        for q in range(int(rng.integers(1, 6))):
+            d = float(rng.uniform(0, 5e-10))
+            rise = float(rng.choice([1e-15, 1e-11, 3e-11]))
+            width = float(rng.uniform(1e-11, 2e-10))
+            amp = float(rng.choice([0.0, 1e-3, -2e-3]))
+            tt = [0.0, d, d + rise, d + rise + width, d + 2 * rise + width, 1e-9]
+            tt = sorted(set(tt))
+            vv = [0.0] * len(tt)
+            for k, x in enumerate(tt):
+                if d + rise <= x <= d + rise + width:
+                    vv[k] = amp
+            pwl.append((tt, vv))
+            corners += tt
+        for _ in range(40):
+            if rng.random() < 0.5:
+                t = float(rng.choice(corners))
+                h = float(rng.choice(corners)) - t if rng.random() < 0.5 else float(rng.uniform(0, 5e-11))
+            else:
+                t = float(rng.uniform(0, 1e-9))
+                h = float(rng.uniform(0, 5e-11))
+            want = h > 0 and any(_py_pwl(tt, vv, t + h) != _py_pwl(tt, vv, t) for tt, vv in pwl)
+            assert E.pwl_ramp(pwl, t, h) == want, (trial, t, h)
+    assert not E.pwl_ramp([([0.0, 1e-12], [0.0, 1.0])], 0.5e-12, 0.0)
+    with pytest.raises(E.ErsError):
+        E.pwl_ramp([([1e-12, 1e-12], [0.0, 1.0])], 0.0, 1e-12)
